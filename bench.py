@@ -1,0 +1,344 @@
+#!/usr/bin/env python
+"""Throughput of the vectorised object-MLP training step (vMAP, section 3.2).
+
+Workload (default, "room50"): 50 object MLPs (hidden 32, rays per object
+log-uniform in 32-600) plus one background MLP (hidden 128, 1,200 rays), 22
+samples per ray, every object present (the steady state after the last
+incremental insertion), FP32. One step = ray picking + depth-guided sampling
++ encoding + MLP forward + rendering + losses + backward + Adam for all 51
+objects.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line. Under torchrun every rank trains its own 51-object
+scene (objects are independent, no collective on the data path: weak
+scaling); rank 0 prints the aggregate.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "object-MLP train steps/s and sampled pts/s at 50 objs; time-to-depth-L1 vs FP32"
+UNIT = "pts/s"
+L2_FLUSH_BYTES = 512 << 20   # > 126 MB L2
+FP32_LANES_PER_SM = 128      # FFMA lanes per SM (4 SMSPs x 32)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=12, help="oracle steps of the CPU baseline sample")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def rank_seed(rank):
+    """Each rank trains its own independent scene (the unit of sharding is an object)."""
+    return 2 + 1000 * rank
+
+
+def workload(rank):
+    from paper_2302_01838_b300 import scenes
+    return scenes.scene_room(seed=rank_seed(rank))
+
+
+def samples_per_step(scene):
+    return sum(o["rays"] * (o["n_surface"] + o["n_strat"]) for o in scene["objects"])
+
+
+def flops_per_sample(H):
+    """Algorithmic flops of one sample's forward + backward MLP GEMMs:
+    forward F = 93H + 3H^2 + 4H MACs, weight gradient F MACs, input gradient
+    3H^2 + 4H MACs (layer 1 skipped); 2 flops per MAC."""
+    F = 93 * H + 3 * H * H + 4 * H
+    return 2 * (2 * F + 3 * H * H + 4 * H)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2302_01838_b300", "csrc")
+    for fn in sorted(os.listdir(d)):
+        with open(os.path.join(d, fn), "rb") as f:
+            h.update(fn.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the
+    current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        t = json.load(f)
+    e = t.get(kernel)
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e.get("bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled while the timed region runs."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [l.strip().split(",") for l in self.file.read().splitlines() if l.strip()]
+        os.unlink(self.file.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for n, v in zip(names, r[5:9]):
+                    if v.strip() == "Active":
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(scene, steps):
+    """The FP64 oracle as it stands on this host's cores: `steps` full steps of
+    the same 51-object workload."""
+    import numpy as np
+    from oracle import vmap_step as vs
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count()
+    cfg = vs.Config(seed=scene["seed"], B=np.asarray(scene["B"], np.float64))
+    st = [vs.ObjectState(H=o["H"], pool=o["pool"], center=np.asarray(o["center"], np.float64),
+                         scale=float(o["scale"]), n_surface=o["n_surface"], n_strat=o["n_strat"],
+                         stream=k, params=o["init"]) for k, o in enumerate(scene["objects"])]
+    R = [o["rays"] for o in scene["objects"]]
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        vs.train_step(cfg, st, R)
+    dt = time.perf_counter() - t0
+    return {"value": samples_per_step(scene) * steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} full steps of the room50 workload (51 objects, {samples_per_step(scene)} "
+                      f"samples/step), FP64 numpy, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    sc = workload(0)
+    import numpy as np
+    from oracle import vmap_step as vs
+    cfg = vs.Config(seed=sc["seed"], B=np.asarray(sc["B"], np.float64))
+    st = [vs.ObjectState(H=o["H"], pool=o["pool"], center=np.asarray(o["center"], np.float64),
+                         scale=float(o["scale"]), n_surface=o["n_surface"], n_strat=o["n_strat"],
+                         stream=k, params=o["init"]) for k, o in enumerate(sc["objects"])]
+    R = [o["rays"] for o in sc["objects"]]
+    for _ in range(args.warmup):
+        vs.train_step(cfg, st, R)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vs.train_step(cfg, st, R)
+    dt = time.perf_counter() - t0
+    sps = samples_per_step(sc)
+    value = sps * args.steps / dt
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count()
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": "room50: 50 objects (hidden 32) + background (hidden 128), 22 samples/ray",
+                      "objects": len(sc["objects"]), "samples_per_step": sps},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"{args.steps} full steps of the room50 workload"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2302_01838_b300.api import VMap
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    sc = workload(rank)
+    objs = sc["objects"]
+    R = [o["rays"] for o in objs]
+    K = len(objs)
+    vm = VMap(max_objects=K + 8, max_rays_total=2 * sum(R), max_pool_rays=sum(o["pool"].shape[0] for o in objs) + 16,
+              B=sc["B"], seed=sc["seed"])
+    for k, o in enumerate(objs):
+        vm.add_object(o["pool"], hidden=o["H"], center=o["center"], scale=float(o["scale"]),
+                      n_surface=o["n_surface"], n_strat=o["n_strat"], init_params=o["init"], stream_id=k)
+    sps = samples_per_step(sc)
+    loss = torch.empty(K, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device="cuda")
+    for _ in range(max(args.warmup, 3)):
+        vm.sample_rays(R)
+        vm.train_step(loss)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    vm.profile_reset()
+    vm.profile_enable(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(float(i))            # L2 flush between timed steps (not timed)
+        ev[i][0].record()
+        vm.sample_rays(R)
+        vm.train_step(loss)
+        ev[i][1].record()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    vm.profile_enable(False)
+    prof = vm.profile()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    assert np.all(np.isfinite(loss.cpu().numpy())), "non-finite loss"
+
+    # ---- end to end through the C ABI with host buffers --------------------
+    rng = np.random.default_rng(rank_seed(rank))
+    n_batches = 4
+    host_batches = []
+    for _ in range(n_batches):
+        parts = [o["pool"][rng.integers(0, o["pool"].shape[0], o["rays"])] for o in objs]
+        host_batches.append(torch.from_numpy(np.concatenate(parts)).pin_memory())
+    loss_h = torch.empty(K, dtype=torch.float32).pin_memory()
+    for i in range(3):
+        vm.train_step_host(host_batches[i % n_batches], R, loss_h)
+    torch.cuda.synchronize()
+    e2e_s = 0.0
+    for i in range(args.e2e_steps):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        vm.train_step_host(host_batches[i % n_batches], R, loss_h)
+        e2e_s += time.perf_counter() - t0
+    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_s = float(e2e_t.item())
+
+    if rank == 0:
+        peaks = measured_peaks()
+        props = torch.cuda.get_device_properties(local)
+        sm_max = peaks.get("sm_max_mhz", 2032.0)
+        fp32_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        # dominant kernel by device time
+        tiles = {k: v for k, v in prof.items() if k.startswith("k_tile")}
+        dom = max(tiles, key=lambda k: tiles[k][1])
+        Hd = int(dom.split("<")[1].rstrip(">"))
+        flops = sum(o["rays"] * (o["n_surface"] + o["n_strat"]) * flops_per_sample(o["H"])
+                    for o in objs if o["H"] == Hd)
+        launches, dom_ms = tiles[dom]
+        achieved = flops / (dom_ms / launches * 1e-3) / 1e12
+        traffic = traffic_for(dom)
+        value = world * sps * args.steps / (ms_max * 1e-3)
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "steps_per_s": 1e3 * args.steps / ms_max,
+            "config": {"workload": "room50: 50 objects (hidden 32, 32-600 rays) + background (hidden 128, 1200 rays), "
+                                   "22 samples/ray, FP32, all objects present",
+                       "objects_per_gpu": K, "samples_per_step_per_gpu": sps,
+                       "rays_per_step_per_gpu": sum(R), "l2": "flushed (512 MB write) between timed steps",
+                       "parallelism": f"objects sharded, {world} independent scene(s), no collective"},
+            "roofline": {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": fp32_peak,
+                         "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
+                         "peak_note": f"FP32 FFMA: {props.multi_processor_count} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_max:.0f} MHz",
+                         "flops_per_launch": flops, "avg_launch_ms": dom_ms / launches},
+            "kernels": {k: {"launches": n, "total_ms": round(t_, 4), "share": round(t_ / sum(v[1] for v in prof.values()), 4)}
+                        for k, (n, t_) in prof.items()},
+            "gpu_launches": int(sum(n for n, _ in prof.values())),
+            "e2e": {"value": world * sps * args.e2e_steps / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": int(sum(R) * 48), "d2h_bytes_per_step": int(K * 4),
+                    "api": "vmap_train_step_host (pinned host rays in, host losses out, synchronous)"},
+            "clocks": clk,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(sc, args.cpu_steps)
+        print(json.dumps(out), flush=True)
+    vm.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,231 @@
+/*
+ * vmap.h - C ABI of the B300 (sm_103a) vectorised object-MLP training library.
+ *
+ * The library trains many independent per-object MLP occupancy/colour fields
+ * in one pass, as vMAP does (Kong, Liu, Taher, Davison, "vMAP: Vectorised
+ * Object Mapping for Neural Field SLAM", CVPR 2023, section 3.2 "Vectorised
+ * Training"). One training step, for every object k in the batch:
+ *   - picks R_k rays, uniformly with replacement, from the object's own ray
+ *     pool (section 3.2 "Object Supervision": each object samples its own
+ *     keyframes);
+ *   - draws N_c stratified depths in [t_near, t_s + depth_pad] (Eq. 1) and
+ *     N_s depths ~ N(t_s, d_sigma^2) (Eq. 2), t_s = the ray's depth, or t_far
+ *     when the depth is invalid (<= 0), sorted ascending;
+ *   - encodes x~ = (o + t d - c_k) / s_k (supplementary B, object-level
+ *     scale) as [x~, sin(B x~), cos(B x~)] (93 features, B is 45 x 3);
+ *   - runs the object's MLP 93 -> H -> H -> H -> H -> 4 (ReLU hidden units,
+ *     sigmoid occupancy and colour; section 4.1 "Implementation Details");
+ *   - renders T_i = o_i prod_{j<i}(1 - o_j), O^ = sum T_i, D^ = sum T_i t_i,
+ *     C^ = sum T_i c_i (Eq. 3);
+ *   - takes the loss L_k = mean_r M|D^ - D| + lambda_colour mean_{r,c} M|C^ - C|
+ *     + lambda_occ mean_r |O^ - M| (Eq. 4-5 read as means over the batch;
+ *     M is the ray's mask value, and the depth term is dropped for invalid
+ *     depths);
+ *   - back-propagates through rendering, MLP and encoding, and
+ *   - applies Adam with the object's own step count.
+ *
+ * Conventions
+ *   - Every call is stream-ordered and asynchronous on the stream given to
+ *     vmap_init_objects, unless its comment says it synchronises.
+ *   - Pointers documented as DEVICE must point to memory of the current
+ *     CUDA device; HOST pointers to host memory. Sizes are element counts.
+ *   - The library owns weights, Adam moments, ray pools and scratch; the
+ *     caller owns every buffer it passes in, and may reuse it as soon as the
+ *     stream has passed the call.
+ *   - No C++ exception crosses this boundary. Every function returns a
+ *     vmap_status; on failure vmap_last_error(ctx) gives a message. A failed
+ *     call leaves the context usable unless it returns VMAP_ERR_CUDA.
+ *   - Floating-point work is FP32 (VMAP_FP32) or BF16 tensor-core GEMMs with
+ *     FP32 accumulation, FP32 master weights, moments, rendering and losses
+ *     (VMAP_BF16).
+ *
+ * Ray record: 12 floats per ray, 48 bytes, row-major [n][12]:
+ *   [0..2] origin (world, metres)   [3..5] direction (world, unnormalised:
+ *   the ray parameter t is the camera z-depth)   [6] depth (<= 0: invalid)
+ *   [7..9] rgb in [0, 1]   [10] mask M (1 inside the object mask, 0 inside
+ *   its 2D box only)   [11] reserved, 0.
+ *
+ * Parameters of one object, canonical packed layout (P(H) floats):
+ *   W1 [H][93], b1 [H], W2 [H][H], b2 [H], W3 [H][H], b3 [H], W4 [H][H],
+ *   b4 [H], W5 [4][H], b5 [4]; W row-major [out][in].
+ *   P(16) = 2388, P(32) = 6308, P(64) = 18756, P(128) = 62084.
+ */
+#ifndef VMAP_H
+#define VMAP_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VMAP_REC_FLOATS 12
+#define VMAP_N_FREQ 45
+#define VMAP_D_IN 93
+#define VMAP_MAX_SAMPLES 32
+
+typedef struct vmap_ctx vmap_ctx;
+
+typedef enum {
+    VMAP_OK = 0,
+    VMAP_ERR_ARG = -1,       /* invalid argument (NULL, out of range, bad handle) */
+    VMAP_ERR_CAPACITY = -2,  /* a capacity fixed at vmap_init_objects is exceeded */
+    VMAP_ERR_CUDA = -3,      /* a CUDA call failed; the message names it */
+    VMAP_ERR_NAN = -4,       /* an object's loss or gradient was not finite: it is frozen */
+    VMAP_ERR_TIMEOUT = -5,   /* a bounded device-side wait gave up */
+    VMAP_ERR_STATE = -6      /* call out of order (e.g. train_step without sample_rays) */
+} vmap_status;
+
+enum { VMAP_FP32 = 0, VMAP_BF16 = 1 };
+
+typedef struct {
+    int max_objects;              /* objects the context can hold */
+    int max_rays_total;           /* rays per step over all objects */
+    long long max_pool_rays;      /* ray records over all object pools */
+    long long max_param_floats;   /* parameters over all objects; 0 = max_objects * P(128) */
+    float t_near;                 /* near bound t_n (0.05 m) */
+    float depth_pad;              /* stratified samples reach depth + pad (0.1 m) */
+    float d_sigma;                /* std of the surface samples (0.03 m, section 3.3) */
+    float t_far;                  /* far bound used for invalid depths */
+    float lambda_colour;          /* lambda_1 (5) */
+    float lambda_occ;             /* lambda_2 (0 on the plain path; 10 in the full objective) */
+    float lr, beta1, beta2, eps;  /* Adam (1e-3, 0.9, 0.999, 1e-8) */
+    int precision;                /* VMAP_FP32 or VMAP_BF16 */
+    unsigned long long seed;      /* Philox4x32-10 key of every random draw */
+    const float* B;               /* HOST [45][3] row-major encoding matrix; copied */
+} vmap_config;
+
+typedef struct {
+    int hidden;                   /* H: 16, 32, 64 or 128 */
+    int n_surface;                /* N_s Gaussian samples per ray */
+    int n_strat;                  /* N_c stratified samples per ray; 1 <= N_s + N_c <= 32 */
+    float center[3];              /* c_k: centre of the object's bound (world) */
+    float scale;                  /* s_k > 0: maps the bound into about [-1, 1]^3 */
+    const float* rays;            /* DEVICE [n_rays][12] ray records; copied into the pool */
+    long long n_rays;             /* >= 1 */
+    unsigned int stream;          /* Philox stream id of the object (its draws depend only
+                                     on seed, stream, its own step count and the ray index) */
+} vmap_object_desc;
+
+/* Fill *cfg with the defaults listed above (capacities 0 must be set). */
+void vmap_default_config(vmap_config* cfg);
+
+/* Create a context on the current device. cuda_stream is a cudaStream_t
+ * (NULL = legacy default stream). Allocates every arena up front from the
+ * capacities in *cfg. Synchronises. */
+vmap_status vmap_init_objects(vmap_ctx** out, const vmap_config* cfg, void* cuda_stream);
+
+/* Free the context and all device memory it owns. Synchronises. NULL is a no-op. */
+vmap_status vmap_destroy(vmap_ctx* ctx);
+
+/* Message of the last failed call on ctx ("" if none). Valid until the next call. */
+const char* vmap_last_error(const vmap_ctx* ctx);
+
+/* Add an object (section 3.2: a new object model appended to the stack).
+ * init_params: DEVICE [P(H)] canonical layout, or NULL for the seeded default
+ * U(-1/sqrt(fan_in), 1/sqrt(fan_in)) draw. Adam moments start at zero and the
+ * object's step count at 0. *out_id (HOST) receives the object index. Objects
+ * can be added between any two steps; nothing already recorded must change. */
+vmap_status vmap_add_object(vmap_ctx* ctx, const vmap_object_desc* desc,
+                            const float* init_params, int* out_id);
+
+/* Draw this step's batch: rays_per_object HOST [n_objects], R_k >= 0 rays of
+ * object k (0 = object k sits this step out; inactive objects are skipped).
+ * Picks rays and draws sorted sample depths (Eq. 1-2) on the device. */
+vmap_status vmap_sample_rays(vmap_ctx* ctx, const int* rays_per_object);
+
+/* Like vmap_sample_rays, but the caller gives this step's rays instead of
+ * the library picking them from the pools (e.g. a caller with its own
+ * keyframe buffers). rays: DEVICE [sum_k R_k][12], object-major: the R_k
+ * rays of every active object with R_k > 0, in object-index order. The
+ * records are copied; sample depths are drawn on the device as above. */
+vmap_status vmap_sample_rays_given(vmap_ctx* ctx, const float* rays, const int* rays_per_object);
+
+/* One whole step for a caller whose data lives in host memory: copies the
+ * given rays (HOST [sum_k R_k][12], layout as vmap_sample_rays_given; pinned
+ * memory makes the copy asynchronous), draws depths, trains, and copies the
+ * per-object losses to loss (HOST [n_objects], NaN for objects not trained).
+ * Synchronises. */
+vmap_status vmap_train_step_host(vmap_ctx* ctx, const float* rays, const int* rays_per_object,
+                                 float* loss);
+
+/* One training step over the batch drawn by the last vmap_sample_rays:
+ * forward, rendering, loss, backward and Adam for every object in it, then
+ * each trained object's step count advances. out_loss: DEVICE [n_objects]
+ * or NULL; receives L_k before the update (NaN for objects not trained).
+ * An object whose loss or gradient is not finite is frozen and flagged (see
+ * vmap_sync_status); the others are unaffected. */
+vmap_status vmap_train_step(vmap_ctx* ctx, float* out_loss);
+
+/* Loss of the current batch without changing any state.
+ * out_loss: DEVICE [n_objects] (NaN for objects not in the batch). */
+vmap_status vmap_forward(vmap_ctx* ctx, float* out_loss);
+
+/* Gradients of sum_k grad_loss[k] * L_k over the current batch, no update.
+ * grad_loss: DEVICE [n_objects] or NULL (all ones). grad_params: DEVICE,
+ * parameter-arena layout (vmap_param_arena_size floats, object k's block at
+ * its vmap_object_info offset); entries of objects outside the batch are
+ * left untouched. grad_center: DEVICE [n_objects][3] or NULL: dL/dc_k through
+ * the encoding (the encoding backward). */
+vmap_status vmap_backward(vmap_ctx* ctx, const float* grad_loss, float* grad_params,
+                          float* grad_center);
+
+/* Occupancy (and colour) of n arbitrary world points of one object (section
+ * 3.4: an object is queried inside its bound). pts DEVICE [n][3];
+ * occ DEVICE [n]; rgb DEVICE [n][3] or NULL. n = 0 is a no-op. */
+vmap_status vmap_query_occupancy(vmap_ctx* ctx, int obj, const float* pts, long long n,
+                                 float* occ, float* rgb);
+
+/* Rendered depth of n rays of one object with n_samples stratified
+ * midpoints between the ray's entry and exit of the box c_k +- box_half
+ * (world, metres). rays DEVICE [n][12] (only origin and direction are read);
+ * depth DEVICE [n]; a ray that misses the box renders 0. */
+vmap_status vmap_render_depth(vmap_ctx* ctx, int obj, const float* rays, long long n,
+                              const float* box_half, int n_samples, float* depth);
+
+/* Object state in canonical layout. Any DEVICE pointer may be NULL.
+ * step: HOST, may be NULL (reading it synchronises). */
+vmap_status vmap_get_object_state(vmap_ctx* ctx, int obj, float* params, float* m, float* v,
+                                  int* step);
+vmap_status vmap_set_object_state(vmap_ctx* ctx, int obj, const float* params, const float* m,
+                                  const float* v, int step);
+
+/* Whole parameter arena (all objects, vmap_param_arena_size floats), DEVICE. */
+vmap_status vmap_get_params(vmap_ctx* ctx, float* arena);
+vmap_status vmap_set_params(vmap_ctx* ctx, const float* arena);
+vmap_status vmap_param_arena_size(vmap_ctx* ctx, long long* n_floats);
+
+/* Stop (0) or resume (1) training of one object (section 3.2: training of any
+ * object can stop and resume with no interference). Takes effect at the
+ * next vmap_sample_rays. Resuming clears a NaN freeze. */
+vmap_status vmap_set_object_active(vmap_ctx* ctx, int obj, int active);
+
+/* Move an object's centre c_k (HOST [3]). Takes effect at the next call. */
+vmap_status vmap_set_object_center(vmap_ctx* ctx, int obj, const float* center);
+
+/* HOST outputs, any may be NULL. */
+vmap_status vmap_object_info(vmap_ctx* ctx, int obj, int* hidden, int* param_count,
+                             long long* param_offset, int* samples_per_ray);
+vmap_status vmap_num_objects(vmap_ctx* ctx, int* n);
+
+/* The current batch, for inspection: total rays and samples (HOST), and
+ * DEVICE copies of the picked pool indices [rays] and sample depths
+ * [samples] (object-major, ray-major, sorted per ray). Either array may be NULL. */
+vmap_status vmap_batch_info(vmap_ctx* ctx, int* n_rays, long long* n_samples);
+vmap_status vmap_get_samples(vmap_ctx* ctx, int* pick, float* t);
+
+/* Synchronise and report frozen objects: *n_faulted (HOST) and, if ids is
+ * not NULL, up to max_ids of their indices. Returns VMAP_ERR_NAN if any. */
+vmap_status vmap_sync_status(vmap_ctx* ctx, int* n_faulted, int* ids, int max_ids);
+
+/* Tracing: with profiling enabled, every kernel launch is bracketed by CUDA
+ * events on the context stream. vmap_profile_read synchronises and returns,
+ * for kernel slot `slot` (0 .. until VMAP_ERR_ARG), its name (static
+ * string), launch count and summed device milliseconds since the last reset. */
+vmap_status vmap_profile_enable(vmap_ctx* ctx, int on);
+vmap_status vmap_profile_reset(vmap_ctx* ctx);
+vmap_status vmap_profile_read(vmap_ctx* ctx, int slot, const char** name, long long* launches,
+                              double* total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VMAP_H */

@@ -136,6 +136,20 @@ def sample_object(cfg, pool, n_rays, n_surface, n_strat, stream, step):
     w = ray_words(cfg.seed, stream, step, np.arange(n_rays), n_words)
     pick = word_to_index(w[:, 0], pool.shape[0])
     depth = pool[pick, R_DEPTH].astype(np.float64)
+    return pick, sample_depths(cfg, depth, w, n_surface, n_strat)
+
+
+def sample_given(cfg, rays, n_surface, n_strat, stream, step):
+    """Sorted sample depths for rays the caller chose: the same draws as
+    ``sample_object`` with word 0 (the pick) unused."""
+    n_words = words_per_ray(n_surface, n_strat)
+    w = ray_words(cfg.seed, stream, step, np.arange(rays.shape[0]), n_words)
+    return sample_depths(cfg, rays[:, R_DEPTH].astype(np.float64), w, n_surface, n_strat)
+
+
+def sample_depths(cfg, depth, w, n_surface, n_strat):
+    """Eq. 1 and Eq. 2 for rays of the given depths from their Philox words w."""
+    n_rays = depth.shape[0]
     ts = np.where(depth > 0.0, depth, cfg.t_far)
     lo = cfg.t_near
     hi = ts + cfg.depth_pad
@@ -152,7 +166,7 @@ def sample_object(cfg, pool, n_rays, n_surface, n_strat, stream, step):
         z[:, 2 * p + 1] = rho * np.sin(2.0 * np.pi * u2)
     surf = np.maximum(ts[:, None] + cfg.d_sigma * z[:, :n_surface], cfg.t_near)
     t = np.concatenate([surf, strat], axis=1)
-    return pick, np.sort(t, axis=1, kind="stable")
+    return np.sort(t, axis=1, kind="stable")
 
 
 # ----------------------------------------------------------------------------
@@ -349,8 +363,11 @@ class ObjectState:
             self.v = np.zeros(P)
 
 
-def train_step(cfg, objects, rays_per_object):
+def train_step(cfg, objects, rays_per_object, given=None):
     """One vectorised step: every active object trains on its own batch.
+
+    given: optional list of per-object ray arrays chosen by the caller (the
+    pick is then skipped, see ``sample_given``).
 
     Objects are independent: nothing of object j enters object k's loss or
     update (the objective of Eq. 5 is a plain sum over objects). Returns the
@@ -362,8 +379,12 @@ def train_step(cfg, objects, rays_per_object):
     for k, (ob, R) in enumerate(zip(objects, rays_per_object)):
         if not ob.active or R <= 0:
             continue
-        pick, t = sample_object(cfg, ob.pool, R, ob.n_surface, ob.n_strat, ob.stream, ob.step)
-        rays = ob.pool[pick].astype(np.float64)
+        if given is None:
+            pick, t = sample_object(cfg, ob.pool, R, ob.n_surface, ob.n_strat, ob.stream, ob.step)
+            rays = ob.pool[pick].astype(np.float64)
+        else:
+            rays = np.asarray(given[k], np.float64)
+            t = sample_given(cfg, rays, ob.n_surface, ob.n_strat, ob.stream, ob.step)
         res = object_forward_backward(cfg, ob.params, ob.H, rays, t, ob.center, ob.scale)
         losses[k] = res["loss"]
         if not (np.isfinite(res["loss"]) and np.all(np.isfinite(res["grad"]))):

@@ -1,0 +1,244 @@
+"""Thin Python wrapper over the C ABI (argument marshalling only).
+
+torch is used for device memory and streams: tensors are passed to the
+library as raw pointers, the context runs on torch's current CUDA stream.
+"""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import native
+from .native import VmapConfig, VmapError, VmapObjectDesc
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class VMap:
+    """One training context: a stack of per-object MLPs trained together."""
+
+    def __init__(self, max_objects, max_rays_total, max_pool_rays, B, seed=0,
+                 max_param_floats=0, stream=None, **hyper):
+        self.lib = native.load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("the vMAP library needs a CUDA device")
+        cfg = VmapConfig()
+        self.lib.vmap_default_config(ctypes.byref(cfg))
+        cfg.max_objects = int(max_objects)
+        cfg.max_rays_total = int(max_rays_total)
+        cfg.max_pool_rays = int(max_pool_rays)
+        cfg.max_param_floats = int(max_param_floats)
+        cfg.seed = int(seed)
+        for k, v in hyper.items():
+            if not hasattr(cfg, k):
+                raise TypeError(f"unknown hyper-parameter {k}")
+            setattr(cfg, k, v)
+        self._B = np.ascontiguousarray(np.asarray(B, np.float32).reshape(native.N_FREQ, 3))
+        cfg.B = self._B.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        st = self.lib.vmap_init_objects(ctypes.byref(h), ctypes.byref(cfg),
+                                        ctypes.c_void_p(self.stream.cuda_stream))
+        if st != 0:
+            raise VmapError(st, "vmap_init_objects failed")
+        self.h = h
+        self.cfg = cfg
+
+    # ------------------------------------------------------------------
+    def _check(self, st):
+        if st != 0:
+            raise VmapError(st, self.lib.vmap_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.vmap_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------
+    def add_object(self, rays, hidden=32, center=(0, 0, 0), scale=1.0, n_surface=10, n_strat=12,
+                   init_params=None, stream_id=None):
+        rays = torch.as_tensor(rays, dtype=torch.float32).reshape(-1, native.REC_FLOATS)
+        rays = rays.to("cuda").contiguous()
+        d = VmapObjectDesc()
+        d.hidden = int(hidden)
+        d.n_surface = int(n_surface)
+        d.n_strat = int(n_strat)
+        for a in range(3):
+            d.center[a] = float(center[a])
+        d.scale = float(scale)
+        d.rays = _ptr(rays).value
+        d.n_rays = rays.shape[0]
+        d.stream = self.num_objects() if stream_id is None else int(stream_id)
+        ip = None
+        if init_params is not None:
+            init_params = torch.as_tensor(init_params, dtype=torch.float32).to("cuda").contiguous()
+            ip = _ptr(init_params)
+        oid = ctypes.c_int()
+        self._check(self.lib.vmap_add_object(self.h, ctypes.byref(d), ip, ctypes.byref(oid)))
+        return oid.value
+
+    def num_objects(self):
+        n = ctypes.c_int()
+        self._check(self.lib.vmap_num_objects(self.h, ctypes.byref(n)))
+        return n.value
+
+    def sample_rays(self, rays_per_object):
+        arr = (ctypes.c_int * len(rays_per_object))(*[int(r) for r in rays_per_object])
+        self._check(self.lib.vmap_sample_rays(self.h, arr))
+
+    def sample_rays_given(self, rays, rays_per_object):
+        arr = (ctypes.c_int * len(rays_per_object))(*[int(r) for r in rays_per_object])
+        self._check(self.lib.vmap_sample_rays_given(self.h, _ptr(rays), arr))
+
+    def train_step_host(self, rays, rays_per_object, loss_out):
+        """rays, loss_out: CPU tensors (pinned for an asynchronous copy)."""
+        if rays.is_cuda or loss_out.is_cuda:
+            raise ValueError("train_step_host takes host tensors")
+        arr = (ctypes.c_int * len(rays_per_object))(*[int(r) for r in rays_per_object])
+        self._check(self.lib.vmap_train_step_host(self.h, ctypes.c_void_p(rays.data_ptr()), arr,
+                                                  ctypes.c_void_p(loss_out.data_ptr())))
+        return loss_out
+
+    def profile_enable(self, on=True):
+        self._check(self.lib.vmap_profile_enable(self.h, int(bool(on))))
+
+    def profile_reset(self):
+        self._check(self.lib.vmap_profile_reset(self.h))
+
+    def profile(self):
+        """{kernel name: (launches, total device ms)} since the last reset."""
+        out = {}
+        slot = 0
+        while True:
+            name = ctypes.c_char_p()
+            n = ctypes.c_longlong()
+            ms = ctypes.c_double()
+            st = self.lib.vmap_profile_read(self.h, slot, ctypes.byref(name), ctypes.byref(n),
+                                            ctypes.byref(ms))
+            if st != 0:
+                break
+            if n.value:
+                out[name.value.decode()] = (n.value, ms.value)
+            slot += 1
+        return out
+
+    def train_step(self, out_loss=None):
+        self._check(self.lib.vmap_train_step(self.h, _ptr(out_loss)))
+        return out_loss
+
+    def forward(self, out_loss):
+        self._check(self.lib.vmap_forward(self.h, _ptr(out_loss)))
+        return out_loss
+
+    def backward(self, grad_params, grad_loss=None, grad_center=None):
+        self._check(self.lib.vmap_backward(self.h, _ptr(grad_loss), _ptr(grad_params),
+                                           _ptr(grad_center)))
+
+    def query_occupancy(self, obj, pts, occ, rgb=None):
+        self._check(self.lib.vmap_query_occupancy(self.h, int(obj), _ptr(pts), pts.shape[0],
+                                                  _ptr(occ), _ptr(rgb)))
+
+    def render_depth(self, obj, rays, box_half, n_samples, depth):
+        hb = (ctypes.c_float * 3)(*[float(x) for x in box_half])
+        self._check(self.lib.vmap_render_depth(self.h, int(obj), _ptr(rays), rays.shape[0], hb,
+                                               int(n_samples), _ptr(depth)))
+
+    def object_info(self, obj):
+        H, P, S = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        off = ctypes.c_longlong()
+        self._check(self.lib.vmap_object_info(self.h, int(obj), ctypes.byref(H), ctypes.byref(P),
+                                              ctypes.byref(off), ctypes.byref(S)))
+        return dict(hidden=H.value, param_count=P.value, param_offset=off.value,
+                    samples_per_ray=S.value)
+
+    def get_object_state(self, obj):
+        P = self.object_info(obj)["param_count"]
+        p = torch.empty(P, device="cuda")
+        m = torch.empty(P, device="cuda")
+        v = torch.empty(P, device="cuda")
+        st = ctypes.c_int()
+        self._check(self.lib.vmap_get_object_state(self.h, int(obj), _ptr(p), _ptr(m), _ptr(v),
+                                                   ctypes.byref(st)))
+        return p, m, v, st.value
+
+    def set_object_state(self, obj, params=None, m=None, v=None, step=0):
+        self._check(self.lib.vmap_set_object_state(self.h, int(obj), _ptr(params), _ptr(m),
+                                                   _ptr(v), int(step)))
+
+    def arena_size(self):
+        n = ctypes.c_longlong()
+        self._check(self.lib.vmap_param_arena_size(self.h, ctypes.byref(n)))
+        return n.value
+
+    def get_params(self):
+        out = torch.empty(self.arena_size(), device="cuda")
+        self._check(self.lib.vmap_get_params(self.h, _ptr(out)))
+        return out
+
+    def set_params(self, arena):
+        self._check(self.lib.vmap_set_params(self.h, _ptr(arena)))
+
+    def set_object_active(self, obj, active):
+        self._check(self.lib.vmap_set_object_active(self.h, int(obj), int(bool(active))))
+
+    def set_object_center(self, obj, center):
+        c = (ctypes.c_float * 3)(*[float(x) for x in center])
+        self._check(self.lib.vmap_set_object_center(self.h, int(obj), c))
+
+    def batch_info(self):
+        r, s = ctypes.c_int(), ctypes.c_longlong()
+        self._check(self.lib.vmap_batch_info(self.h, ctypes.byref(r), ctypes.byref(s)))
+        return r.value, s.value
+
+    def get_samples(self):
+        r, s = self.batch_info()
+        pick = torch.empty(r, dtype=torch.int32, device="cuda")
+        t = torch.empty(s, dtype=torch.float32, device="cuda")
+        self._check(self.lib.vmap_get_samples(self.h, _ptr(pick), _ptr(t)))
+        return pick, t
+
+    def sync_status(self, max_ids=1024):
+        n = ctypes.c_int()
+        ids = (ctypes.c_int * max_ids)()
+        st = self.lib.vmap_sync_status(self.h, ctypes.byref(n), ids, max_ids)
+        if st not in (0, -4):
+            self._check(st)
+        return [ids[i] for i in range(min(n.value, max_ids))]
+
+
+class VMapLoss(torch.autograd.Function):
+    """Per-object losses of the current batch as a differentiable function of the
+    whole parameter arena and of the object centres; forward and backward run
+    in the library (vmap_forward / vmap_backward)."""
+
+    @staticmethod
+    def forward(ctx, vm, params, centers):
+        vm.set_params(params.detach().contiguous())
+        for k in range(vm.num_objects()):
+            vm.set_object_center(k, centers[k].tolist())
+        loss = torch.empty(vm.num_objects(), device="cuda")
+        vm.forward(loss)
+        ctx.vm = vm
+        return loss
+
+    @staticmethod
+    def backward(ctx, grad_loss):
+        vm = ctx.vm
+        gp = torch.zeros(vm.arena_size(), device="cuda")
+        gc = torch.zeros(vm.num_objects(), 3, device="cuda")
+        vm.backward(gp, grad_loss=grad_loss.contiguous(), grad_center=gc)
+        return None, gp, gc

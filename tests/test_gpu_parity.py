@@ -1,0 +1,376 @@
+"""Parity of the CUDA library with the FP64 oracle, through the C ABI.
+
+Tolerances (FP32 library vs FP64 oracle):
+  * picked ray indices: bit-exact (integer work);
+  * sample depths: |dt| <= 1e-6 |t| + 1e-6 (FP32 arithmetic of the same formulas);
+  * per-step loss: 1e-5 relative, per object;
+  * weights after the steps, gradients: relative L2 error per weight or
+    bias tensor <= 1e-4 (an elementwise bound would be wrong for Adam, whose
+    first steps move every weight by about lr * sign(g), so a gradient within
+    FP32 noise of zero may legitimately move the other way). Rows of hidden
+    units whose pre-activation came within 1e-5 of zero on some sample (a
+    ReLU kink, where FP32 and FP64 may take different sides) are left out of
+    the weight comparison of the mixed-width stress test; at most half of a
+    layer's rows may be left out. The 20-step small-scene test compares every
+    row.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import evaluate as ev
+from oracle import vmap_step as vs
+from paper_2302_01838_b300 import scenes
+
+import vmap_harness as vh
+
+pytestmark = pytest.mark.gpu
+
+LOSS_RTOL = 1e-5
+W_RTOL = 1e-4
+
+
+def _check_samples(vm, scene, rays_per_object, steps):
+    cfg = vh.oracle_config(scene)
+    pick, t = vm.get_samples()
+    pick = pick.cpu().numpy()
+    t = t.cpu().numpy().astype(np.float64)
+    ro = so = 0
+    for k, o in enumerate(scene["objects"]):
+        R = rays_per_object[k]
+        if R == 0:
+            continue
+        S = o["n_surface"] + o["n_strat"]
+        pk, tk = vs.sample_object(cfg, o["pool"], R, o["n_surface"], o["n_strat"], k, steps[k])
+        assert np.array_equal(pick[ro:ro + R], pk), f"object {k}: picks differ"
+        tg = t[so:so + R * S].reshape(R, S)
+        err = np.abs(tg - tk)
+        assert np.all(err <= 1e-6 * np.abs(tk) + 1e-6), f"object {k}: max dt {err.max()}"
+        assert np.all(np.diff(tg, axis=1) >= 0)
+        ro += R
+        so += R * S
+
+
+def test_sampler_matches_oracle():
+    sc = vh.mixed_scene(seed=11)
+    vm = vh.library_context(sc)
+    R = [o["rays"] for o in sc["objects"]]
+    vm.sample_rays(R)
+    _check_samples(vm, sc, R, [0] * len(R))
+    # after a step every trained object draws from its own next step
+    vm.train_step()
+    R2 = list(R)
+    R2[2] = 0
+    vm.sample_rays(R2)
+    _check_samples(vm, sc, R2, [1] * len(R))
+
+
+def test_train_step_parity_small_scene_20_steps():
+    """4 objects x 120 rays x 22 samples, hidden 32, 20 steps (FP32 vs FP64)."""
+    sc = scenes.scene_small(seed=1)
+    vm = vh.library_context(sc)
+    cfg = vh.oracle_config(sc)
+    ost = vh.oracle_states(sc)
+    K = len(ost)
+    loss = torch.empty(K, device="cuda")
+    for step in range(20):
+        vm.sample_rays([120] * K)
+        vm.train_step(loss)
+        Lo = vs.train_step(cfg, ost, [120] * K)
+        Lg = loss.cpu().numpy().astype(np.float64)
+        rel = np.abs(Lg - Lo) / np.abs(Lo)
+        assert np.all(rel <= LOSS_RTOL), f"step {step}: loss rel err {rel}"
+    for k in range(K):
+        p, m, v, st = vm.get_object_state(k)
+        assert st == 20
+        errs = vh.layer_errors(p.cpu().numpy(), ost[k].params, 32)
+        assert max(errs) <= W_RTOL, f"object {k}: weight errors {errs}"
+
+
+def test_train_step_parity_mixed_widths_ragged_tiles():
+    """H in {16, 32, 64, 128}, S in {16, 22, 32}, rays spanning several tiles,
+    a ragged last tile and a single-ray object; 3 steps."""
+    sc = vh.mixed_scene(seed=12)
+    vm = vh.library_context(sc)
+    cfg = vh.oracle_config(sc)
+    ost = vh.oracle_states(sc)
+    K = len(ost)
+    R = [o["rays"] for o in sc["objects"]]
+    loss = torch.empty(K, device="cuda")
+    skip = [dict() for _ in range(K)]
+    for step in range(3):
+        vm.sample_rays(R)
+        vm.train_step(loss)
+        for k in range(K):
+            for l, rows in vh.kink_rows(cfg, ost[k], R[k]).items():
+                skip[k].setdefault(l, set()).update(rows)
+        Lo = vs.train_step(cfg, ost, R)
+        rel = np.abs(loss.cpu().numpy() - Lo) / np.abs(Lo)
+        assert np.all(rel <= LOSS_RTOL), f"step {step}: {rel}"
+    for k in range(K):
+        p, _, _, st = vm.get_object_state(k)
+        assert st == 3
+        errs = vh.layer_errors_masked(p.cpu().numpy(), ost[k].params, ost[k].H, skip[k])
+        assert max(errs) <= W_RTOL, f"object {k} (H={ost[k].H}): {errs}, kink rows {skip[k]}"
+        assert all(len(r) <= ost[k].H // 2 for r in skip[k].values()), skip[k]
+
+
+def test_gradients_and_center_gradient_match_oracle():
+    sc = vh.mixed_scene(seed=13)
+    vm = vh.library_context(sc)
+    cfg = vh.oracle_config(sc)
+    K = len(sc["objects"])
+    R = [o["rays"] for o in sc["objects"]]
+    vm.sample_rays(R)
+    gp = torch.zeros(vm.arena_size(), device="cuda")
+    gc = torch.zeros(K, 3, device="cuda")
+    gl = torch.linspace(0.5, 2.0, K, device="cuda")
+    vm.backward(gp, grad_loss=gl, grad_center=gc)
+    gp = gp.cpu().numpy()
+    gc = gc.cpu().numpy()
+    for k, o in enumerate(sc["objects"]):
+        pk, tk = vs.sample_object(cfg, o["pool"], R[k], o["n_surface"], o["n_strat"], k, 0)
+        res = vs.object_forward_backward(cfg, np.asarray(o["init"], np.float64), o["H"],
+                                         o["pool"][pk].astype(np.float64), tk,
+                                         np.asarray(o["center"], np.float64), float(o["scale"]),
+                                         want_center_grad=True)
+        info = vm.object_info(k)
+        g = gp[info["param_offset"]:info["param_offset"] + info["param_count"]]
+        w = float(gl[k])
+        errs = vh.layer_errors(g, w * res["grad"], o["H"])
+        assert max(errs) <= W_RTOL, f"object {k}: {errs}"
+        assert vh.rel_l2(gc[k], w * res["dcenter"]) <= 1e-3, f"object {k}: {gc[k]} vs {w * res['dcenter']}"
+
+
+def test_forward_loss_matches_train_step_loss_and_changes_nothing():
+    sc = scenes.scene_small(seed=3)
+    vm = vh.library_context(sc)
+    K = len(sc["objects"])
+    vm.sample_rays([120] * K)
+    lf = torch.empty(K, device="cuda")
+    vm.forward(lf)
+    p0 = vm.get_params().clone()
+    vm.forward(lf)
+    assert torch.equal(p0, vm.get_params())
+    lt = torch.empty(K, device="cuda")
+    vm.train_step(lt)
+    assert torch.equal(lf, lt)
+
+
+def test_query_and_render_depth_match_oracle():
+    sc = vh.mixed_scene(seed=14)
+    vm = vh.library_context(sc)
+    cfg = vh.oracle_config(sc)
+    rng = np.random.default_rng(0)
+    for k, o in enumerate(sc["objects"]):
+        n = 1000 + k
+        pts = (o["center"] + rng.uniform(-1, 1, (n, 3)) * o["scale"]).astype(np.float32)
+        occ = torch.empty(n, device="cuda")
+        rgb = torch.empty(n, 3, device="cuda")
+        vm.query_occupancy(k, torch.from_numpy(pts).cuda(), occ, rgb)
+        oo, co = vs.query(cfg, np.asarray(o["init"], np.float64), o["H"], o["center"], o["scale"], pts)
+        assert np.max(np.abs(occ.cpu().numpy() - oo)) < 2e-6
+        assert np.max(np.abs(rgb.cpu().numpy() - co)) < 2e-6
+        # held-out style rendering: 300 pool rays, box = 1.1 x bound
+        rays = o["pool"][:300].copy()
+        half = np.full(3, 1.1 * o["scale"], np.float32)
+        ns = 96 if o["H"] < 128 else 48
+        dep = torch.empty(rays.shape[0], device="cuda")
+        vm.render_depth(k, torch.from_numpy(rays).cuda(), half, ns, dep)
+        do = ev.render_depth(cfg, np.asarray(o["init"], np.float64), o["H"], o["center"],
+                             o["scale"], rays, half, ns)
+        assert np.max(np.abs(dep.cpu().numpy() - do)) < 1e-5 * max(1.0, np.abs(do).max())
+    # n = 0 is a no-op
+    vm.query_occupancy(0, torch.empty(0, 3, device="cuda"), torch.empty(0, device="cuda"))
+
+
+def test_together_equals_separate_bitwise():
+    """The paper's independence: N objects trained together = N separate runs."""
+    sc = vh.mixed_scene(seed=15)
+    R = [o["rays"] for o in sc["objects"]]
+    vm = vh.library_context(sc)
+    K = len(R)
+    lt = torch.empty(K, device="cuda")
+    hist = []
+    for _ in range(3):
+        vm.sample_rays(R)
+        vm.train_step(lt)
+        hist.append(lt.clone())
+    from paper_2302_01838_b300.api import VMap
+    for k in (0, 3, 5):
+        vs1 = VMap(max_objects=2, max_rays_total=4096, max_pool_rays=sc["objects"][k]["pool"].shape[0] + 8,
+                   B=sc["B"], seed=sc["seed"])
+        o = sc["objects"][k]
+        vs1.add_object(o["pool"], hidden=o["H"], center=o["center"], scale=float(o["scale"]),
+                       n_surface=o["n_surface"], n_strat=o["n_strat"], init_params=o["init"], stream_id=k)
+        l1 = torch.empty(1, device="cuda")
+        for s in range(3):
+            vs1.sample_rays([R[k]])
+            vs1.train_step(l1)
+            assert l1.item() == hist[s][k].item()
+        assert torch.equal(vs1.get_object_state(0)[0], vm.get_object_state(k)[0])
+
+
+def test_nonfinite_object_is_frozen_and_others_unaffected():
+    sc = scenes.scene_small(seed=5, n_objects=3, rays=64)
+    ref = vh.library_context(sc)
+    bad_scene = dict(sc)
+    bad_scene["objects"] = [dict(o) for o in sc["objects"]]
+    pool = sc["objects"][1]["pool"].copy()
+    pool[:, 7] = np.nan
+    bad_scene["objects"][1]["pool"] = pool
+    bad = vh.library_context(bad_scene)
+    p_before = bad.get_object_state(1)[0].clone()
+    lr_, lb = torch.empty(3, device="cuda"), torch.empty(3, device="cuda")
+    for _ in range(3):
+        ref.sample_rays([64] * 3)
+        ref.train_step(lr_)
+        bad.sample_rays([64] * 3)
+        bad.train_step(lb)
+    assert bad.sync_status() == [1]
+    assert ref.sync_status() == []
+    p, m, v, st = bad.get_object_state(1)
+    assert st == 0 and torch.equal(p, p_before)
+    for k in (0, 2):
+        assert lr_[k].item() == lb[k].item()
+        assert torch.equal(ref.get_object_state(k)[0], bad.get_object_state(k)[0])
+
+
+def test_checkpoint_resume_is_bitwise():
+    sc = scenes.scene_small(seed=6, n_objects=2, rays=50)
+    a = vh.library_context(sc)
+    for _ in range(4):
+        a.sample_rays([50, 50]); a.train_step()
+    saved = [a.get_object_state(k) for k in range(2)]
+    b = vh.library_context(sc)
+    for k, (p, m, v, st) in enumerate(saved):
+        b.set_object_state(k, p, m, v, st)
+    la, lb = torch.empty(2, device="cuda"), torch.empty(2, device="cuda")
+    for _ in range(3):
+        a.sample_rays([50, 50]); a.train_step(la)
+        b.sample_rays([50, 50]); b.train_step(lb)
+        assert torch.equal(la, lb)
+    for k in range(2):
+        assert torch.equal(a.get_object_state(k)[0], b.get_object_state(k)[0])
+
+
+def test_stop_resume_and_objects_outside_the_batch():
+    sc = scenes.scene_small(seed=8, n_objects=3, rays=40)
+    vm = vh.library_context(sc)
+    cfg = vh.oracle_config(sc)
+    ost = vh.oracle_states(sc)
+    loss = torch.empty(3, device="cuda")
+    vm.set_object_active(1, False)
+    ost[1].active = False
+    for step in range(4):
+        R = [40, 40, 0 if step % 2 else 25]
+        vm.sample_rays(R)
+        vm.train_step(loss)
+        Lo = vs.train_step(cfg, ost, R)
+        Lg = loss.cpu().numpy()
+        assert np.array_equal(np.isnan(Lg), np.isnan(Lo))
+        ok = ~np.isnan(Lo)
+        assert np.all(np.abs(Lg[ok] - Lo[ok]) <= LOSS_RTOL * np.abs(Lo[ok]))
+    assert vm.get_object_state(1)[3] == 0 and vm.get_object_state(2)[3] == 2
+    vm.set_object_active(1, True)
+    vm.sample_rays([0, 40, 0])
+    vm.train_step(loss)
+    assert vm.get_object_state(1)[3] == 1
+
+
+def test_seeded_default_init_matches_oracle():
+    sc = scenes.scene_small(seed=9, n_objects=1, rays=10)
+    from paper_2302_01838_b300.api import VMap
+    vm = VMap(max_objects=4, max_rays_total=64, max_pool_rays=20000, B=sc["B"], seed=77)
+    o = sc["objects"][0]
+    for H, stream in ((16, 3), (32, 5), (128, 9)):
+        k = vm.add_object(o["pool"], hidden=H, center=o["center"], scale=float(o["scale"]), stream_id=stream)
+        p = vm.get_object_state(k)[0].cpu().numpy().astype(np.float64)
+        ref = vs.init_params(77, stream, H)
+        assert np.max(np.abs(p - ref)) < 1e-6
+
+
+def test_errors_are_reported_not_raised_as_faults():
+    from paper_2302_01838_b300.native import VmapError
+    sc = scenes.scene_small(seed=10, n_objects=1, rays=10)
+    vm = vh.library_context(sc, max_rays=32)
+    o = sc["objects"][0]
+    with pytest.raises(VmapError, match="ERR_STATE"):
+        vm.train_step()
+    with pytest.raises(VmapError, match="ERR_CAPACITY"):
+        vm.sample_rays([33])
+    with pytest.raises(VmapError, match="ERR_ARG"):
+        vm.sample_rays([-1])
+    with pytest.raises(VmapError, match="ERR_ARG"):
+        vm.add_object(o["pool"], hidden=48)
+    with pytest.raises(VmapError, match="ERR_ARG"):
+        vm.add_object(o["pool"], hidden=32, n_surface=20, n_strat=20)
+    with pytest.raises(VmapError, match="ERR_ARG"):
+        vm.add_object(o["pool"], hidden=32, scale=0.0)
+    with pytest.raises(VmapError, match="ERR_ARG"):
+        vm.query_occupancy(5, torch.zeros(3, 3, device="cuda"), torch.zeros(3, device="cuda"))
+    with pytest.raises(VmapError, match="ERR_ARG"):
+        vm.render_depth(0, torch.zeros(3, 12, device="cuda"), [1, 1, 1], 500, torch.zeros(3, device="cuda"))
+    # the context still works afterwards
+    vm.sample_rays([10])
+    vm.train_step()
+    assert vm.get_object_state(0)[3] == 1
+
+
+def test_autograd_function_directional_finite_difference():
+    """The hand-written backward behind torch.autograd.Function, checked against
+    central finite differences of the library's own FP32 forward."""
+    from paper_2302_01838_b300.api import VMapLoss
+    sc = scenes.scene_small(seed=16, n_objects=2, rays=120)
+    vm = vh.library_context(sc)
+    vm.sample_rays([120, 120])
+    params = vm.get_params().clone().requires_grad_(True)
+    centers = torch.tensor(np.stack([o["center"] for o in sc["objects"]]), device="cuda",
+                           requires_grad=True)
+    L = VMapLoss.apply(vm, params, centers)
+    w = torch.tensor([1.0, 0.5], device="cuda")
+    (L * w).sum().backward()
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    dp = torch.randn(params.shape, device="cuda", generator=gen)
+    dp /= dp.norm()
+    h = 3e-2
+    with torch.no_grad():
+        f = lambda p, c: (VMapLoss.apply(vm, p, c) * w).sum().item()
+        fd = (f(params + h * dp, centers) - f(params - h * dp, centers)) / (2 * h)
+        an = float((params.grad * dp).sum())
+        assert abs(fd - an) <= 5e-2 * abs(an) + 1e-5, (fd, an)
+        for a in range(3):
+            e = torch.zeros_like(centers); e[0, a] = 1e-2
+            fdc = (f(params, centers + e) - f(params, centers - e)) / 2e-2
+            assert abs(fdc - centers.grad[0, a].item()) <= 3e-2 * abs(fdc) + 2e-3, (a, fdc, centers.grad[0])
+
+
+def test_given_rays_and_host_step_match_oracle():
+    """Caller-chosen rays (device: vmap_sample_rays_given; host, end to end:
+    vmap_train_step_host) train exactly like the oracle on the same rays."""
+    sc = vh.mixed_scene(seed=17)
+    K = len(sc["objects"])
+    R = [o["rays"] for o in sc["objects"]]
+    R[1] = 0
+    cfg = vh.oracle_config(sc)
+    ost = vh.oracle_states(sc)
+    dev = vh.library_context(sc)
+    host = vh.library_context(sc)
+    rng = np.random.default_rng(3)
+    loss_d = torch.empty(K, device="cuda")
+    loss_h = torch.empty(K).pin_memory()
+    for step in range(2):
+        given = [o["pool"][rng.integers(0, o["pool"].shape[0], max(R[k], 1))][:R[k]]
+                 for k, o in enumerate(sc["objects"])]
+        flat = np.concatenate([g for g in given if g.shape[0]]).astype(np.float32)
+        dev.sample_rays_given(torch.from_numpy(flat).cuda(), R)
+        dev.train_step(loss_d)
+        host.train_step_host(torch.from_numpy(flat).pin_memory(), R, loss_h)
+        Lo = vs.train_step(cfg, ost, R, given=given)
+        Ld = loss_d.cpu().numpy()
+        assert np.array_equal(Ld, loss_h.numpy(), equal_nan=True)
+        ok = ~np.isnan(Lo)
+        assert np.array_equal(ok, ~np.isnan(Ld))
+        assert np.all(np.abs(Ld[ok] - Lo[ok]) <= LOSS_RTOL * np.abs(Lo[ok]))
+    for k in range(K):
+        assert torch.equal(dev.get_object_state(k)[0], host.get_object_state(k)[0])

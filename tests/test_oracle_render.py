@@ -147,3 +147,27 @@ def test_param_counts():
         assert np.array_equal(vs.pack(Ws, bs), p)
         assert Ws[0][0, 1] == 1 and bs[0][0] == 93 * H and Ws[1][0, 0] == 94 * H
     assert list(itertools.chain(*vs.layer_shapes(4))) == [4, 93, 4, 4, 4, 4, 4, 4, 4, 4]
+
+
+def test_eval_ray_box_and_render_closed_forms():
+    from oracle import evaluate as ev
+    o = np.array([[-5.0, 0.2, 0.1], [0.0, 3.0, 0.0], [0.0, 0.0, 0.0], [2.0, 2.0, 5.0]])
+    d = np.array([[2.0, 0.0, 0.0], [0.0, -1.0, 0.0], [0.0, 0.0, 1.0], [0.0, 0.0, 1.0]])
+    t_in, t_out = ev.ray_box(o, d, np.array([-1.0, -1, -1]), np.array([1.0, 1, 1]))
+    assert np.allclose([t_in[0], t_out[0]], [2.0, 3.0])      # enters at x=-1, leaves at x=1
+    assert np.allclose([t_in[1], t_out[1]], [2.0, 4.0])
+    assert t_in[2] == 0.0 and t_out[2] == 1.0                # starts inside
+    assert t_out[3] < t_in[3]                                # parallel and outside: miss
+    # an MLP that is fully occupied everywhere renders its first midpoint
+    H = 4
+    p = np.zeros(vs.param_count(H))
+    Ws, bs = vs.unpack(p, H)
+    bs[4][0] = 40.0                                          # sigmoid(40) == 1 in FP64
+    p = vs.pack(Ws, bs)
+    cfg = vs.Config(B=np.zeros((45, 3)))
+    rays = np.zeros((2, 12)); rays[:, 0:3] = o[:2]; rays[:, 3:6] = d[:2]
+    D = ev.render_depth(cfg, p, H, np.zeros(3), 1.0, rays, [1, 1, 1], 10)
+    assert np.allclose(D, [2.0 + 0.05 * 1.0, 2.0 + 0.05 * 2.0], rtol=1e-15)
+    # a miss renders 0
+    rays[1, 0:3] = [5, 5, 5]
+    assert ev.render_depth(cfg, p, H, np.zeros(3), 1.0, rays, [1, 1, 1], 10)[1] == 0.0

@@ -122,3 +122,14 @@ def test_init_params_bounds_and_uniformity():
         assert np.all(np.abs(W) < bound) and np.all(np.abs(b) < bound)
     assert stats.kstest(Ws[0].ravel() * np.sqrt(93) * 0.5 + 0.5, "uniform").pvalue > 1e-3
     assert not np.array_equal(p, vs.init_params(5, 8, H))
+
+
+def test_given_rays_reuse_the_pick_stream_layout():
+    """Depths drawn for caller-given rays equal the depths drawn for the same
+    rays when the generator picked them (word 0 is skipped, not shifted)."""
+    cfg = vs.Config(seed=15)
+    pool = np.zeros((40, 12), np.float32)
+    pool[:, 6] = np.linspace(0.5, 3.0, 40)
+    pick, t = vs.sample_object(cfg, pool, 64, 10, 12, stream=4, step=2)
+    t2 = vs.sample_given(cfg, pool[pick], 10, 12, stream=4, step=2)
+    assert np.array_equal(t, t2)

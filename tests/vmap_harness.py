@@ -1,0 +1,103 @@
+"""Test helpers: put one seeded scene into both the CUDA library and the oracle.
+
+The scene comes from the shared input generator; each side then computes
+on its own (the library never sees oracle values and vice versa)."""
+import numpy as np
+
+from oracle import vmap_step as vs
+from paper_2302_01838_b300 import scenes
+
+
+def oracle_config(scene, **kw):
+    return vs.Config(seed=scene["seed"], B=np.asarray(scene["B"], np.float64), **kw)
+
+
+def oracle_states(scene):
+    out = []
+    for k, o in enumerate(scene["objects"]):
+        out.append(vs.ObjectState(H=o["H"], pool=o["pool"], center=np.asarray(o["center"], np.float64),
+                                  scale=float(o["scale"]), n_surface=o["n_surface"],
+                                  n_strat=o["n_strat"], stream=k, params=o["init"]))
+    return out
+
+
+def library_context(scene, extra_objects=0, max_rays=None, **kw):
+    from paper_2302_01838_b300.api import VMap
+    objs = scene["objects"]
+    pool = sum(o["pool"].shape[0] for o in objs)
+    rays = max_rays or max(64, 2 * sum(o["rays"] for o in objs))
+    vm = VMap(max_objects=len(objs) + extra_objects + 1, max_rays_total=rays,
+              max_pool_rays=2 * pool + 1024, B=scene["B"], seed=scene["seed"], **kw)
+    for k, o in enumerate(objs):
+        vm.add_object(o["pool"], hidden=o["H"], center=o["center"], scale=float(o["scale"]),
+                      n_surface=o["n_surface"], n_strat=o["n_strat"], init_params=o["init"],
+                      stream_id=k)
+    return vm
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+
+
+def layer_errors(gpu_flat, oracle_flat, H):
+    """Relative L2 error of each weight / bias tensor (10 numbers)."""
+    Wg, bg = vs.unpack(np.asarray(gpu_flat, np.float64), H)
+    Wo, bo = vs.unpack(oracle_flat, H)
+    out = []
+    for a, b in zip(Wg + bg, Wo + bo):
+        out.append(rel_l2(a, b))
+    return out
+
+
+def mixed_scene(seed=7):
+    """Objects of every hidden width and samples-per-ray class, with ray counts
+    that span several tiles plus a ragged tail, and one single-ray object."""
+    rng = np.random.default_rng(seed)
+    spec = [(16, (7, 9), 37), (32, (10, 12), 83), (64, (15, 17), 29), (128, (10, 12), 7),
+            (32, (15, 17), 1), (16, (10, 12), 200), (64, (7, 9), 45), (128, (7, 9), 5)]
+    objs = []
+    for H, (ns, nc), R in spec:
+        o = scenes.make_object(rng, (1, 3), 0.1, 0.3, 0.2, H=H, per_view=200)
+        o["init"] = scenes.init_weights(rng, H)
+        o["n_surface"], o["n_strat"] = ns, nc
+        o["rays"] = R
+        objs.append(o)
+    return dict(objects=objs, B=scenes.make_B(seed + 1000), seed=seed)
+
+
+def kink_rows(cfg, ob, R, tau=1e-5):
+    """Hidden units whose ReLU pre-activation comes within tau of 0 on some
+    sample of this step's batch (oracle values). Their ReLU' may differ
+    between FP32 and FP64, which changes that unit's whole weight row; the
+    weight comparison leaves those rows out. Returns {layer: set(rows)}."""
+    pick, t = vs.sample_object(cfg, ob.pool, R, ob.n_surface, ob.n_strat, ob.stream, ob.step)
+    Ws, bs = vs.unpack(ob.params, ob.H)
+    xt = vs.points(ob.pool[pick].astype(np.float64), t, ob.center, ob.scale).reshape(-1, 3)
+    a = vs.encode(xt, cfg.B)
+    out = {}
+    for l in range(4):
+        z = a @ Ws[l].T + bs[l]
+        out[l] = set(np.nonzero(np.any(np.abs(z) < tau, axis=0))[0].tolist())
+        a = np.maximum(z, 0.0)
+    return out
+
+
+def layer_errors_masked(gpu_flat, oracle_flat, H, skip):
+    """layer_errors with the rows in skip[l] (hidden layers l = 0..3) left out
+    of W_l and b_l."""
+    Wg, bg = vs.unpack(np.asarray(gpu_flat, np.float64), H)
+    Wo, bo = vs.unpack(oracle_flat, H)
+    out = []
+    for l in range(5):
+        keep = np.ones(Wo[l].shape[0], bool)
+        if l < 4 and skip.get(l):
+            keep[list(skip[l])] = False
+        out.append(rel_l2(Wg[l][keep], Wo[l][keep]))
+    for l in range(5):
+        keep = np.ones(bo[l].shape[0], bool)
+        if l < 4 and skip.get(l):
+            keep[list(skip[l])] = False
+        out.append(rel_l2(bg[l][keep], bo[l][keep]))
+    return out
