@@ -225,6 +225,28 @@ vmap_status vmap_profile_reset(vmap_ctx* ctx);
 vmap_status vmap_profile_read(vmap_ctx* ctx, int slot, const char** name, long long* launches,
                               double* total_ms);
 
+/* Replay the step as CUDA graphs (on = 1) or launch kernel by kernel (0, the
+ * default). The batch layout lives in device memory, so a captured step stays
+ * valid while objects are admitted, stopped or resized; adding the first
+ * object of a new hidden width recaptures once. Graphs are captured lazily at
+ * the next vmap_sample_rays / vmap_train_step. */
+vmap_status vmap_set_graph(vmap_ctx* ctx, int on);
+
+/* Launch shape per hidden-width class (index 0..3 = H 16, 32, 64, 128):
+ * rays per tile (1..32, further capped so a tile holds at most the class's
+ * sample budget) and the persistent grid multiplier (1..2; the grid is
+ * SMs x CTAs per SM x multiplier). HOST arrays [4], either may be NULL. */
+vmap_status vmap_get_launch(vmap_ctx* ctx, int* rays_per_tile, int* grid_mult);
+vmap_status vmap_set_launch(vmap_ctx* ctx, const int* rays_per_tile, const int* grid_mult);
+
+/* Autotuner: for every width class present, time the training tile kernel on
+ * the batch rays_per_object (HOST [n_objects]) over `reps` launches for each
+ * candidate (rays per tile, grid multiplier) and keep the fastest. Changes no
+ * object state; the next step must draw a fresh batch. best_ms: HOST [4] or
+ * NULL, the best per-launch milliseconds per class (0 for absent classes).
+ * Synchronises. */
+vmap_status vmap_autotune(vmap_ctx* ctx, const int* rays_per_object, int reps, float* best_ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -136,6 +136,25 @@ class VMap:
             slot += 1
         return out
 
+    def set_graph(self, on=True):
+        self._check(self.lib.vmap_set_graph(self.h, int(bool(on))))
+
+    def get_launch(self):
+        rt, gm = (ctypes.c_int * 4)(), (ctypes.c_int * 4)()
+        self._check(self.lib.vmap_get_launch(self.h, rt, gm))
+        return list(rt), list(gm)
+
+    def set_launch(self, rays_per_tile=None, grid_mult=None):
+        rt = (ctypes.c_int * 4)(*rays_per_tile) if rays_per_tile is not None else None
+        gm = (ctypes.c_int * 4)(*grid_mult) if grid_mult is not None else None
+        self._check(self.lib.vmap_set_launch(self.h, rt, gm))
+
+    def autotune(self, rays_per_object, reps=3):
+        arr = (ctypes.c_int * len(rays_per_object))(*[int(r) for r in rays_per_object])
+        best = (ctypes.c_float * 4)()
+        self._check(self.lib.vmap_autotune(self.h, arr, int(reps), best))
+        return list(best)
+
     def train_step(self, out_loss=None):
         self._check(self.lib.vmap_train_step(self.h, _ptr(out_loss)))
         return out_loss

@@ -1,5 +1,8 @@
-// C ABI of the vMAP training library: context, object table, batch
-// construction and kernel launches. See include/vmap.h for the contract.
+// C ABI of the vMAP training library: context, object table, launches,
+// CUDA-graph replay, profiling and the launch autotuner. The batch layout is
+// built on the device (vmap_build.cuh), so one step is a fixed sequence of
+// launches that a CUDA graph can replay while objects come and go.
+// See include/vmap.h for the contract.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -11,6 +14,7 @@
 #include <vector>
 
 #include "../../include/vmap.h"
+#include "vmap_build.cuh"
 #include "vmap_common.cuh"
 #include "vmap_optim.cuh"
 #include "vmap_sample.cuh"
@@ -18,24 +22,57 @@
 
 using namespace vmapk;
 
+namespace {
+
+enum ProfSlot { PS_BUILD = 0, PS_SAMPLE = 1, PS_TILE = 2 /* + class */, PS_REDUCE = 6, PS_FINISH = 7, PS_N = 8 };
+const char* kProfNames[PS_N] = {"k_build",         "k_sample",         "k_tile_fp32<16>", "k_tile_fp32<32>",
+                                "k_tile_fp32<64>", "k_tile_fp32<128>", "k_reduce",        "k_finish"};
+
+int mmax_of(int c) {
+    switch (c) {
+        case 0: return TileCfg<16>::MMAX;
+        case 1: return TileCfg<32>::MMAX;
+        case 2: return TileCfg<64>::MMAX;
+        default: return TileCfg<128>::MMAX;
+    }
+}
+int ctas_of(int c) {
+    switch (c) {
+        case 0: return TileCfg<16>::CTAS;
+        case 1: return TileCfg<32>::CTAS;
+        case 2: return TileCfg<64>::CTAS;
+        default: return TileCfg<128>::CTAS;
+    }
+}
+bool valid_hidden(int H) { return H == 16 || H == 32 || H == 64 || H == 128; }
+constexpr int GMULT_MAX = 2;   // persistent grid: n_sm * CTAS * gmult CTAs per class
+
+struct ProfPair {
+    int slot;
+    cudaEvent_t a, b;
+};
+
+}  // namespace
+
 struct vmap_ctx {
     vmap_config cfg{};
     cudaStream_t stream = nullptr;
     std::string err;
     StepParams sp{};
-    int device = 0;
+    int device = 0, n_sm = 148;
 
-    // object table
+    // objects: static table (host + device mirror), per-batch table (device)
     std::vector<ObjDev> objs;
     ObjDev* objs_d = nullptr;
+    ObjBatch* ob_d = nullptr;
+    int* n_obj_d = nullptr;
     int* steps_d = nullptr;
     int* status_d = nullptr;
+    int* req_d = nullptr;
+    std::vector<int> req_h;
 
     // arenas
-    float* params_d = nullptr;
-    float* wt_d = nullptr;
-    float* m_d = nullptr;
-    float* v_d = nullptr;
+    float *params_d = nullptr, *wt_d = nullptr, *m_d = nullptr, *v_d = nullptr;
     long long param_used = 0, param_cap = 0, wt_used = 0, wt_cap = 0;
     float* pool_d = nullptr;
     long long pool_used = 0, pool_cap = 0;
@@ -43,91 +80,43 @@ struct vmap_ctx {
     // batch
     int* pick_d = nullptr;
     float* t_d = nullptr;
-    int* bobj_d = nullptr;
-    int* bray_d = nullptr;
+    int *bobj_d = nullptr, *bray_d = nullptr;
     TileDev* tiles_d = nullptr;
-    float* part_d = nullptr;
-    long long part_cap = 0;
+    int* flags_d = nullptr;
     int tile_cap = 0;
+    float* part_d = nullptr;
+    long long part_base[NCLASS] = {0, 0, 0, 0};
+    int2* items_d = nullptr;
+    int* counts_d = nullptr;
+    float* given_d = nullptr;
+    float* loss_d = nullptr;
     bool batch_ready = false;
-    int nb = 0;
+    bool batch_given = false;
     int total_rays = 0;
     long long total_samples = 0;
-    std::vector<int> bobj;
-    int cls_begin[4] = {0, 0, 0, 0}, cls_count[4] = {0, 0, 0, 0};
-    int n_tiles = 0;
-    int max_chunks = 1;
-    bool batch_given = false;      // the batch's rays came from the caller (staging buffer)
-    float* given_d = nullptr;      // [max_rays_total][12] staging for caller-given rays
-    float* loss_d = nullptr;       // [max_objects] loss scratch of vmap_train_step_host
 
-    // profiling: CUDA events around every kernel launch, on the context stream
+    // launch configuration (autotuned)
+    int rt[NCLASS] = {RTMAX, RTMAX, RTMAX, RTMAX};
+    int gmult[NCLASS] = {1, 1, 1, 1};
+
+    // CUDA graphs (captured on a private stream, replayed on the context stream)
+    bool graph_on = false;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t g_sample[2] = {nullptr, nullptr};   // [given]
+    cudaGraphExec_t g_train = nullptr;
+    int g_classes = -1;                 // class mask the train graph was captured for
+    std::vector<ProfPair> g_prof[3];    // profile pairs recorded inside each graph
+
+    // profiling
     bool prof_on = false;
     std::vector<cudaEvent_t> ev_free;
-    struct Pending { int slot; cudaEvent_t a, b; };
-    std::vector<Pending> pending;
-    double prof_ms[16] = {0};
-    long long prof_n[16] = {0};
+    std::vector<ProfPair> pending;
+    std::vector<ProfPair>* capture_prof = nullptr;   // set while capturing
+    double prof_ms[PS_N] = {0};
+    long long prof_n[PS_N] = {0};
 };
 
 namespace {
-
-const int kHidden[4] = {16, 32, 64, 128};
-
-enum ProfSlot { PS_SAMPLE = 0, PS_TILE = 1 /* + hidden class */, PS_REDUCE = 5, PS_FINISH = 6, PS_N = 7 };
-const char* kProfNames[PS_N] = {"k_sample", "k_tile_fp32<16>", "k_tile_fp32<32>", "k_tile_fp32<64>",
-                                "k_tile_fp32<128>", "k_reduce", "k_finish"};
-
-// returns a pending index (or -1) after recording the start event
-int prof_begin(vmap_ctx* ctx, int slot) {
-    if (!ctx->prof_on) return -1;
-    cudaEvent_t ev[2];
-    for (int i = 0; i < 2; ++i) {
-        if (ctx->ev_free.empty()) {
-            if (cudaEventCreate(&ev[i]) != cudaSuccess) return -1;
-        } else {
-            ev[i] = ctx->ev_free.back();
-            ctx->ev_free.pop_back();
-        }
-    }
-    cudaEventRecord(ev[0], ctx->stream);
-    ctx->pending.push_back({slot, ev[0], ev[1]});
-    return (int)ctx->pending.size() - 1;
-}
-
-void prof_end(vmap_ctx* ctx, int idx) {
-    if (idx >= 0) cudaEventRecord(ctx->pending[idx].b, ctx->stream);
-}
-
-void prof_flush(vmap_ctx* ctx) {
-    if (ctx->pending.empty()) return;
-    cudaStreamSynchronize(ctx->stream);
-    for (auto& p : ctx->pending) {
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
-            ctx->prof_ms[p.slot] += ms;
-            ctx->prof_n[p.slot] += 1;
-        }
-        ctx->ev_free.push_back(p.a);
-        ctx->ev_free.push_back(p.b);
-    }
-    ctx->pending.clear();
-}
-
-int hidden_class(int H) {
-    for (int c = 0; c < 4; ++c)
-        if (kHidden[c] == H) return c;
-    return -1;
-}
-
-int mmax_of(int H) {
-    switch (H) {
-        case 16: return TileCfg<16>::MMAX;
-        case 32: return TileCfg<32>::MMAX;
-        case 64: return TileCfg<64>::MMAX;
-        default: return TileCfg<128>::MMAX;
-    }
-}
 
 vmap_status fail(vmap_ctx* c, vmap_status s, const char* fmt, ...) {
     char buf[512];
@@ -154,65 +143,108 @@ vmap_status fail(vmap_ctx* c, vmap_status s, const char* fmt, ...) {
                         cudaGetErrorString(e_));                                               \
     } while (0)
 
-template <int H>
-size_t tile_smem() { return TileSmem<H>::BYTES; }
-
-size_t tile_smem_of(int H) {
-    switch (H) {
-        case 16: return tile_smem<16>();
-        case 32: return tile_smem<32>();
-        case 64: return tile_smem<64>();
-        default: return tile_smem<128>();
+// ---- profiling: event pairs around launches ---------------------------------
+cudaEvent_t take_event(vmap_ctx* ctx) {
+    cudaEvent_t e = nullptr;
+    if (ctx->ev_free.empty()) {
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    } else {
+        e = ctx->ev_free.back();
+        ctx->ev_free.pop_back();
     }
+    return e;
 }
 
-template <int H, int MODE>
-cudaError_t launch_tile(int n_tiles, cudaStream_t st, const StepParams& sp, const TileArgs& ta) {
-    static bool attr_set = false;
-    const size_t smem = TileSmem<H>::BYTES;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_tile_fp32<H, MODE>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
-    if (n_tiles <= 0) return cudaSuccess;
-    k_tile_fp32<H, MODE><<<n_tiles, NTHREADS, smem, st>>>(sp, ta);
-    return cudaGetLastError();
+int prof_begin(vmap_ctx* ctx, int slot) {
+    if (!ctx->prof_on) return -1;
+    ProfPair p{slot, take_event(ctx), take_event(ctx)};
+    if (!p.a || !p.b) return -1;
+    cudaEventRecord(p.a, ctx->stream);
+    std::vector<ProfPair>& dst = ctx->capture_prof ? *ctx->capture_prof : ctx->pending;
+    dst.push_back(p);
+    return (int)dst.size() - 1;
 }
 
-template <int MODE>
-cudaError_t launch_tile_h(int H, int n_tiles, cudaStream_t st, const StepParams& sp,
-                          const TileArgs& ta) {
-    switch (H) {
-        case 16: return launch_tile<16, MODE>(n_tiles, st, sp, ta);
-        case 32: return launch_tile<32, MODE>(n_tiles, st, sp, ta);
-        case 64: return launch_tile<64, MODE>(n_tiles, st, sp, ta);
-        default: return launch_tile<128, MODE>(n_tiles, st, sp, ta);
+void prof_end(vmap_ctx* ctx, int idx) {
+    if (idx < 0) return;
+    std::vector<ProfPair>& dst = ctx->capture_prof ? *ctx->capture_prof : ctx->pending;
+    cudaEventRecord(dst[idx].b, ctx->stream);
+}
+
+bool graph_owned(vmap_ctx* ctx, cudaEvent_t e) {
+    for (auto& gv : ctx->g_prof)
+        for (auto& q : gv)
+            if (q.a == e || q.b == e) return true;
+    return false;
+}
+
+// synchronise and accumulate every pending pair; pairs owned by a graph are
+// read but kept (the graph records them again at its next replay)
+void prof_flush(vmap_ctx* ctx) {
+    if (ctx->pending.empty()) return;
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& p : ctx->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            ctx->prof_ms[p.slot] += ms;
+            ctx->prof_n[p.slot] += 1;
+        }
+        if (!graph_owned(ctx, p.a)) {
+            ctx->ev_free.push_back(p.a);
+            ctx->ev_free.push_back(p.b);
+        }
     }
+    ctx->pending.clear();
+}
+
+void release_graph_prof(vmap_ctx* ctx, std::vector<ProfPair>& gv) {
+    for (auto& p : gv) {
+        ctx->ev_free.push_back(p.a);
+        ctx->ev_free.push_back(p.b);
+    }
+    gv.clear();
+}
+
+void drop_graphs(vmap_ctx* ctx) {
+    prof_flush(ctx);
+    for (auto& g : ctx->g_sample)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    if (ctx->g_train) {
+        cudaGraphExecDestroy(ctx->g_train);
+        ctx->g_train = nullptr;
+    }
+    for (auto& gv : ctx->g_prof) release_graph_prof(ctx, gv);
+    ctx->g_classes = -1;
 }
 
 vmap_status check_obj(vmap_ctx* ctx, int obj) {
     if (!ctx) return VMAP_ERR_ARG;
     if (obj < 0 || obj >= (int)ctx->objs.size())
-        return fail(ctx, VMAP_ERR_ARG, "object index %d out of range [0, %d)", obj,
-                    (int)ctx->objs.size());
+        return fail(ctx, VMAP_ERR_ARG, "object index %d out of range [0, %d)", obj, (int)ctx->objs.size());
     return VMAP_OK;
 }
 
-vmap_status upload_objs(vmap_ctx* ctx) {
-    if (ctx->objs.empty()) return VMAP_OK;
-    CU(cudaMemcpyAsync(ctx->objs_d, ctx->objs.data(), sizeof(ObjDev) * ctx->objs.size(),
-                       cudaMemcpyHostToDevice, ctx->stream));
-    // the host vector may change before the copy runs: make the copy complete
-    CU(cudaStreamSynchronize(ctx->stream));
+vmap_status upload_obj(vmap_ctx* ctx, int k) {
+    // pageable source: the bytes are staged before the call returns
+    CU(cudaMemcpyAsync(ctx->objs_d + k, &ctx->objs[k], sizeof(ObjDev), cudaMemcpyHostToDevice, ctx->stream));
     return VMAP_OK;
 }
+
+int class_mask(vmap_ctx* ctx) {
+    int m = 0;
+    for (const ObjDev& o : ctx->objs) m |= 1 << class_of(o.hidden);
+    return m;
+}
+
+int grid_of(vmap_ctx* ctx, int c) { return ctx->n_sm * ctas_of(c) * ctx->gmult[c]; }
 
 TileArgs base_args(vmap_ctx* ctx) {
     TileArgs ta{};
     ta.objs = ctx->objs_d;
-    ta.tiles = ctx->tiles_d;
+    ta.obs = ctx->ob_d;
     ta.pool = ctx->batch_given ? ctx->given_d : ctx->pool_d;
     ta.pick = ctx->pick_d;
     ta.tbuf = ctx->t_d;
@@ -222,33 +254,182 @@ TileArgs base_args(vmap_ctx* ctx) {
     return ta;
 }
 
+template <int H, int MODE>
+cudaError_t launch_tile(int grid, cudaStream_t st, const StepParams& sp, const TileArgs& ta) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_tile_fp32<H, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)TileSmem<H>::BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    if (grid <= 0) return cudaSuccess;
+    k_tile_fp32<H, MODE><<<grid, NTHREADS, TileSmem<H>::BYTES, st>>>(sp, ta);
+    return cudaGetLastError();
+}
+
 template <int MODE>
-vmap_status run_tiles(vmap_ctx* ctx) {
+cudaError_t launch_tile_c(int c, int grid, cudaStream_t st, const StepParams& sp, const TileArgs& ta) {
+    switch (c) {
+        case 0: return launch_tile<16, MODE>(grid, st, sp, ta);
+        case 1: return launch_tile<32, MODE>(grid, st, sp, ta);
+        case 2: return launch_tile<64, MODE>(grid, st, sp, ta);
+        default: return launch_tile<128, MODE>(grid, st, sp, ta);
+    }
+}
+
+// ---- the step's launches ------------------------------------------------------
+vmap_status launch_build_sample(vmap_ctx* ctx, int given) {
+    BuildArgs a{};
+    a.objs = ctx->objs_d;
+    a.ob = ctx->ob_d;
+    a.n_obj = ctx->n_obj_d;
+    a.req = ctx->req_d;
+    a.status = ctx->status_d;
+    a.given = given;
+    for (int c = 0; c < NCLASS; ++c) {
+        a.rt[c] = ctx->rt[c];
+        a.mmax[c] = mmax_of(c);
+        a.grid[c] = grid_of(ctx, c);
+        a.part_base[c] = ctx->part_base[c];
+    }
+    a.rtmax = RTMAX;
+    a.tiles = ctx->tiles_d;
+    a.flags = ctx->flags_d;
+    a.tile_cap = ctx->tile_cap;
+    a.bobj = ctx->bobj_d;
+    a.bray = ctx->bray_d;
+    a.items = ctx->items_d;
+    a.counts = ctx->counts_d;
+    int pi = prof_begin(ctx, PS_BUILD);
+    k_build<<<1, BUILD_THREADS, 0, ctx->stream>>>(a);
+    prof_end(ctx, pi);
+    CHECK_LAUNCH("k_build");
+    const int blocks = (ctx->cfg.max_rays_total + 127) / 128;
+    pi = prof_begin(ctx, PS_SAMPLE);
+    k_sample<<<blocks, 128, 0, ctx->stream>>>(ctx->sp, ctx->objs_d, ctx->ob_d, ctx->bobj_d, ctx->bray_d,
+                                             ctx->counts_d, given ? ctx->given_d : ctx->pool_d, given,
+                                             ctx->steps_d, ctx->pick_d, ctx->t_d);
+    prof_end(ctx, pi);
+    CHECK_LAUNCH("k_sample");
+    return VMAP_OK;
+}
+
+template <int MODE>
+vmap_status launch_tiles(vmap_ctx* ctx, int mask) {
     TileArgs ta = base_args(ctx);
-    for (int c = 0; c < 4; ++c) {
-        if (ctx->cls_count[c] == 0) continue;
-        ta.tile_begin = ctx->cls_begin[c];
+    for (int c = 0; c < NCLASS; ++c) {
+        if (!(mask & (1 << c))) continue;
+        ta.tiles = ctx->tiles_d + (long long)c * ctx->tile_cap;
+        ta.n_tiles = ctx->counts_d + BC_TILES + c;
         const int pi = MODE == MODE_TRAIN ? prof_begin(ctx, PS_TILE + c) : -1;
-        cudaError_t e = launch_tile_h<MODE>(kHidden[c], ctx->cls_count[c], ctx->stream, ctx->sp, ta);
+        cudaError_t e = launch_tile_c<MODE>(c, grid_of(ctx, c), ctx->stream, ctx->sp, ta);
         prof_end(ctx, pi);
         if (e != cudaSuccess)
-            return fail(ctx, VMAP_ERR_CUDA, "tile kernel (H=%d) failed: %s", kHidden[c],
-                        cudaGetErrorString(e));
+            return fail(ctx, VMAP_ERR_CUDA, "tile kernel (H=%d) failed: %s", hidden_of(c), cudaGetErrorString(e));
     }
     return VMAP_OK;
 }
 
-vmap_status run_reduce(vmap_ctx* ctx, int mode, const float* grad_loss, float* grad_out,
-                       float* loss_out, float* dcenter_out) {
-    if (ctx->nb == 0) return VMAP_OK;
-    dim3 grid(ctx->max_chunks, ctx->nb);
+vmap_status launch_reduce(vmap_ctx* ctx, int mode, const float* grad_loss, float* grad_out, float* loss_out,
+                          float* dcenter_out) {
     const int pi = prof_begin(ctx, PS_REDUCE);
-    k_reduce<<<grid, 256, 0, ctx->stream>>>(ctx->sp, ctx->objs_d, ctx->bobj_d, ctx->part_d,
-                                            ctx->params_d, ctx->wt_d, ctx->m_d, ctx->v_d,
-                                            ctx->steps_d, ctx->status_d, mode, grad_loss, grad_out,
-                                            loss_out, dcenter_out);
+    k_reduce<<<ctx->n_sm * 4, 256, 0, ctx->stream>>>(ctx->sp, ctx->objs_d, ctx->ob_d, ctx->bobj_d, ctx->items_d,
+                                                     ctx->counts_d, ctx->part_d, ctx->params_d, ctx->wt_d,
+                                                     ctx->m_d, ctx->v_d, ctx->steps_d, ctx->status_d, mode,
+                                                     grad_loss, grad_out, loss_out, dcenter_out);
     prof_end(ctx, pi);
     CHECK_LAUNCH("k_reduce");
+    return VMAP_OK;
+}
+
+vmap_status launch_train(vmap_ctx* ctx, int mask) {
+    CU(cudaMemsetAsync(ctx->loss_d, 0xFF, sizeof(float) * ctx->cfg.max_objects, ctx->stream));
+    if (vmap_status s = launch_tiles<MODE_TRAIN>(ctx, mask)) return s;
+    if (vmap_status s = launch_reduce(ctx, RED_ADAM, nullptr, nullptr, ctx->loss_d, nullptr)) return s;
+    const int pi = prof_begin(ctx, PS_FINISH);
+    k_finish<<<4, 256, 0, ctx->stream>>>(ctx->bobj_d, ctx->counts_d, ctx->steps_d, ctx->status_d);
+    prof_end(ctx, pi);
+    CHECK_LAUNCH("k_finish");
+    return VMAP_OK;
+}
+
+// capture fn() into an executable graph on the context stream
+template <typename F>
+vmap_status capture(vmap_ctx* ctx, cudaGraphExec_t* out, std::vector<ProfPair>* prof, F fn) {
+    cudaGraph_t g = nullptr;
+    if (!ctx->cap_stream) CU(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    // the context stream may be the legacy default stream, which cannot be captured
+    CU(cudaStreamSynchronize(ctx->stream));
+    CU(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaStream_t user = ctx->stream;
+    ctx->stream = ctx->cap_stream;
+    ctx->capture_prof = prof;
+    vmap_status s = fn();
+    ctx->capture_prof = nullptr;
+    ctx->stream = user;
+    cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
+    if (s) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+    }
+    if (e != cudaSuccess) return fail(ctx, VMAP_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(ctx, VMAP_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+    return VMAP_OK;
+}
+
+vmap_status replay(vmap_ctx* ctx, cudaGraphExec_t g, std::vector<ProfPair>& prof) {
+    if (ctx->prof_on) prof_flush(ctx);   // the replay records the graph's events again
+    CU(cudaGraphLaunch(g, ctx->stream));
+    if (ctx->prof_on)
+        for (auto& p : prof) ctx->pending.push_back(p);
+    return VMAP_OK;
+}
+
+// Build the batch: rays_per_object[k] rays of every active object. With
+// given == NULL the rays are picked from the objects' pools; otherwise given
+// holds sum_k R_k records (object-major, active objects with R_k > 0, in
+// index order) in memory of the kind `kind`, which are staged on the device.
+vmap_status sample_impl(vmap_ctx* ctx, const int* rays_per_object, const float* given, cudaMemcpyKind kind) {
+    if (!ctx || !rays_per_object) return fail(ctx, VMAP_ERR_ARG, "null argument");
+    const int K = (int)ctx->objs.size();
+    long long rays = 0, samples = 0;
+    long long tiles[NCLASS] = {0, 0, 0, 0};
+    for (int k = 0; k < K; ++k) {
+        if (rays_per_object[k] < 0) return fail(ctx, VMAP_ERR_ARG, "negative ray count for object %d", k);
+        const ObjDev& ob = ctx->objs[k];
+        const int R = ob.active ? rays_per_object[k] : 0;
+        if (R == 0) continue;
+        const int c = class_of(ob.hidden);
+        const int rt = std::max(1, std::min(std::min(ctx->rt[c], RTMAX), mmax_of(c) / ob.S));
+        rays += R;
+        samples += (long long)R * ob.S;
+        tiles[c] += (R + rt - 1) / rt;
+    }
+    if (rays > ctx->cfg.max_rays_total)
+        return fail(ctx, VMAP_ERR_CAPACITY, "%lld rays exceed max_rays_total %d", rays, ctx->cfg.max_rays_total);
+    for (int c = 0; c < NCLASS; ++c)
+        if (tiles[c] > ctx->tile_cap) return fail(ctx, VMAP_ERR_CAPACITY, "too many tiles");
+    ctx->req_h.assign(rays_per_object, rays_per_object + K);
+    if (K) CU(cudaMemcpyAsync(ctx->req_d, ctx->req_h.data(), sizeof(int) * K, cudaMemcpyHostToDevice, ctx->stream));
+    ctx->batch_given = given != nullptr;
+    if (given && rays) CU(cudaMemcpyAsync(ctx->given_d, given, sizeof(float) * REC * rays, kind, ctx->stream));
+    const int gi = given ? 1 : 0;
+    if (ctx->graph_on) {
+        if (!ctx->g_sample[gi]) {
+            vmap_status s = capture(ctx, &ctx->g_sample[gi], &ctx->g_prof[gi],
+                                    [&] { return launch_build_sample(ctx, gi); });
+            if (s) return s;
+        }
+        if (vmap_status s = replay(ctx, ctx->g_sample[gi], ctx->g_prof[gi])) return s;
+    } else {
+        if (vmap_status s = launch_build_sample(ctx, gi)) return s;
+    }
+    ctx->total_rays = (int)rays;          // upper bounds until read back (frozen objects drop out)
+    ctx->total_samples = samples;
+    ctx->batch_ready = true;
     return VMAP_OK;
 }
 
@@ -303,22 +484,29 @@ vmap_status vmap_init_objects(vmap_ctx** out, const vmap_config* cfg, void* cuda
     ctx->sp.key0 = (uint32_t)(cfg->seed & 0xFFFFFFFFull);
     ctx->sp.key1 = (uint32_t)(cfg->seed >> 32);
 
-    auto bail = [&](vmap_status s) { vmap_destroy(ctx); return s; };
-    cudaError_t e;
+    auto bail = [&](vmap_status s) {
+        vmap_destroy(ctx);
+        return s;
+    };
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (e != cudaSuccess) return bail(VMAP_ERR_CUDA);
 #define ALLOC(ptr, bytes)                                                                      \
     do {                                                                                       \
         e = cudaMalloc((void**)&(ptr), (bytes));                                               \
         if (e != cudaSuccess) return bail(VMAP_ERR_CUDA);                                      \
     } while (0)
-    cudaGetDevice(&ctx->device);
     const int K = cfg->max_objects;
     ctx->param_cap = cfg->max_param_floats > 0 ? cfg->max_param_floats : (long long)K * param_count(128);
     ctx->param_cap = (ctx->param_cap + 63) & ~63LL;
     ctx->wt_cap = ctx->param_cap + 64LL * K;   // wt_count(H) <= param_count(H) per object + alignment
     ctx->pool_cap = cfg->max_pool_rays;
     ALLOC(ctx->objs_d, sizeof(ObjDev) * K);
+    ALLOC(ctx->ob_d, sizeof(ObjBatch) * K);
+    ALLOC(ctx->n_obj_d, sizeof(int));
     ALLOC(ctx->steps_d, sizeof(int) * K);
     ALLOC(ctx->status_d, sizeof(int) * K);
+    ALLOC(ctx->req_d, sizeof(int) * K);
     ALLOC(ctx->params_d, sizeof(float) * ctx->param_cap);
     ALLOC(ctx->wt_d, sizeof(float) * ctx->wt_cap);
     ALLOC(ctx->m_d, sizeof(float) * ctx->param_cap);
@@ -327,15 +515,28 @@ vmap_status vmap_init_objects(vmap_ctx** out, const vmap_config* cfg, void* cuda
     ALLOC(ctx->pick_d, sizeof(int) * cfg->max_rays_total);
     ALLOC(ctx->t_d, sizeof(float) * (size_t)cfg->max_rays_total * SMAX);
     ALLOC(ctx->bobj_d, sizeof(int) * K);
-    ALLOC(ctx->bray_d, sizeof(int) * (K + 1));
-    // tiles: every object contributes at most ceil(R_k / rt_k) <= R_k tiles
-    ctx->tile_cap = cfg->max_rays_total + K;
-    ALLOC(ctx->tiles_d, sizeof(TileDev) * ctx->tile_cap);
+    ALLOC(ctx->bray_d, sizeof(int) * K);
+    ctx->tile_cap = cfg->max_rays_total + 16;
+    ALLOC(ctx->tiles_d, sizeof(TileDev) * (size_t)ctx->tile_cap * NCLASS);
+    ALLOC(ctx->flags_d, sizeof(int) * (size_t)ctx->tile_cap * NCLASS);
+    // run slots per class: at most one per CTA plus one per object
+    long long part = 0;
+    for (int c = 0; c < NCLASS; ++c) {
+        ctx->part_base[c] = part;
+        const long long slots = (long long)ctx->n_sm * ctas_of(c) * GMULT_MAX + K;
+        part += slots * (param_count(hidden_of(c)) + NEXTRA);
+    }
+    ALLOC(ctx->part_d, sizeof(float) * part);
+    ALLOC(ctx->items_d, sizeof(int2) * (size_t)K * ((param_count(128) + REDUCE_CHUNK - 1) / REDUCE_CHUNK));
+    ALLOC(ctx->counts_d, sizeof(int) * BC_N);
     ALLOC(ctx->given_d, sizeof(float) * REC * (size_t)cfg->max_rays_total);
     ALLOC(ctx->loss_d, sizeof(float) * K);
 #undef ALLOC
     e = cudaMemsetAsync(ctx->steps_d, 0, sizeof(int) * K, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->status_d, 0, sizeof(int) * K, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->req_d, 0, sizeof(int) * K, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->n_obj_d, 0, sizeof(int), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->counts_d, 0, sizeof(int) * BC_N, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return bail(VMAP_ERR_CUDA);
     *out = ctx;
@@ -346,9 +547,11 @@ vmap_status vmap_destroy(vmap_ctx* ctx) {
     if (!ctx) return VMAP_OK;
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     else cudaDeviceSynchronize();
-    void* ptrs[] = {ctx->objs_d, ctx->steps_d, ctx->status_d, ctx->params_d, ctx->wt_d, ctx->m_d,
-                    ctx->v_d, ctx->pool_d, ctx->pick_d, ctx->t_d, ctx->bobj_d, ctx->bray_d,
-                    ctx->tiles_d, ctx->part_d, ctx->given_d, ctx->loss_d};
+    drop_graphs(ctx);
+    void* ptrs[] = {ctx->objs_d,   ctx->ob_d,     ctx->n_obj_d,  ctx->steps_d, ctx->status_d, ctx->req_d,
+                    ctx->params_d, ctx->wt_d,     ctx->m_d,      ctx->v_d,     ctx->pool_d,   ctx->pick_d,
+                    ctx->t_d,      ctx->bobj_d,   ctx->bray_d,   ctx->tiles_d, ctx->flags_d,  ctx->part_d,
+                    ctx->items_d,  ctx->counts_d, ctx->given_d,  ctx->loss_d};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& p : ctx->pending) {
@@ -356,18 +559,18 @@ vmap_status vmap_destroy(vmap_ctx* ctx) {
         cudaEventDestroy(p.b);
     }
     for (cudaEvent_t e : ctx->ev_free) cudaEventDestroy(e);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     delete ctx;
     return VMAP_OK;
 }
 
-vmap_status vmap_add_object(vmap_ctx* ctx, const vmap_object_desc* d, const float* init_params,
-                            int* out_id) {
+vmap_status vmap_add_object(vmap_ctx* ctx, const vmap_object_desc* d, const float* init_params, int* out_id) {
     if (!ctx || !d || !out_id) return fail(ctx, VMAP_ERR_ARG, "null argument");
-    if (hidden_class(d->hidden) < 0) return fail(ctx, VMAP_ERR_ARG, "hidden %d not in {16,32,64,128}", d->hidden);
+    if (!valid_hidden(d->hidden)) return fail(ctx, VMAP_ERR_ARG, "hidden %d not in {16,32,64,128}", d->hidden);
     const int S = d->n_surface + d->n_strat;
     if (d->n_surface < 0 || d->n_strat < 0 || S < 1 || S > SMAX)
         return fail(ctx, VMAP_ERR_ARG, "samples per ray %d+%d not in [1, %d]", d->n_surface, d->n_strat, SMAX);
-    if (S > mmax_of(d->hidden))
+    if (S > mmax_of(class_of(d->hidden)))
         return fail(ctx, VMAP_ERR_ARG, "samples per ray %d exceed the tile of hidden %d", S, d->hidden);
     if (!(d->scale > 0.f) || !std::isfinite(d->scale)) return fail(ctx, VMAP_ERR_ARG, "scale must be > 0");
     if (!d->rays || d->n_rays < 1) return fail(ctx, VMAP_ERR_ARG, "empty ray pool");
@@ -379,8 +582,8 @@ vmap_status vmap_add_object(vmap_ctx* ctx, const vmap_object_desc* d, const floa
     if (poff + P > ctx->param_cap || woff + wt_count(d->hidden) > ctx->wt_cap)
         return fail(ctx, VMAP_ERR_CAPACITY, "parameter arena full");
     if (ctx->pool_used + d->n_rays > ctx->pool_cap)
-        return fail(ctx, VMAP_ERR_CAPACITY, "ray pool arena full (%lld + %lld > %lld)",
-                    ctx->pool_used, d->n_rays, ctx->pool_cap);
+        return fail(ctx, VMAP_ERR_CAPACITY, "ray pool arena full (%lld + %lld > %lld)", ctx->pool_used, d->n_rays,
+                    ctx->pool_cap);
     const int id = (int)ctx->objs.size();
     ObjDev ob{};
     ob.hidden = d->hidden;
@@ -398,11 +601,11 @@ vmap_status vmap_add_object(vmap_ctx* ctx, const vmap_object_desc* d, const floa
     CU(cudaMemcpyAsync(ctx->pool_d + ob.pool_off * REC, d->rays, sizeof(float) * REC * d->n_rays,
                        cudaMemcpyDeviceToDevice, ctx->stream));
     if (init_params) {
-        CU(cudaMemcpyAsync(ctx->params_d + poff, init_params, sizeof(float) * P,
-                           cudaMemcpyDeviceToDevice, ctx->stream));
+        CU(cudaMemcpyAsync(ctx->params_d + poff, init_params, sizeof(float) * P, cudaMemcpyDeviceToDevice,
+                           ctx->stream));
     } else {
-        k_init_params<<<8, 256, 0, ctx->stream>>>(ctx->params_d + poff, d->hidden, d->stream,
-                                                  ctx->sp.key0, ctx->sp.key1);
+        k_init_params<<<8, 256, 0, ctx->stream>>>(ctx->params_d + poff, d->hidden, d->stream, ctx->sp.key0,
+                                                  ctx->sp.key1);
         CHECK_LAUNCH("k_init_params");
     }
     k_shadow<<<16, 256, 0, ctx->stream>>>(ctx->params_d + poff, ctx->wt_d + woff, d->hidden);
@@ -411,127 +614,18 @@ vmap_status vmap_add_object(vmap_ctx* ctx, const vmap_object_desc* d, const floa
     CU(cudaMemsetAsync(ctx->v_d + poff, 0, sizeof(float) * P, ctx->stream));
     CU(cudaMemsetAsync(ctx->steps_d + id, 0, sizeof(int), ctx->stream));
     CU(cudaMemsetAsync(ctx->status_d + id, 0, sizeof(int), ctx->stream));
+    CU(cudaMemsetAsync(ctx->req_d + id, 0, sizeof(int), ctx->stream));
     ctx->param_used = poff + P;
     ctx->wt_used = woff + wt_count(d->hidden);
     ctx->pool_used += d->n_rays;
     ctx->objs.push_back(ob);
-    ctx->max_chunks = std::max(ctx->max_chunks, (int)((P + 1023) / 1024));
+    if (vmap_status s = upload_obj(ctx, id)) return s;
+    const int n = (int)ctx->objs.size();
+    CU(cudaMemcpyAsync(ctx->n_obj_d, &n, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
     ctx->batch_ready = false;
     *out_id = id;
-    return upload_objs(ctx);
-}
-
-}  // extern "C"
-
-namespace {
-// Build the batch: rays_per_object[k] rays of every active object. With
-// given == NULL the rays are picked from the objects' pools; otherwise given
-// holds sum_k R_k records (object-major, active objects with R_k > 0, in
-// index order) in memory of the kind `kind`, which are staged on the device.
-vmap_status sample_impl(vmap_ctx* ctx, const int* rays_per_object, const float* given, cudaMemcpyKind kind) {
-    if (!ctx || !rays_per_object) return fail(ctx, VMAP_ERR_ARG, "null argument");
-    const int K = (int)ctx->objs.size();
-    long long rays = 0, samples = 0, part = 0;
-    int tiles = 0;
-    for (int k = 0; k < K; ++k) {
-        if (rays_per_object[k] < 0) return fail(ctx, VMAP_ERR_ARG, "negative ray count for object %d", k);
-        const ObjDev& ob = ctx->objs[k];
-        const int R = ob.active ? rays_per_object[k] : 0;
-        if (R == 0) continue;
-        const int rt = mmax_of(ob.hidden) / ob.S;
-        const int nt = (R + rt - 1) / rt;
-        rays += R;
-        samples += (long long)R * ob.S;
-        tiles += nt;
-        part += (long long)nt * (param_count(ob.hidden) + NEXTRA);
-    }
-    if (rays > ctx->cfg.max_rays_total)
-        return fail(ctx, VMAP_ERR_CAPACITY, "%lld rays exceed max_rays_total %d", rays, ctx->cfg.max_rays_total);
-    if (tiles > ctx->tile_cap) return fail(ctx, VMAP_ERR_CAPACITY, "too many tiles");
-    if (part > ctx->part_cap) {
-        // grow the partial buffer (synchronises; never inside a captured region)
-        CU(cudaStreamSynchronize(ctx->stream));
-        if (ctx->part_d) CU(cudaFree(ctx->part_d));
-        ctx->part_d = nullptr;
-        ctx->part_cap = 0;
-        const long long cap = part + part / 4 + 4096;
-        CU(cudaMalloc((void**)&ctx->part_d, sizeof(float) * cap));
-        ctx->part_cap = cap;
-    }
-    // batch objects in index order; tiles grouped by hidden class, object order within
-    ctx->bobj.clear();
-    std::vector<int> bray;
-    int ray_off = 0;
-    long long s_off = 0;
-    for (int k = 0; k < K; ++k) {
-        ObjDev& ob = ctx->objs[k];
-        const int R = ob.active ? rays_per_object[k] : 0;
-        ob.R = R;
-        ob.n_tiles = 0;
-        if (R == 0) continue;
-        ob.ray_off = ray_off;
-        ob.sample_off = s_off;
-        ob.src_off = given ? (long long)ray_off : ob.pool_off;
-        ctx->bobj.push_back(k);
-        bray.push_back(ray_off);
-        ray_off += R;
-        s_off += (long long)R * ob.S;
-    }
-    std::vector<TileDev> tl;
-    tl.reserve(tiles);
-    long long poff = 0;
-    for (int c = 0; c < 4; ++c) {
-        ctx->cls_begin[c] = (int)tl.size();
-        for (int k : ctx->bobj) {
-            ObjDev& ob = ctx->objs[k];
-            if (ob.hidden != kHidden[c]) continue;
-            const int rt = mmax_of(ob.hidden) / ob.S;
-            const long long stride = param_count(ob.hidden) + NEXTRA;
-            ob.tile_begin = (int)tl.size();
-            ob.part_off = poff;
-            int idx = 0;
-            for (int r0 = 0; r0 < ob.R; r0 += rt, ++idx) {
-                TileDev td{};
-                td.obj = k;
-                td.ray0 = ob.ray_off + r0;
-                td.nr = std::min(rt, ob.R - r0);
-                td.idx = idx;
-                td.part = poff;
-                poff += stride;
-                tl.push_back(td);
-            }
-            ob.n_tiles = idx;
-        }
-        ctx->cls_count[c] = (int)tl.size() - ctx->cls_begin[c];
-    }
-    ctx->nb = (int)ctx->bobj.size();
-    ctx->total_rays = (int)rays;
-    ctx->total_samples = samples;
-    ctx->n_tiles = (int)tl.size();
-    ctx->batch_given = given != nullptr;
-    if (given && rays)
-        CU(cudaMemcpyAsync(ctx->given_d, given, sizeof(float) * REC * rays, kind, ctx->stream));
-    if (vmap_status s = upload_objs(ctx)) return s;
-    if (ctx->nb) {
-        CU(cudaMemcpyAsync(ctx->bobj_d, ctx->bobj.data(), sizeof(int) * ctx->nb, cudaMemcpyHostToDevice, ctx->stream));
-        CU(cudaMemcpyAsync(ctx->bray_d, bray.data(), sizeof(int) * ctx->nb, cudaMemcpyHostToDevice, ctx->stream));
-        CU(cudaMemcpyAsync(ctx->tiles_d, tl.data(), sizeof(TileDev) * tl.size(), cudaMemcpyHostToDevice, ctx->stream));
-        CU(cudaStreamSynchronize(ctx->stream));   // host vectors go out of scope
-        const int blocks = (int)((rays + 127) / 128);
-        const int pi = prof_begin(ctx, PS_SAMPLE);
-        k_sample<<<blocks, 128, 0, ctx->stream>>>(ctx->sp, ctx->objs_d, ctx->bobj_d, ctx->bray_d, ctx->nb,
-                                                 (int)rays, given ? ctx->given_d : ctx->pool_d, given ? 1 : 0,
-                                                 ctx->steps_d, ctx->pick_d, ctx->t_d);
-        prof_end(ctx, pi);
-        CHECK_LAUNCH("k_sample");
-    }
-    ctx->batch_ready = true;
     return VMAP_OK;
 }
-
-}  // namespace
-
-extern "C" {
 
 vmap_status vmap_sample_rays(vmap_ctx* ctx, const int* rays_per_object) {
     return sample_impl(ctx, rays_per_object, nullptr, cudaMemcpyDeviceToDevice);
@@ -542,56 +636,39 @@ vmap_status vmap_sample_rays_given(vmap_ctx* ctx, const float* rays, const int* 
     return sample_impl(ctx, rays_per_object, rays, cudaMemcpyDeviceToDevice);
 }
 
-vmap_status vmap_train_step_host(vmap_ctx* ctx, const float* rays, const int* rays_per_object,
-                                 float* loss) {
-    if (!ctx || !rays || !loss) return fail(ctx, VMAP_ERR_ARG, "null argument");
-    if (vmap_status s = sample_impl(ctx, rays_per_object, rays, cudaMemcpyHostToDevice)) return s;
-    if (vmap_status s = vmap_train_step(ctx, ctx->loss_d)) return s;
-    CU(cudaMemcpyAsync(loss, ctx->loss_d, sizeof(float) * ctx->objs.size(), cudaMemcpyDeviceToHost, ctx->stream));
-    CU(cudaStreamSynchronize(ctx->stream));
-    return VMAP_OK;
-}
-
-vmap_status vmap_profile_enable(vmap_ctx* ctx, int on) {
-    if (!ctx) return VMAP_ERR_ARG;
-    prof_flush(ctx);
-    ctx->prof_on = on != 0;
-    return VMAP_OK;
-}
-
-vmap_status vmap_profile_reset(vmap_ctx* ctx) {
-    if (!ctx) return VMAP_ERR_ARG;
-    prof_flush(ctx);
-    for (int i = 0; i < PS_N; ++i) {
-        ctx->prof_ms[i] = 0.0;
-        ctx->prof_n[i] = 0;
-    }
-    return VMAP_OK;
-}
-
-vmap_status vmap_profile_read(vmap_ctx* ctx, int slot, const char** name, long long* launches, double* total_ms) {
-    if (!ctx) return VMAP_ERR_ARG;
-    if (slot < 0 || slot >= PS_N) return VMAP_ERR_ARG;
-    prof_flush(ctx);
-    if (name) *name = kProfNames[slot];
-    if (launches) *launches = ctx->prof_n[slot];
-    if (total_ms) *total_ms = ctx->prof_ms[slot];
-    return VMAP_OK;
-}
-
 vmap_status vmap_train_step(vmap_ctx* ctx, float* out_loss) {
     if (!ctx) return VMAP_ERR_ARG;
     if (!ctx->batch_ready) return fail(ctx, VMAP_ERR_STATE, "train_step needs a fresh vmap_sample_rays");
-    if (vmap_status s = fill_nan(ctx, out_loss, ctx->objs.size())) return s;
-    if (vmap_status s = run_tiles<MODE_TRAIN>(ctx)) return s;
-    if (vmap_status s = run_reduce(ctx, RED_ADAM, nullptr, nullptr, out_loss, nullptr)) return s;
-    if (ctx->nb) {
-        const int pi = prof_begin(ctx, PS_FINISH);
-        k_finish<<<1, 256, 0, ctx->stream>>>(ctx->bobj_d, ctx->nb, ctx->steps_d, ctx->status_d);
-        prof_end(ctx, pi);
-        CHECK_LAUNCH("k_finish");
+    const int mask = class_mask(ctx);
+    if (ctx->graph_on) {
+        if (ctx->g_train && ctx->g_classes != mask) {
+            prof_flush(ctx);
+            cudaGraphExecDestroy(ctx->g_train);
+            ctx->g_train = nullptr;
+            release_graph_prof(ctx, ctx->g_prof[2]);
+        }
+        if (!ctx->g_train) {
+            vmap_status s = capture(ctx, &ctx->g_train, &ctx->g_prof[2], [&] { return launch_train(ctx, mask); });
+            if (s) return s;
+            ctx->g_classes = mask;
+        }
+        if (vmap_status s = replay(ctx, ctx->g_train, ctx->g_prof[2])) return s;
+    } else {
+        if (vmap_status s = launch_train(ctx, mask)) return s;
     }
+    if (out_loss)
+        CU(cudaMemcpyAsync(out_loss, ctx->loss_d, sizeof(float) * ctx->objs.size(), cudaMemcpyDeviceToDevice,
+                           ctx->stream));
     ctx->batch_ready = false;
+    return VMAP_OK;
+}
+
+vmap_status vmap_train_step_host(vmap_ctx* ctx, const float* rays, const int* rays_per_object, float* loss) {
+    if (!ctx || !rays || !loss) return fail(ctx, VMAP_ERR_ARG, "null argument");
+    if (vmap_status s = sample_impl(ctx, rays_per_object, rays, cudaMemcpyHostToDevice)) return s;
+    if (vmap_status s = vmap_train_step(ctx, nullptr)) return s;
+    CU(cudaMemcpyAsync(loss, ctx->loss_d, sizeof(float) * ctx->objs.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
     return VMAP_OK;
 }
 
@@ -599,16 +676,17 @@ vmap_status vmap_forward(vmap_ctx* ctx, float* out_loss) {
     if (!ctx || !out_loss) return fail(ctx, VMAP_ERR_ARG, "null argument");
     if (!ctx->batch_ready) return fail(ctx, VMAP_ERR_STATE, "forward needs a drawn batch");
     if (vmap_status s = fill_nan(ctx, out_loss, ctx->objs.size())) return s;
-    if (vmap_status s = run_tiles<MODE_FORWARD>(ctx)) return s;
-    return run_reduce(ctx, RED_LOSS, nullptr, nullptr, out_loss, nullptr);
+    if (vmap_status s = launch_tiles<MODE_FORWARD>(ctx, class_mask(ctx))) return s;
+    return launch_reduce(ctx, RED_LOSS, nullptr, nullptr, out_loss, nullptr);
 }
 
 vmap_status vmap_backward(vmap_ctx* ctx, const float* grad_loss, float* grad_params, float* grad_center) {
     if (!ctx || !grad_params) return fail(ctx, VMAP_ERR_ARG, "null argument");
     if (!ctx->batch_ready) return fail(ctx, VMAP_ERR_STATE, "backward needs a drawn batch");
-    vmap_status s = grad_center ? run_tiles<MODE_GRAD_CENTER>(ctx) : run_tiles<MODE_TRAIN>(ctx);
+    const int mask = class_mask(ctx);
+    vmap_status s = grad_center ? launch_tiles<MODE_GRAD_CENTER>(ctx, mask) : launch_tiles<MODE_TRAIN>(ctx, mask);
     if (s) return s;
-    return run_reduce(ctx, RED_GRAD, grad_loss, grad_params, nullptr, grad_center);
+    return launch_reduce(ctx, RED_GRAD, grad_loss, grad_params, nullptr, grad_center);
 }
 
 vmap_status vmap_query_occupancy(vmap_ctx* ctx, int obj, const float* pts, long long n, float* occ, float* rgb) {
@@ -616,40 +694,39 @@ vmap_status vmap_query_occupancy(vmap_ctx* ctx, int obj, const float* pts, long 
     if (n < 0) return fail(ctx, VMAP_ERR_ARG, "negative point count");
     if (n == 0) return VMAP_OK;
     if (!pts || !occ) return fail(ctx, VMAP_ERR_ARG, "null argument");
-    const int H = ctx->objs[obj].hidden;
+    const int c = class_of(ctx->objs[obj].hidden);
     TileArgs ta = base_args(ctx);
     ta.eval_obj = obj;
     ta.eval_n = n;
     ta.qpts = pts;
     ta.qocc = occ;
     ta.qrgb = rgb;
-    const int rt = mmax_of(H);
+    const int rt = mmax_of(c);
     const long long blocks = (n + rt - 1) / rt;
-    cudaError_t e = launch_tile_h<MODE_QUERY>(H, (int)blocks, ctx->stream, ctx->sp, ta);
+    cudaError_t e = launch_tile_c<MODE_QUERY>(c, (int)blocks, ctx->stream, ctx->sp, ta);
     if (e != cudaSuccess) return fail(ctx, VMAP_ERR_CUDA, "query kernel failed: %s", cudaGetErrorString(e));
     return VMAP_OK;
 }
 
-vmap_status vmap_render_depth(vmap_ctx* ctx, int obj, const float* rays, long long n,
-                              const float* box_half, int n_samples, float* depth) {
+vmap_status vmap_render_depth(vmap_ctx* ctx, int obj, const float* rays, long long n, const float* box_half,
+                              int n_samples, float* depth) {
     if (vmap_status s = check_obj(ctx, obj)) return s;
     if (!rays || !box_half || !depth) return fail(ctx, VMAP_ERR_ARG, "null argument");
     if (n < 0) return fail(ctx, VMAP_ERR_ARG, "negative ray count");
-    const int H = ctx->objs[obj].hidden;
-    if (n_samples < 1 || n_samples > mmax_of(H))
-        return fail(ctx, VMAP_ERR_ARG, "n_samples must be in [1, %d] for hidden %d", mmax_of(H), H);
+    const int c = class_of(ctx->objs[obj].hidden);
+    if (n_samples < 1 || n_samples > mmax_of(c))
+        return fail(ctx, VMAP_ERR_ARG, "n_samples must be in [1, %d] for hidden %d", mmax_of(c), hidden_of(c));
     if (n == 0) return VMAP_OK;
     TileArgs ta = base_args(ctx);
     ta.pool = rays;
-    ta.pick = nullptr;
     ta.eval_out = depth;
     for (int a = 0; a < 3; ++a) ta.eval_half[a] = box_half[a];
     ta.eval_obj = obj;
     ta.eval_n = n;
     ta.eval_S = n_samples;
-    const int rt = mmax_of(H) / n_samples;
+    const int rt = std::min(RTMAX, mmax_of(c) / n_samples);
     const long long blocks = (n + rt - 1) / rt;
-    cudaError_t e = launch_tile_h<MODE_EVAL>(H, (int)blocks, ctx->stream, ctx->sp, ta);
+    cudaError_t e = launch_tile_c<MODE_EVAL>(c, (int)blocks, ctx->stream, ctx->sp, ta);
     if (e != cudaSuccess) return fail(ctx, VMAP_ERR_CUDA, "eval kernel failed: %s", cudaGetErrorString(e));
     return VMAP_OK;
 }
@@ -658,7 +735,8 @@ vmap_status vmap_get_object_state(vmap_ctx* ctx, int obj, float* params, float* 
     if (vmap_status s = check_obj(ctx, obj)) return s;
     const ObjDev& ob = ctx->objs[obj];
     const size_t bytes = sizeof(float) * param_count(ob.hidden);
-    if (params) CU(cudaMemcpyAsync(params, ctx->params_d + ob.param_off, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (params)
+        CU(cudaMemcpyAsync(params, ctx->params_d + ob.param_off, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
     if (m) CU(cudaMemcpyAsync(m, ctx->m_d + ob.param_off, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
     if (v) CU(cudaMemcpyAsync(v, ctx->v_d + ob.param_off, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
     if (step) {
@@ -668,7 +746,8 @@ vmap_status vmap_get_object_state(vmap_ctx* ctx, int obj, float* params, float* 
     return VMAP_OK;
 }
 
-vmap_status vmap_set_object_state(vmap_ctx* ctx, int obj, const float* params, const float* m, const float* v, int step) {
+vmap_status vmap_set_object_state(vmap_ctx* ctx, int obj, const float* params, const float* m, const float* v,
+                                  int step) {
     if (vmap_status s = check_obj(ctx, obj)) return s;
     if (step < 0) return fail(ctx, VMAP_ERR_ARG, "negative step");
     const ObjDev& ob = ctx->objs[obj];
@@ -695,14 +774,16 @@ vmap_status vmap_param_arena_size(vmap_ctx* ctx, long long* n) {
 vmap_status vmap_get_params(vmap_ctx* ctx, float* arena) {
     if (!ctx || !arena) return fail(ctx, VMAP_ERR_ARG, "null argument");
     if (ctx->param_used)
-        CU(cudaMemcpyAsync(arena, ctx->params_d, sizeof(float) * ctx->param_used, cudaMemcpyDeviceToDevice, ctx->stream));
+        CU(cudaMemcpyAsync(arena, ctx->params_d, sizeof(float) * ctx->param_used, cudaMemcpyDeviceToDevice,
+                           ctx->stream));
     return VMAP_OK;
 }
 
 vmap_status vmap_set_params(vmap_ctx* ctx, const float* arena) {
     if (!ctx || !arena) return fail(ctx, VMAP_ERR_ARG, "null argument");
     if (!ctx->param_used) return VMAP_OK;
-    CU(cudaMemcpyAsync(ctx->params_d, arena, sizeof(float) * ctx->param_used, cudaMemcpyDeviceToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(ctx->params_d, arena, sizeof(float) * ctx->param_used, cudaMemcpyDeviceToDevice,
+                       ctx->stream));
     for (const ObjDev& ob : ctx->objs) {
         k_shadow<<<16, 256, 0, ctx->stream>>>(ctx->params_d + ob.param_off, ctx->wt_d + ob.wt_off, ob.hidden);
         CHECK_LAUNCH("k_shadow");
@@ -715,17 +796,18 @@ vmap_status vmap_set_object_active(vmap_ctx* ctx, int obj, int active) {
     ctx->objs[obj].active = active ? 1 : 0;
     if (active) CU(cudaMemsetAsync(ctx->status_d + obj, 0, sizeof(int), ctx->stream));
     ctx->batch_ready = false;
-    return VMAP_OK;
+    return upload_obj(ctx, obj);
 }
 
 vmap_status vmap_set_object_center(vmap_ctx* ctx, int obj, const float* center) {
     if (vmap_status s = check_obj(ctx, obj)) return s;
     if (!center) return fail(ctx, VMAP_ERR_ARG, "null center");
     for (int a = 0; a < 3; ++a) ctx->objs[obj].c[a] = center[a];
-    return upload_objs(ctx);
+    return upload_obj(ctx, obj);
 }
 
-vmap_status vmap_object_info(vmap_ctx* ctx, int obj, int* hidden, int* param_count_out, long long* param_offset, int* spr) {
+vmap_status vmap_object_info(vmap_ctx* ctx, int obj, int* hidden, int* param_count_out, long long* param_offset,
+                             int* spr) {
     if (vmap_status s = check_obj(ctx, obj)) return s;
     const ObjDev& ob = ctx->objs[obj];
     if (hidden) *hidden = ob.hidden;
@@ -743,6 +825,11 @@ vmap_status vmap_num_objects(vmap_ctx* ctx, int* n) {
 
 vmap_status vmap_batch_info(vmap_ctx* ctx, int* n_rays, long long* n_samples) {
     if (!ctx) return VMAP_ERR_ARG;
+    int c[BC_N];
+    CU(cudaMemcpyAsync(c, ctx->counts_d, sizeof c, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    ctx->total_rays = c[BC_RAYS];
+    ctx->total_samples = ((long long)c[BC_SAMPLES_HI] << 31) | (long long)c[BC_SAMPLES_LO];
     if (n_rays) *n_rays = ctx->total_rays;
     if (n_samples) *n_samples = ctx->total_samples;
     return VMAP_OK;
@@ -750,6 +837,7 @@ vmap_status vmap_batch_info(vmap_ctx* ctx, int* n_rays, long long* n_samples) {
 
 vmap_status vmap_get_samples(vmap_ctx* ctx, int* pick, float* t) {
     if (!ctx) return VMAP_ERR_ARG;
+    if (vmap_status s = vmap_batch_info(ctx, nullptr, nullptr)) return s;
     if (pick && ctx->total_rays)
         CU(cudaMemcpyAsync(pick, ctx->pick_d, sizeof(int) * ctx->total_rays, cudaMemcpyDeviceToDevice, ctx->stream));
     if (t && ctx->total_samples)
@@ -761,9 +849,7 @@ vmap_status vmap_sync_status(vmap_ctx* ctx, int* n_faulted, int* ids, int max_id
     if (!ctx) return VMAP_ERR_ARG;
     const int K = (int)ctx->objs.size();
     std::vector<int> st(K);
-    if (K) {
-        CU(cudaMemcpyAsync(st.data(), ctx->status_d, sizeof(int) * K, cudaMemcpyDeviceToHost, ctx->stream));
-    }
+    if (K) CU(cudaMemcpyAsync(st.data(), ctx->status_d, sizeof(int) * K, cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
     int nf = 0;
     for (int k = 0; k < K; ++k)
@@ -773,6 +859,130 @@ vmap_status vmap_sync_status(vmap_ctx* ctx, int* n_faulted, int* ids, int max_id
         }
     if (n_faulted) *n_faulted = nf;
     return nf ? VMAP_ERR_NAN : VMAP_OK;
+}
+
+vmap_status vmap_profile_enable(vmap_ctx* ctx, int on) {
+    if (!ctx) return VMAP_ERR_ARG;
+    prof_flush(ctx);
+    if ((on != 0) != ctx->prof_on) drop_graphs(ctx);   // graphs carry (or not) the event records
+    ctx->prof_on = on != 0;
+    return VMAP_OK;
+}
+
+vmap_status vmap_profile_reset(vmap_ctx* ctx) {
+    if (!ctx) return VMAP_ERR_ARG;
+    prof_flush(ctx);
+    for (int i = 0; i < PS_N; ++i) {
+        ctx->prof_ms[i] = 0.0;
+        ctx->prof_n[i] = 0;
+    }
+    return VMAP_OK;
+}
+
+vmap_status vmap_profile_read(vmap_ctx* ctx, int slot, const char** name, long long* launches, double* total_ms) {
+    if (!ctx) return VMAP_ERR_ARG;
+    if (slot < 0 || slot >= PS_N) return VMAP_ERR_ARG;
+    prof_flush(ctx);
+    if (name) *name = kProfNames[slot];
+    if (launches) *launches = ctx->prof_n[slot];
+    if (total_ms) *total_ms = ctx->prof_ms[slot];
+    return VMAP_OK;
+}
+
+vmap_status vmap_set_graph(vmap_ctx* ctx, int on) {
+    if (!ctx) return VMAP_ERR_ARG;
+    drop_graphs(ctx);
+    ctx->graph_on = on != 0;
+    return VMAP_OK;
+}
+
+vmap_status vmap_get_launch(vmap_ctx* ctx, int* rays_per_tile, int* grid_mult) {
+    if (!ctx) return VMAP_ERR_ARG;
+    for (int c = 0; c < NCLASS; ++c) {
+        if (rays_per_tile) rays_per_tile[c] = ctx->rt[c];
+        if (grid_mult) grid_mult[c] = ctx->gmult[c];
+    }
+    return VMAP_OK;
+}
+
+vmap_status vmap_set_launch(vmap_ctx* ctx, const int* rays_per_tile, const int* grid_mult) {
+    if (!ctx) return VMAP_ERR_ARG;
+    for (int c = 0; c < NCLASS; ++c) {
+        if (rays_per_tile && (rays_per_tile[c] < 1 || rays_per_tile[c] > RTMAX))
+            return fail(ctx, VMAP_ERR_ARG, "rays per tile must be in [1, %d]", RTMAX);
+        if (grid_mult && (grid_mult[c] < 1 || grid_mult[c] > GMULT_MAX))
+            return fail(ctx, VMAP_ERR_ARG, "grid multiplier must be in [1, %d]", GMULT_MAX);
+    }
+    drop_graphs(ctx);
+    for (int c = 0; c < NCLASS; ++c) {
+        if (rays_per_tile) ctx->rt[c] = rays_per_tile[c];
+        if (grid_mult) ctx->gmult[c] = grid_mult[c];
+    }
+    ctx->batch_ready = false;
+    return VMAP_OK;
+}
+
+vmap_status vmap_autotune(vmap_ctx* ctx, const int* rays_per_object, int reps, float* best_ms) {
+    if (!ctx || !rays_per_object || reps < 1) return fail(ctx, VMAP_ERR_ARG, "bad argument");
+    const int mask = class_mask(ctx);
+    const bool graph = ctx->graph_on, prof = ctx->prof_on;
+    drop_graphs(ctx);
+    ctx->graph_on = false;
+    ctx->prof_on = false;
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    vmap_status status = VMAP_OK;
+    for (int c = 0; c < NCLASS && status == VMAP_OK; ++c) {
+        if (best_ms) best_ms[c] = 0.f;
+        if (!(mask & (1 << c))) continue;
+        int Smin = SMAX;
+        for (const ObjDev& o : ctx->objs)
+            if (class_of(o.hidden) == c) Smin = std::min(Smin, o.S);
+        const int rt_hi = std::max(1, std::min(RTMAX, mmax_of(c) / Smin));
+        float best = 1e30f;
+        int best_rt = ctx->rt[c], best_g = ctx->gmult[c];
+        for (int g = 1; g <= GMULT_MAX && status == VMAP_OK; ++g) {
+            for (int rt = rt_hi; rt >= 1 && status == VMAP_OK; rt = rt > 4 ? rt - 1 : rt / 2) {
+                ctx->rt[c] = rt;
+                ctx->gmult[c] = g;
+                status = sample_impl(ctx, rays_per_object, nullptr, cudaMemcpyDeviceToDevice);
+                if (status) break;
+                TileArgs ta = base_args(ctx);
+                ta.tiles = ctx->tiles_d + (long long)c * ctx->tile_cap;
+                ta.n_tiles = ctx->counts_d + BC_TILES + c;
+                // the tile kernel only writes partial slots: timing it changes no state
+                cudaError_t e = launch_tile_c<MODE_TRAIN>(c, grid_of(ctx, c), ctx->stream, ctx->sp, ta);
+                if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
+                for (int r = 0; r < reps && e == cudaSuccess; ++r)
+                    e = launch_tile_c<MODE_TRAIN>(c, grid_of(ctx, c), ctx->stream, ctx->sp, ta);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                if (e != cudaSuccess) {
+                    status = fail(ctx, VMAP_ERR_CUDA, "autotune launch failed: %s", cudaGetErrorString(e));
+                    break;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                ms /= reps;
+                if (ms < best) {
+                    best = ms;
+                    best_rt = rt;
+                    best_g = g;
+                }
+                if (rt == 1) break;
+            }
+        }
+        ctx->rt[c] = best_rt;
+        ctx->gmult[c] = best_g;
+        if (best_ms) best_ms[c] = best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->graph_on = graph;
+    ctx->prof_on = prof;
+    ctx->batch_ready = false;
+    return status;
 }
 
 }  // extern "C"

@@ -23,7 +23,8 @@ struct StepParams {
     uint32_t key0, key1;
 };
 
-// One object, as the kernels see it. Rewritten by the host at every batch draw.
+// One object's fixed description, written by the host when the object is
+// added or changed.
 struct ObjDev {
     int hidden, S, n_surface, n_strat;
     float c[3];
@@ -32,25 +33,30 @@ struct ObjDev {
     long long wt_off;      // float offset into the transposed-weight arena
     long long pool_off;    // record offset into the ray-pool arena
     long long pool_n;      // records in the pool
-    long long src_off;     // record offset of this batch's rays in the batch source
-                           // (pool arena: pool_off; caller-given rays: ray_off)
     unsigned stream;       // Philox stream id
-    int R;                 // rays this step (0: not in the batch)
-    int ray_off;           // first batch ray
-    int tile_begin;        // first tile
-    long long sample_off;  // first batch sample
-    long long part_off;    // float offset of the first tile's partial
-    int n_tiles;
-    int active;
+    int active;            // 0: stopped by the caller
 };
 
-// A tile: n_rays consecutive batch rays of one object, processed by one CTA.
+// One object's place in the current batch, written by the device-side batch
+// builder (k_build) at every draw.
+struct ObjBatch {
+    int R;                 // rays this step (0: not in the batch)
+    int ray_off;           // first batch ray
+    long long sample_off;  // first batch sample
+    long long src_off;     // record offset of its rays in the batch source
+                           // (pool arena: pool_off; caller-given rays: ray_off)
+    int tile_begin;        // first tile (within its width class)
+    int n_runs;            // partial slots holding its gradient
+    long long part_off;    // float offset of its first slot
+};
+
+// A tile: nr consecutive batch rays of one object, processed by one CTA.
 struct TileDev {
     int obj;
     int ray0;         // first batch ray
     int nr;           // rays in the tile
-    int idx;          // tile index within its object
-    long long part;   // float offset of this tile's partial
+    int pad;
+    long long part;   // float offset of the slot of the run the tile belongs to
 };
 
 __host__ __device__ constexpr long long param_count(int H) {

@@ -1,6 +1,7 @@
 // Per-object gradient reduction + Adam, weight initialisation, and the
 // transposed-weight shadow that the forward GEMMs stage from.
 #pragma once
+#include "vmap_build.cuh"
 #include "vmap_common.cuh"
 
 namespace vmapk {
@@ -23,23 +24,27 @@ __device__ __forceinline__ long long wt_index(int H, long long p) {
     return -1;
 }
 
-__device__ __forceinline__ float object_loss(const StepParams& sp, const ObjDev& ob,
+__device__ __forceinline__ float object_loss(const StepParams& sp, const ObjDev& ob, const ObjBatch& bt,
                                              const float* __restrict__ part) {
     const long long P = param_count(ob.hidden);
     float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-    for (int t = 0; t < ob.n_tiles; ++t) {
-        const float* e = part + ob.part_off + (long long)t * (P + NEXTRA) + P;
+    for (int t = 0; t < bt.n_runs; ++t) {
+        const float* e = part + bt.part_off + (long long)t * (P + NEXTRA) + P;
         s0 += e[0]; s1 += e[1]; s2 += e[2];
     }
-    const float R = (float)ob.R;
+    const float R = (float)bt.R;
     return s0 / R + sp.lam_c * (s1 / (3.f * R)) + sp.lam_o * (s2 / R);
 }
 
-// grid (chunks, batch objects); each block covers 4 * blockDim parameters of one object.
-// Sums the object's tile partials in tile order, then (RED_ADAM) applies Adam
-// with the object's step count + 1, or (RED_GRAD) writes grad_loss[k] * g.
+// Fixed grid; each block takes reduce work items (batch object, chunk of
+// REDUCE_CHUNK parameters) from the builder's list. Sums the object's run
+// slots in slot order, then (RED_ADAM) applies Adam with the object's step
+// count + 1, or (RED_GRAD) writes grad_loss[k] * g.
 __global__ void __launch_bounds__(256) k_reduce(StepParams sp, const ObjDev* __restrict__ objs,
+                                                const ObjBatch* __restrict__ obs,
                                                 const int* __restrict__ bobj,
+                                                const int2* __restrict__ items,
+                                                const int* __restrict__ counts,
                                                 const float* __restrict__ part, float* params,
                                                 float* wt, float* mom, float* vel,
                                                 const int* __restrict__ steps, int* status,
@@ -47,61 +52,68 @@ __global__ void __launch_bounds__(256) k_reduce(StepParams sp, const ObjDev* __r
                                                 float* __restrict__ grad_out,
                                                 float* __restrict__ loss_out,
                                                 float* __restrict__ dcenter_out) {
-    const int k = bobj[blockIdx.y];
-    const ObjDev& ob = objs[k];
-    const int H = ob.hidden;
-    const long long P = param_count(H);
-    const long long p0 = (long long)blockIdx.x * blockDim.x * 4;
-    if (p0 >= P) return;
-    const float L = object_loss(sp, ob, part);
-    const bool frozen = status[k] != 0;
-    const float gl = grad_loss ? grad_loss[k] : 1.f;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        if (loss_out) loss_out[k] = frozen ? __int_as_float(0x7fc00000) : L;
-        if (dcenter_out) {
-            float d[3] = {0.f, 0.f, 0.f};
-            for (int t = 0; t < ob.n_tiles; ++t) {
-                const float* e = part + ob.part_off + (long long)t * (P + NEXTRA) + P;
-                d[0] += e[3]; d[1] += e[4]; d[2] += e[5];
+    const int n_items = counts[BC_ITEMS];
+#pragma unroll 1
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const int2 item = items[it];
+        const int k = bobj[item.x];
+        const ObjDev& ob = objs[k];
+        const ObjBatch& bt = obs[k];
+        const int H = ob.hidden;
+        const long long P = param_count(H);
+        const long long p0 = (long long)item.y * REDUCE_CHUNK;
+        const float L = object_loss(sp, ob, bt, part);
+        const bool frozen = status[k] != 0;
+        const float gl = grad_loss ? grad_loss[k] : 1.f;
+        if (item.y == 0 && threadIdx.x == 0) {
+            if (loss_out) loss_out[k] = frozen ? __int_as_float(0x7fc00000) : L;
+            if (dcenter_out) {
+                float d[3] = {0.f, 0.f, 0.f};
+                for (int t = 0; t < bt.n_runs; ++t) {
+                    const float* e = part + bt.part_off + (long long)t * (P + NEXTRA) + P;
+                    d[0] += e[3]; d[1] += e[4]; d[2] += e[5];
+                }
+                for (int a = 0; a < 3; ++a) dcenter_out[3 * k + a] = gl * d[a];
             }
-            for (int a = 0; a < 3; ++a) dcenter_out[3 * k + a] = gl * d[a];
         }
-    }
-    if (mode == RED_LOSS) return;
-    if (mode == RED_ADAM && (frozen || !isfinite(L))) {
-        if (!frozen && blockIdx.x == 0 && threadIdx.x == 0) status[k] = 1;
-        return;
-    }
-    const int t1 = steps[k] + 1;
-    const float bc1 = 1.f - powf(sp.beta1, (float)t1);
-    const float bc2 = 1.f - powf(sp.beta2, (float)t1);
-    const long long end = min(P, p0 + (long long)blockDim.x * 4);
-    for (long long p = p0 + threadIdx.x; p < end; p += blockDim.x) {
-        float g = 0.f;
-        const float* src = part + ob.part_off + p;
-        for (int t = 0; t < ob.n_tiles; ++t) g += src[(long long)t * (P + NEXTRA)];
-        if (mode == RED_GRAD) {
-            grad_out[ob.param_off + p] = gl * g;
+        if (mode == RED_LOSS) continue;
+        if (mode == RED_ADAM && (frozen || !isfinite(L))) {
+            if (!frozen && item.y == 0 && threadIdx.x == 0) status[k] = 1;
             continue;
         }
-        if (!isfinite(g)) {            // leave the element, flag the object
-            atomicOr(status + k, 2);
-            continue;
+        const int t1 = steps[k] + 1;
+        const float bc1 = 1.f - powf(sp.beta1, (float)t1);
+        const float bc2 = 1.f - powf(sp.beta2, (float)t1);
+        const long long end = min(P, p0 + REDUCE_CHUNK);
+        for (long long p = p0 + threadIdx.x; p < end; p += blockDim.x) {
+            float g = 0.f;
+            const float* src = part + bt.part_off + p;
+            for (int t = 0; t < bt.n_runs; ++t) g += src[(long long)t * (P + NEXTRA)];
+            if (mode == RED_GRAD) {
+                grad_out[ob.param_off + p] = gl * g;
+                continue;
+            }
+            if (!isfinite(g)) {            // leave the element, flag the object
+                atomicOr(status + k, 2);
+                continue;
+            }
+            const long long q = ob.param_off + p;
+            const float m = sp.beta1 * mom[q] + (1.f - sp.beta1) * g;
+            const float v = sp.beta2 * vel[q] + (1.f - sp.beta2) * g * g;
+            mom[q] = m;
+            vel[q] = v;
+            const float th = params[q] - sp.lr * (m / bc1) / (sqrtf(v / bc2) + sp.eps);
+            params[q] = th;
+            const long long w = wt_index(H, p);
+            if (w >= 0) wt[ob.wt_off + w] = th;
         }
-        const long long q = ob.param_off + p;
-        const float m = sp.beta1 * mom[q] + (1.f - sp.beta1) * g;
-        const float v = sp.beta2 * vel[q] + (1.f - sp.beta2) * g * g;
-        mom[q] = m;
-        vel[q] = v;
-        const float th = params[q] - sp.lr * (m / bc1) / (sqrtf(v / bc2) + sp.eps);
-        params[q] = th;
-        const long long w = wt_index(H, p);
-        if (w >= 0) wt[ob.wt_off + w] = th;
     }
 }
 
 // after the update: advance the step count of every object that was trained
-__global__ void k_finish(const int* __restrict__ bobj, int nb, int* steps, const int* status) {
+__global__ void k_finish(const int* __restrict__ bobj, const int* __restrict__ counts, int* steps,
+                         const int* status) {
+    const int nb = counts[BC_NB];
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nb; j += gridDim.x * blockDim.x) {
         const int k = bobj[j];
         if (status[k] == 0) steps[k] += 1;

@@ -1,5 +1,6 @@
 // Ray picking and depth-guided sampling (vMAP section 3.3, Eq. 1 and Eq. 2).
 #pragma once
+#include "vmap_build.cuh"
 #include "vmap_common.cuh"
 
 namespace vmapk {
@@ -34,27 +35,32 @@ __device__ __forceinline__ int upper_index(const int* off, int n, int i) {
     return lo;
 }
 
-// One thread per batch ray. Writes the picked pool index (the ray's own index
-// when the caller gives the rays) and S sorted depths.
+// One thread per batch ray (fixed grid; threads past the batch exit). Writes
+// the picked pool index (the ray's own index when the caller gives the rays)
+// and S sorted depths.
 //   word 0          -> pick = floor(w * n_pool / 2^32)
 //   words 1..N_c    -> u_j, t = t_n + (j + u_j) / N_c * (t_s + pad - t_n)      (Eq. 1)
 //   next word pairs -> Box-Muller z = sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2),
 //                      t = max(t_s + d_sigma z, t_n)                            (Eq. 2)
 // t_s is the ray's depth, or t_far when the depth is not positive.
 __global__ void __launch_bounds__(128) k_sample(StepParams sp, const ObjDev* __restrict__ objs,
+                                                const ObjBatch* __restrict__ obs,
                                                 const int* __restrict__ bobj,
-                                                const int* __restrict__ bray_off, int nb,
-                                                int total_rays, const float* __restrict__ src,
-                                                int given,
+                                                const int* __restrict__ bray_off,
+                                                const int* __restrict__ counts,
+                                                const float* __restrict__ src, int given,
                                                 const int* __restrict__ steps,
                                                 int* __restrict__ pick_out,
                                                 float* __restrict__ t_out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int total_rays = counts[BC_RAYS];
+    const int nb = counts[BC_NB];
     if (i >= total_rays) return;
     const int j = upper_index(bray_off, nb, i);
     const int k = bobj[j];
     const ObjDev& ob = objs[k];
-    const int r = i - ob.ray_off;
+    const ObjBatch& bt = obs[k];
+    const int r = i - bt.ray_off;
     WordStream ws((uint32_t)r, (uint32_t)steps[k], ob.stream, sp.key0, sp.key1);
 
     // word 0 picks the ray; with caller-given rays it is drawn and dropped so
@@ -63,7 +69,7 @@ __global__ void __launch_bounds__(128) k_sample(StepParams sp, const ObjDev* __r
     const long long pick = given ? (long long)r
                                  : (long long)(((unsigned long long)w0 * (unsigned long long)ob.pool_n) >> 32);
     pick_out[i] = (int)pick;
-    const float depth = src[(ob.src_off + pick) * REC + 6];
+    const float depth = src[(bt.src_off + pick) * REC + 6];
     const float ts = depth > 0.f ? depth : sp.t_far;
     const float lo = sp.t_near;
     const float span = ts + sp.depth_pad - lo;
@@ -90,7 +96,7 @@ __global__ void __launch_bounds__(128) k_sample(StepParams sp, const ObjDev* __r
         while (b >= 0 && t[b] > v) { t[b + 1] = t[b]; --b; }
         t[b + 1] = v;
     }
-    float* dst = t_out + ob.sample_off + (long long)r * S;
+    float* dst = t_out + bt.sample_off + (long long)r * S;
     for (int a = 0; a < S; ++a) dst[a] = t[a];
 }
 

@@ -1,14 +1,22 @@
-// Fused per-tile FP32 training kernel: encoding, MLP forward, occupancy
-// rendering, losses, backward through rendering / MLP / encoding.
+// Persistent fused FP32 training kernel: encoding, MLP forward, occupancy
+// rendering, losses, and the backward through rendering, MLP and encoding.
 //
-// One CTA processes a tile of whole rays of one object (so the per-ray scans
-// of Eq. 3 stay inside the CTA). Activations live in shared memory in
-// feature-major layout [feature][sample] with a row stride LD = Mpad + 4
-// (LD = 4 mod 8, so eight rows read at the same sample column hit distinct
-// banks). Each layer is a shared-memory SIMT GEMM with 4x4 register tiles.
-// The CTA writes the tile's weight gradient and loss sums to its own slot of
-// the partial buffer; the reduce/Adam kernel adds the slots of an object in a
-// fixed order (bitwise reproducible).
+// Work unit: a tile of whole rays of one object (so the per-ray scans of
+// Eq. 3 stay inside one CTA). A class launch (one hidden width H) runs a
+// fixed grid; CTA c processes the contiguous tile range
+// [c n / G, (c + 1) n / G) of the class's n tiles, which the device-side batch
+// builder wrote. Consecutive tiles of the same object form a run; the CTA adds
+// each tile's weight gradient into the run's slot of the partial buffer (the
+// first tile stores, the next ones add), so an object has at most
+// (CTAs covering it + 1) slots and the reduce/Adam kernel adds them in a
+// fixed order: results are bitwise reproducible.
+//
+// Activations live in shared memory, feature-major [feature][sample], row
+// stride LD = Mpad + 4 (LD = 4 mod 8: eight consecutive rows read at one
+// sample column hit distinct banks). Each layer is a shared-memory SIMT GEMM
+// with 4x4 register tiles. For H >= 32 the 96-row encoding shares the rows of
+// hidden layers 2-4 (it is recomputed for the layer-1 weight gradient), which
+// lets two CTAs share an SM at H = 32.
 #pragma once
 #include "vmap_common.cuh"
 
@@ -17,27 +25,29 @@ namespace vmapk {
 enum TileMode { MODE_TRAIN = 0, MODE_FORWARD = 1, MODE_GRAD_CENTER = 2, MODE_EVAL = 3, MODE_QUERY = 4 };
 
 template <int H> struct TileCfg;
-template <> struct TileCfg<16>  { static constexpr int MMAX = 240; };
-template <> struct TileCfg<32>  { static constexpr int MMAX = 176; };
-template <> struct TileCfg<64>  { static constexpr int MMAX = 112; };
-template <> struct TileCfg<128> { static constexpr int MMAX = 48; };
+template <> struct TileCfg<16>  { static constexpr int MMAX = 120; static constexpr bool GSEP = true;  static constexpr int CTAS = 2; };
+template <> struct TileCfg<32>  { static constexpr int MMAX = 136; static constexpr bool GSEP = false; static constexpr int CTAS = 2; };
+template <> struct TileCfg<64>  { static constexpr int MMAX = 112; static constexpr bool GSEP = false; static constexpr int CTAS = 1; };
+template <> struct TileCfg<128> { static constexpr int MMAX = 48;  static constexpr bool GSEP = false; static constexpr int CTAS = 1; };
 
 constexpr int RED_FLOATS = 4096;   // split-reduction scratch
 constexpr int RAYF = 16;           // floats of per-ray scratch
+constexpr int RTMAX = 32;          // rays per tile, at most (training / eval modes)
 
 template <int H> struct TileSmem {
     static constexpr int MMAX = TileCfg<H>::MMAX;
+    static constexpr bool GSEP = TileCfg<H>::GSEP;
+    static_assert(GSEP || 3 * H >= DINP, "the encoding must fit in hidden rows 2-4");
     static constexpr int LD = MMAX + 4;
-    static constexpr int RTMAX = MMAX;      // at most one sample per ray
     static constexpr int WS = (DINP * H > H * H ? DINP * H : H * H);
-    static constexpr int G = 0;                                  // [96][LD] encoding
-    static constexpr int ACT = G + DINP * LD;                    // [4][H][LD] hidden activations
-    static constexpr int Y = ACT + 4 * H * LD;                   // [4][LD] outputs / their grads
-    static constexpr int W = Y + 4 * LD;                         // weight staging
-    static constexpr int RED = W + WS;                           // split reduction scratch
-    static constexpr int PS = RED + RED_FLOATS;                  // [LD] prod_{j<i}(1-o_j)
-    static constexpr int TS = PS + LD;                           // [LD] sample depths t
-    static constexpr int RAYS = TS + LD;                         // [RTMAX][RAYF]
+    static constexpr int ACT = 0;                                      // [4][H][LD] hidden activations
+    static constexpr int G = GSEP ? 4 * H * LD : H * LD;               // [96][LD] encoding
+    static constexpr int Y = GSEP ? (4 * H + DINP) * LD : 4 * H * LD;  // [4][LD] outputs / grads
+    static constexpr int W = Y + 4 * LD;                               // weight staging
+    static constexpr int RED = W + WS;
+    static constexpr int PS = RED + RED_FLOATS;                        // [LD] per-sample scratch
+    static constexpr int TS = PS + LD;                                 // [LD] sample depths t
+    static constexpr int RAYS = TS + LD;                               // [RTMAX][RAYF]
     static constexpr int TOTAL = RAYS + RTMAX * RAYF;
     static constexpr size_t BYTES = (size_t)TOTAL * sizeof(float);
 };
@@ -45,8 +55,7 @@ template <int H> struct TileSmem {
 // ---------------------------------------------------------------------------
 // out[n][m] = epi( sum_k A[k][m] * Bm[k][n] ),  m < Mpad, n < N.
 // A: [K][lda] in smem, Bm: [K][N] dense in smem.
-// EPI 0: + bias, ReLU;  EPI 1: + bias;  EPI 2: * (out[n][m] > 0), in place;
-// EPI 3: plain store.
+// EPI 0: + bias, ReLU;  EPI 1: + bias;  EPI 2: * (out[n][m] > 0), in place.
 // A warp covers 8 sample quads x 4 output quads: its A loads touch 128
 // consecutive bytes and its B loads 64, one wavefront each.
 // ---------------------------------------------------------------------------
@@ -91,8 +100,6 @@ __device__ __forceinline__ void gemm_fwd(const float* __restrict__ A, int lda,
                 v.y = prev.y > 0.f ? acc[1][j] : 0.f;
                 v.z = prev.z > 0.f ? acc[2][j] : 0.f;
                 v.w = prev.w > 0.f ? acc[3][j] : 0.f;
-            } else if (EPI == 3) {
-                v.x = acc[0][j]; v.y = acc[1][j]; v.z = acc[2][j]; v.w = acc[3][j];
             } else {
                 const float bb = bias[n];
                 v.x = acc[0][j] + bb; v.y = acc[1][j] + bb; v.z = acc[2][j] + bb; v.w = acc[3][j] + bb;
@@ -105,16 +112,21 @@ __device__ __forceinline__ void gemm_fwd(const float* __restrict__ A, int lda,
     }
 }
 
+__device__ __forceinline__ void acc_store(float* p, float v, bool first) { *p = first ? v : *p + v; }
+
 // ---------------------------------------------------------------------------
-// dW[n][k] = sum_m Z[n][m] * A[k][m]   (reduction over the tile's samples)
-// and db[n] = sum_m Z[n][m]. Written to global g (canonical [n][Kreal]) and gb.
+// dW[n][k] (+)= sum_m Z[n][m] * A[k][m]   (reduction over the tile's samples)
+// and db[n] (+)= sum_m Z[n][m], into global g (canonical [n][Kreal]) and gb;
+// `first` stores, otherwise the tile's sums are added to what the run holds.
+// A thread owns rows n = nq + NQ i and k = kq + KQ j (i, j < 4): the eight
+// lanes that differ in nq read eight consecutive rows (no bank conflicts).
 // The sample range is split SPLIT ways (interleaved quads) to fill the CTA;
 // split partials are combined in a fixed order through smem.
 // ---------------------------------------------------------------------------
 template <int N, int KP>
 __device__ __forceinline__ void gemm_dw(const float* __restrict__ Z, const float* __restrict__ A,
                                         int ld, int Mpad, float* red, float* __restrict__ g,
-                                        int Kreal, float* __restrict__ gb) {
+                                        int Kreal, float* __restrict__ gb, bool first) {
     constexpr int NQ = N / 4, KQ = KP / 4, T = NQ * KQ;
     constexpr int S0 = NTHREADS / T > 0 ? NTHREADS / T : 1;
     constexpr int S1 = RED_FLOATS / (N * KP) > 0 ? RED_FLOATS / (N * KP) : 1;
@@ -132,9 +144,9 @@ __device__ __forceinline__ void gemm_dw(const float* __restrict__ Z, const float
         for (int q = s; q < MQ; q += SPLIT) {
             float4 z[4], a[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) z[i] = *reinterpret_cast<const float4*>(Z + (nq * 4 + i) * ld + q * 4);
+            for (int i = 0; i < 4; ++i) z[i] = *reinterpret_cast<const float4*>(Z + (nq + NQ * i) * ld + q * 4);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) a[j] = *reinterpret_cast<const float4*>(A + (kq * 4 + j) * ld + q * 4);
+            for (int j = 0; j < 4; ++j) a[j] = *reinterpret_cast<const float4*>(A + (kq + KQ * j) * ld + q * 4);
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -148,18 +160,28 @@ __device__ __forceinline__ void gemm_dw(const float* __restrict__ Z, const float
                 }
         }
         if (SPLIT == 1) {
+            // read what the run holds first (16 independent loads in flight), then add and store
+            if (!first) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int k = kq + KQ * j;
+                        if (k < Kreal) acc[i][j] += g[(nq + NQ * i) * Kreal + k];
+                    }
+            }
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    const int k = kq * 4 + j;
-                    if (k < Kreal) g[(nq * 4 + i) * Kreal + k] = acc[i][j];
+                    const int k = kq + KQ * j;
+                    if (k < Kreal) g[(nq + NQ * i) * Kreal + k] = acc[i][j];
                 }
         } else {
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) red[(s * N + nq * 4 + i) * KP + kq * 4 + j] = acc[i][j];
+                for (int j = 0; j < 4; ++j) red[(s * N + nq + NQ * i) * KP + kq + KQ * j] = acc[i][j];
         }
     }
     // bias gradient: 8 lanes per output row, combined by a fixed xor tree
@@ -173,16 +195,31 @@ __device__ __forceinline__ void gemm_dw(const float* __restrict__ Z, const float
         v += __shfl_xor_sync(0xffffffffu, v, 4);
         v += __shfl_xor_sync(0xffffffffu, v, 2);
         v += __shfl_xor_sync(0xffffffffu, v, 1);
-        if (l == 0) gb[n] = v;
+        if (l == 0) acc_store(gb + n, v, first);
     }
     if (SPLIT > 1) {
         __syncthreads();
-        for (int e = threadIdx.x; e < N * KP; e += blockDim.x) {
-            const int n = e / KP, k = e % KP;
-            if (k >= Kreal) continue;
-            float v = red[n * KP + k];
-            for (int s = 1; s < SPLIT; ++s) v += red[(s * N + n) * KP + k];
-            g[n * Kreal + k] = v;
+        // four elements per thread per pass: their old values load together
+        constexpr int NE = N * KP;
+        for (int e0 = threadIdx.x; e0 < NE; e0 += 4 * blockDim.x) {
+            float v[4], old[4];
+            int idx[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = e0 + u * blockDim.x;
+                const int n = e / KP, k = e % KP;
+                idx[u] = (e < NE && k < Kreal) ? n * Kreal + k : -1;
+                old[u] = (!first && idx[u] >= 0) ? g[idx[u]] : 0.f;
+                float s_ = 0.f;
+                if (idx[u] >= 0) {
+                    s_ = red[n * KP + k];
+                    for (int s = 1; s < SPLIT; ++s) s_ += red[(s * N + n) * KP + k];
+                }
+                v[u] = s_;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (idx[u] >= 0) g[idx[u]] = v[u] + old[u];
         }
     }
 }
@@ -202,17 +239,34 @@ __device__ __forceinline__ void stage_w1_rows(float* dst, const float* __restric
     }
 }
 
+// Gaussian encoding of the tile's points: rows 0..2 of g hold x~ on entry;
+// rows 3..47 get sin(B x~), rows 48..92 cos(B x~), rows 93..95 zero.
+template <int LD>
+__device__ __forceinline__ void encode(const StepParams& sp, float* g, int Mpad) {
+    for (int f = threadIdx.x; f < NF * Mpad; f += blockDim.x) {
+        const int j = f / Mpad, m = f - j * Mpad;
+        const float p = fmaf(sp.B[3 * j + 2], g[2 * LD + m],
+                             fmaf(sp.B[3 * j + 1], g[1 * LD + m], sp.B[3 * j] * g[0 * LD + m]));
+        float s, c;
+        sincosf(p, &s, &c);
+        g[(3 + j) * LD + m] = s;
+        g[(3 + NF + j) * LD + m] = c;
+    }
+    for (int i = threadIdx.x; i < 3 * Mpad; i += blockDim.x) g[(DIN + i / Mpad) * LD + (i % Mpad)] = 0.f;
+}
+
 struct TileArgs {
     const ObjDev* objs;
-    const TileDev* tiles;
-    int tile_begin;
+    const ObjBatch* obs;
+    const TileDev* tiles;     // this class's tiles
+    const int* n_tiles;       // device count of this class's tiles
     const float* pool;        // ray source: pool arena, the batch staging buffer, or
                               // (MODE_EVAL) the caller's rays
-    const int* pick;          // batch ray -> pool index (NULL in MODE_EVAL)
+    const int* pick;          // batch ray -> source index
     const float* tbuf;        // batch sample depths
     const float* params;      // canonical parameter arena
     const float* wt;          // transposed-weight arena
-    float* part;              // per-tile partials
+    float* part;              // run partial slots
     float* eval_out;          // MODE_EVAL: rendered depth per ray
     float eval_half[3];       // MODE_EVAL: box half extents
     int eval_obj;             // MODE_EVAL / MODE_QUERY: the object
@@ -223,271 +277,342 @@ struct TileArgs {
     float* qrgb;              // MODE_QUERY: colour [n][3] or NULL
 };
 
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    return v;
+}
+
+// Render one ray per warp (lane i = sample i, S <= 32): forward Eq. 3, the
+// ray's loss terms, and (GRAD) dL/dy for its samples. The exclusive product
+// P_i = prod_{j<i}(1 - o_j) is a multiplicative scan; the reverse recursion
+// S_i = o_i g_i + (1 - o_i) S_{i+1} is a suffix scan of affine maps
+// x -> (1 - o_i) x + o_i g_i (no division by 1 - o_i anywhere).
+template <bool GRAD, int LD>
+__device__ __forceinline__ void render_ray_warp(const StepParams& sp, float* yb, const float* tsm,
+                                                float* d, int r, int S, float invR) {
+    const int i = threadIdx.x & 31;
+    const bool v = i < S;
+    const int m = r * S + i;
+    float o = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, t = 0.f;
+    if (v) {
+        o = sigmoidf_(yb[m]);
+        c0 = sigmoidf_(yb[LD + m]);
+        c1 = sigmoidf_(yb[2 * LD + m]);
+        c2 = sigmoidf_(yb[3 * LD + m]);
+        t = tsm[m];
+    }
+    float incl = v ? 1.f - o : 1.f;
+#pragma unroll
+    for (int s = 1; s < 32; s <<= 1) {
+        const float u = __shfl_up_sync(0xffffffffu, incl, s);
+        if (i >= s) incl *= u;
+    }
+    float P = __shfl_up_sync(0xffffffffu, incl, 1);
+    if (i == 0) P = 1.f;
+    const float T = o * P;
+    const float Oh = warp_sum(T), Dh = warp_sum(T * t);
+    const float C0 = warp_sum(T * c0), C1 = warp_sum(T * c1), C2 = warp_sum(T * c2);
+    const float D = d[6], Msk = d[10];
+    const float wD = D > 0.f ? Msk : 0.f;
+    const float eD = Dh - D, e0 = C0 - d[7], e1 = C1 - d[8], e2 = C2 - d[9], eO = Oh - Msk;
+    if (i == 0) {
+        d[13] = wD * fabsf(eD);
+        d[14] = Msk * ((fabsf(e0) + fabsf(e1)) + fabsf(e2));
+        d[15] = fabsf(eO);
+    }
+    if (!GRAD) return;
+    const float a = wD * signf_(eD) * invR;
+    const float bsc = sp.lam_c * Msk * invR / 3.f;
+    const float b0 = bsc * signf_(e0), b1 = bsc * signf_(e1), b2 = bsc * signf_(e2);
+    const float e = sp.lam_o * signf_(eO) * invR;
+    const float gi = fmaf(a, t, fmaf(b0, c0, fmaf(b1, c1, b2 * c2))) + e;
+    float al = v ? 1.f - o : 1.f, be = v ? o * gi : 0.f;
+#pragma unroll
+    for (int s = 1; s < 32; s <<= 1) {
+        const float a2 = __shfl_down_sync(0xffffffffu, al, s);
+        const float b2_ = __shfl_down_sync(0xffffffffu, be, s);
+        if (i + s < 32) {
+            be = fmaf(al, b2_, be);
+            al = al * a2;
+        }
+    }
+    float Sn = __shfl_down_sync(0xffffffffu, be, 1);
+    if (i == 31) Sn = 0.f;
+    if (v) {
+        const float dLdo = P * (gi - Sn);
+        yb[m] = dLdo * o * (1.f - o);
+        yb[LD + m] = T * b0 * c0 * (1.f - c0);
+        yb[2 * LD + m] = T * b1 * c1 * (1.f - c1);
+        yb[3 * LD + m] = T * b2 * c2 * (1.f - c2);
+    }
+}
+
 template <int H, int MODE>
-__global__ void __launch_bounds__(NTHREADS, 1) k_tile_fp32(StepParams sp, TileArgs ta) {
+__global__ void __launch_bounds__(NTHREADS, TileCfg<H>::CTAS) k_tile_fp32(StepParams sp, TileArgs ta) {
     using SM = TileSmem<H>;
     constexpr int LD = SM::LD;
+    constexpr bool TRAINISH = MODE == MODE_TRAIN || MODE == MODE_FORWARD || MODE == MODE_GRAD_CENTER;
+    constexpr bool GRAD = MODE == MODE_TRAIN || MODE == MODE_GRAD_CENTER;
     extern __shared__ __align__(16) float smem[];
-    float* g = smem + SM::G;
     float* act = smem + SM::ACT;
+    float* g = smem + SM::G;
     float* yb = smem + SM::Y;
     float* ws = smem + SM::W;
     float* red = smem + SM::RED;
-    float* ps = smem + SM::PS;
     float* tsm = smem + SM::TS;
     float* rays = smem + SM::RAYS;
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
 
-    // ---- the tile ---------------------------------------------------------
-    int k, nr, S;
-    long long sbase = 0, part = 0;
-    long long ray_first;
-    if (MODE == MODE_EVAL || MODE == MODE_QUERY) {
-        k = ta.eval_obj;
-        S = MODE == MODE_EVAL ? ta.eval_S : 1;
-        const int rt = SM::MMAX / S;
-        ray_first = (long long)blockIdx.x * rt;
-        nr = (int)min((long long)rt, ta.eval_n - ray_first);
+    long long t0, t1;
+    if (TRAINISH) {
+        const long long n = *ta.n_tiles;
+        t0 = (long long)blockIdx.x * n / gridDim.x;
+        t1 = (long long)(blockIdx.x + 1) * n / gridDim.x;
     } else {
-        const TileDev td = ta.tiles[ta.tile_begin + blockIdx.x];
-        k = td.obj;
-        nr = td.nr;
-        ray_first = td.ray0;
-        part = td.part;
-        S = ta.objs[k].S;
-        sbase = ta.objs[k].sample_off + (long long)(td.ray0 - ta.objs[k].ray_off) * S;
+        t0 = blockIdx.x;
+        t1 = t0 + 1;
     }
-    const ObjDev& ob = ta.objs[k];
-    const int M = nr * S;
-    const int Mpad = (M + 7) & ~7;
-    const float* P = ta.params + ob.param_off;
-    const float* WT = ta.wt + ob.wt_off;
-    const float cx = ob.c[0], cy = ob.c[1], cz = ob.c[2], sc = ob.scale;
-
-    // ---- rays into smem ---------------------------------------------------
-    for (int r = threadIdx.x; r < nr && MODE != MODE_QUERY; r += blockDim.x) {
-        const float* rec;
-        if (MODE == MODE_EVAL) rec = ta.pool + (ray_first + r) * REC;
-        else rec = ta.pool + (ob.src_off + ta.pick[ray_first + r]) * REC;
-        float* d = rays + r * RAYF;
-#pragma unroll
-        for (int q = 0; q < 11; ++q) d[q] = rec[q];
-        if (MODE == MODE_EVAL) {
-            // ray-box entry / exit (slab method) against c_k +- half
-            float tn = 0.f, tf = 3.0e38f;
-#pragma unroll
-            for (int ax = 0; ax < 3; ++ax) {
-                const float o = d[ax], dir = d[3 + ax];
-                const float lo = ob.c[ax] - ta.eval_half[ax], hi = ob.c[ax] + ta.eval_half[ax];
-                if (dir != 0.f) {
-                    float t1 = (lo - o) / dir, t2 = (hi - o) / dir;
-                    tn = fmaxf(tn, fminf(t1, t2));
-                    tf = fminf(tf, fmaxf(t1, t2));
-                } else if (o < lo || o > hi) {
-                    tf = -1.f;
-                }
-            }
-            d[11] = tn;
-            d[12] = tf;
-        }
-    }
-    __syncthreads();
-
-    // ---- points x~ = (o + t d - c) / s ------------------------------------
-    for (int m = threadIdx.x; m < Mpad; m += blockDim.x) {
-        float x0 = 0.f, x1 = 0.f, x2 = 0.f;
-        if (m < M) {
-            const int r = m / S, i = m - r * S;
-            const float* d = rays + r * RAYF;
-            if (MODE == MODE_QUERY) {
-                const float* q = ta.qpts + (ray_first + m) * 3;
-                x0 = (q[0] - cx) / sc;
-                x1 = (q[1] - cy) / sc;
-                x2 = (q[2] - cz) / sc;
-            } else {
-                float t;
-                if (MODE == MODE_EVAL) t = d[11] + ((float)i + 0.5f) / (float)S * (d[12] - d[11]);
-                else t = ta.tbuf[sbase + m];
-                tsm[m] = t;
-                x0 = (fmaf(t, d[3], d[0]) - cx) / sc;
-                x1 = (fmaf(t, d[4], d[1]) - cy) / sc;
-                x2 = (fmaf(t, d[5], d[2]) - cz) / sc;
-            }
-        }
-        if (m >= M) tsm[m] = 0.f;
-        g[0 * LD + m] = x0;
-        g[1 * LD + m] = x1;
-        g[2 * LD + m] = x2;
-    }
-    for (int i = threadIdx.x; i < 3 * LD; i += blockDim.x) g[(DIN + i / LD) * LD + (i % LD)] = 0.f;
-    __syncthreads();
-    // ---- Gaussian encoding: sin / cos of B x~ --------------------------------
-    for (int f = threadIdx.x; f < NF * Mpad; f += blockDim.x) {
-        const int j = f / Mpad, m = f - j * Mpad;
-        const float p = fmaf(sp.B[3 * j + 2], g[2 * LD + m],
-                             fmaf(sp.B[3 * j + 1], g[1 * LD + m], sp.B[3 * j] * g[0 * LD + m]));
-        float s, c;
-        sincosf(p, &s, &c);
-        g[(3 + j) * LD + m] = s;
-        g[(3 + NF + j) * LD + m] = c;
-    }
-    // layer-1 weights (transposed [96][H])
-    stage(ws, WT + wt_layer_off(H, 0), DINP * H);
-    __syncthreads();
-
-    // ---- forward ----------------------------------------------------------
-    float* h[4] = {act, act + H * LD, act + 2 * H * LD, act + 3 * H * LD};
-    gemm_fwd<H, DINP, 0>(g, LD, ws, P + b_off(H, 0), h[0], LD, Mpad);
-    __syncthreads();
 #pragma unroll 1
-    for (int l = 1; l < 4; ++l) {
-        stage(ws, WT + wt_layer_off(H, l), H * H);
-        __syncthreads();
-        gemm_fwd<H, H, 0>(h[l - 1], LD, ws, P + b_off(H, l), h[l], LD, Mpad);
-        __syncthreads();
-    }
-    stage(ws, WT + wt_layer_off(H, 4), H * NOUT);
-    __syncthreads();
-    gemm_fwd<NOUT, H, 1>(h[3], LD, ws, P + b_off(H, 4), yb, LD, Mpad);
-    __syncthreads();
-    if (MODE == MODE_QUERY) {
-        for (int m = threadIdx.x; m < M; m += blockDim.x) {
-            const long long q = ray_first + m;
-            ta.qocc[q] = sigmoidf_(yb[m]);
-            if (ta.qrgb) {
-                ta.qrgb[3 * q + 0] = sigmoidf_(yb[LD + m]);
-                ta.qrgb[3 * q + 1] = sigmoidf_(yb[2 * LD + m]);
-                ta.qrgb[3 * q + 2] = sigmoidf_(yb[3 * LD + m]);
-            }
-        }
-        return;
-    }
-
-    // ---- rendering (Eq. 3), losses (Eq. 4-5) and their gradient ---------------
-    // one thread per ray; padded samples get zero gradient
-    float* rsum = rays;   // per ray results reuse the ray scratch: [r*RAYF + 13..15]
-    if (threadIdx.x < nr) {
-        const int r = threadIdx.x;
-        float* d = rays + r * RAYF;
-        float Pr = 1.f, Oh = 0.f, Dh = 0.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-        for (int i = 0; i < S; ++i) {
-            const int m = r * S + i;
-            const float o = sigmoidf_(yb[m]);
-            const float c0 = sigmoidf_(yb[LD + m]), c1 = sigmoidf_(yb[2 * LD + m]), c2 = sigmoidf_(yb[3 * LD + m]);
-            const float T = o * Pr;
-            Oh += T;
-            Dh = fmaf(T, tsm[m], Dh);
-            C0 = fmaf(T, c0, C0); C1 = fmaf(T, c1, C1); C2 = fmaf(T, c2, C2);
-            ps[m] = Pr;
-            yb[m] = o; yb[LD + m] = c0; yb[2 * LD + m] = c1; yb[3 * LD + m] = c2;
-            Pr = Pr * (1.f - o);
-        }
-        if (MODE == MODE_EVAL) {
-            const bool hit = d[12] > d[11] && d[12] > 0.f;
-            ta.eval_out[ray_first + r] = hit ? Dh : 0.f;
+    for (long long tl = t0; tl < t1; ++tl) {
+        // ---- the tile -----------------------------------------------------
+        int k, nr, S;
+        long long sbase = 0, part = 0, ray_first;
+        bool first = true;
+        if (MODE == MODE_EVAL || MODE == MODE_QUERY) {
+            k = ta.eval_obj;
+            S = MODE == MODE_EVAL ? ta.eval_S : 1;
+            const int rt = MODE == MODE_EVAL ? min(RTMAX, SM::MMAX / S) : SM::MMAX;
+            ray_first = tl * rt;
+            nr = (int)min((long long)rt, ta.eval_n - ray_first);
         } else {
-            const float D = d[6], Msk = d[10];
-            const float valid = D > 0.f ? 1.f : 0.f;
-            const float wD = Msk * valid;
-            const float eD = Dh - D, e0 = C0 - d[7], e1 = C1 - d[8], e2 = C2 - d[9], eO = Oh - Msk;
-            d[13] = wD * fabsf(eD);
-            d[14] = Msk * ((fabsf(e0) + fabsf(e1)) + fabsf(e2));
-            d[15] = fabsf(eO);
-            if (MODE != MODE_FORWARD) {
-                const float invR = 1.f / (float)ob.R;
-                const float a = wD * signf_(eD) * invR;
-                const float bsc = sp.lam_c * Msk * invR / 3.f;
-                const float b0 = bsc * signf_(e0), b1 = bsc * signf_(e1), b2 = bsc * signf_(e2);
-                const float e = sp.lam_o * signf_(eO) * invR;
-                float Sn = 0.f;
-                for (int i = S - 1; i >= 0; --i) {
-                    const int m = r * S + i;
-                    const float o = yb[m], c0 = yb[LD + m], c1 = yb[2 * LD + m], c2 = yb[3 * LD + m];
-                    const float gi = fmaf(a, tsm[m], fmaf(b0, c0, fmaf(b1, c1, b2 * c2))) + e;
-                    const float Pi = ps[m];
-                    const float dLdo = Pi * (gi - Sn);
-                    Sn = fmaf(o, gi, (1.f - o) * Sn);
-                    const float T = o * Pi;
-                    yb[m] = dLdo * o * (1.f - o);
-                    yb[LD + m] = T * b0 * c0 * (1.f - c0);
-                    yb[2 * LD + m] = T * b1 * c1 * (1.f - c1);
-                    yb[3 * LD + m] = T * b2 * c2 * (1.f - c2);
-                }
-            }
+            const TileDev td = ta.tiles[tl];
+            k = td.obj;
+            nr = td.nr;
+            ray_first = td.ray0;
+            part = td.part;
+            S = ta.objs[k].S;
+            sbase = ta.obs[k].sample_off + (long long)(td.ray0 - ta.obs[k].ray_off) * S;
+            first = tl == t0 || ta.tiles[tl - 1].obj != k;
         }
-    }
-    if (MODE == MODE_EVAL) return;
-    // zero the gradient of padded samples
-    for (int m = M + threadIdx.x; m < Mpad; m += blockDim.x) {
-        yb[m] = 0.f; yb[LD + m] = 0.f; yb[2 * LD + m] = 0.f; yb[3 * LD + m] = 0.f;
-    }
-    __syncthreads();
-    float* gp = ta.part + part;   // this tile's partial slot
-    if (threadIdx.x == 0) {
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-        for (int r = 0; r < nr; ++r) { s0 += rsum[r * RAYF + 13]; s1 += rsum[r * RAYF + 14]; s2 += rsum[r * RAYF + 15]; }
-        const long long P_ = param_count(H);
-        gp[P_ + 0] = s0; gp[P_ + 1] = s1; gp[P_ + 2] = s2;
-        gp[P_ + 3] = 0.f; gp[P_ + 4] = 0.f; gp[P_ + 5] = 0.f;
-    }
-    if (MODE == MODE_FORWARD) return;
+        const ObjDev& ob = ta.objs[k];
+        const int M = nr * S;
+        const int Mpad = (M + 7) & ~7;
+        const float* P = ta.params + ob.param_off;
+        const float* WT = ta.wt + ob.wt_off;
+        const float cx = ob.c[0], cy = ob.c[1], cz = ob.c[2], sc = ob.scale;
 
-    // ---- backward ----------------------------------------------------------
-    // layer 5: dW5 = dY^T h4, dZ4 = (dY W5) * [h4 > 0]
-    gemm_dw<NOUT, H>(yb, h[3], LD, Mpad, red, gp + w_off(H, 4), H, gp + b_off(H, 4));
-    stage(ws, P + w_off(H, 4), NOUT * H);     // W5 [4][H] == B[k=out][n=in]
-    __syncthreads();
-    gemm_fwd<H, NOUT, 2>(yb, LD, ws, nullptr, h[3], LD, Mpad);
-    __syncthreads();
-#pragma unroll 1
-    for (int l = 3; l >= 1; --l) {
-        // dW_{l+1} = dZ_{l+1}^T h_l ; dZ_l = (dZ_{l+1} W_{l+1}) * [h_l > 0]
-        gemm_dw<H, H>(h[l], h[l - 1], LD, Mpad, red, gp + w_off(H, l), H, gp + b_off(H, l));
-        stage(ws, P + w_off(H, l), H * H);
-        __syncthreads();
-        gemm_fwd<H, H, 2>(h[l], LD, ws, nullptr, h[l - 1], LD, Mpad);
-        __syncthreads();
-    }
-    // layer 1: dW1 = dZ1^T gamma
-    gemm_dw<H, DINP>(h[0], g, LD, Mpad, red, gp + w_off(H, 0), DIN, gp + b_off(H, 0));
-    if (MODE == MODE_GRAD_CENTER) {
-        // encoding backward, one thread per sample:
-        //   dgamma_j = sum_n dZ1[n] W1[n][j]
-        //   dx~ = dgamma_xyz + sum_j B_j (cos_j dgamma_sin_j - sin_j dgamma_cos_j)
-        //   dL/dc = -sum_samples dx~ / s
-        __syncthreads();
-        stage_w1_rows<H>(ws, P + w_off(H, 0));
-        __syncthreads();
-        float* acc3 = yb;  // [3][LD], free after the layer-5 backward
-        for (int m = threadIdx.x; m < Mpad; m += blockDim.x) {
-            float d0 = 0.f, d1 = 0.f, d2 = 0.f;
-            if (m < M) {
-                for (int n = 0; n < H; ++n) {
-                    const float z = h[0][n * LD + m];
-                    d0 = fmaf(z, ws[n * DINP + 0], d0);
-                    d1 = fmaf(z, ws[n * DINP + 1], d1);
-                    d2 = fmaf(z, ws[n * DINP + 2], d2);
-                }
-                for (int j = 0; j < NF; ++j) {
-                    float ds = 0.f, dc = 0.f;
-                    for (int n = 0; n < H; ++n) {
-                        const float z = h[0][n * LD + m];
-                        ds = fmaf(z, ws[n * DINP + 3 + j], ds);
-                        dc = fmaf(z, ws[n * DINP + 3 + NF + j], dc);
+        // ---- rays into smem -----------------------------------------------
+        if (MODE != MODE_QUERY) {
+            for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+                const float* rec;
+                if (MODE == MODE_EVAL) rec = ta.pool + (ray_first + r) * REC;
+                else rec = ta.pool + (ta.obs[k].src_off + ta.pick[ray_first + r]) * REC;
+                float* d = rays + r * RAYF;
+#pragma unroll
+                for (int q = 0; q < 11; ++q) d[q] = rec[q];
+                if (MODE == MODE_EVAL) {
+                    // ray-box entry / exit (slab method) against c_k +- half
+                    float tn = 0.f, tf = 3.0e38f;
+#pragma unroll
+                    for (int ax = 0; ax < 3; ++ax) {
+                        const float o = d[ax], dir = d[3 + ax];
+                        const float lo = ob.c[ax] - ta.eval_half[ax], hi = ob.c[ax] + ta.eval_half[ax];
+                        if (dir != 0.f) {
+                            const float u1 = (lo - o) / dir, u2 = (hi - o) / dir;
+                            tn = fmaxf(tn, fminf(u1, u2));
+                            tf = fminf(tf, fmaxf(u1, u2));
+                        } else if (o < lo || o > hi) {
+                            tf = -1.f;
+                        }
                     }
-                    const float w = ds * g[(3 + NF + j) * LD + m] - dc * g[(3 + j) * LD + m];
-                    d0 = fmaf(w, sp.B[3 * j], d0);
-                    d1 = fmaf(w, sp.B[3 * j + 1], d1);
-                    d2 = fmaf(w, sp.B[3 * j + 2], d2);
+                    d[11] = tn;
+                    d[12] = tf;
                 }
             }
-            acc3[m] = d0; acc3[LD + m] = d1; acc3[2 * LD + m] = d2;
+            __syncthreads();
+        }
+
+        // ---- points x~ = (o + t d - c) / s ----------------------------------
+        for (int m = threadIdx.x; m < Mpad; m += blockDim.x) {
+            float x0 = 0.f, x1 = 0.f, x2 = 0.f, t = 0.f;
+            if (m < M) {
+                if (MODE == MODE_QUERY) {
+                    const float* q = ta.qpts + (ray_first + m) * 3;
+                    x0 = (q[0] - cx) / sc;
+                    x1 = (q[1] - cy) / sc;
+                    x2 = (q[2] - cz) / sc;
+                } else {
+                    const int r = m / S, i = m - r * S;
+                    const float* d = rays + r * RAYF;
+                    if (MODE == MODE_EVAL) t = d[11] + ((float)i + 0.5f) / (float)S * (d[12] - d[11]);
+                    else t = ta.tbuf[sbase + m];
+                    x0 = (fmaf(t, d[3], d[0]) - cx) / sc;
+                    x1 = (fmaf(t, d[4], d[1]) - cy) / sc;
+                    x2 = (fmaf(t, d[5], d[2]) - cz) / sc;
+                }
+            }
+            tsm[m] = t;
+            g[0 * LD + m] = x0;
+            g[1 * LD + m] = x1;
+            g[2 * LD + m] = x2;
         }
         __syncthreads();
-        if (threadIdx.x < 3) {
-            float s = 0.f;
-            for (int m = 0; m < M; ++m) s += acc3[threadIdx.x * LD + m];
-            gp[param_count(H) + 3 + threadIdx.x] = -s / sc;
+        encode<LD>(sp, g, Mpad);
+        stage(ws, WT + wt_layer_off(H, 0), DINP * H);   // W1^T [96][H]
+        __syncthreads();
+
+        // ---- forward --------------------------------------------------------
+        gemm_fwd<H, DINP, 0>(g, LD, ws, P + b_off(H, 0), act, LD, Mpad);
+        __syncthreads();
+#pragma unroll 1
+        for (int l = 1; l < 4; ++l) {
+            stage(ws, WT + wt_layer_off(H, l), H * H);
+            __syncthreads();
+            gemm_fwd<H, H, 0>(act + (l - 1) * H * LD, LD, ws, P + b_off(H, l), act + l * H * LD, LD, Mpad);
+            __syncthreads();
         }
+        stage(ws, WT + wt_layer_off(H, 4), H * NOUT);
+        __syncthreads();
+        gemm_fwd<NOUT, H, 1>(act + 3 * H * LD, LD, ws, P + b_off(H, 4), yb, LD, Mpad);
+        __syncthreads();
+        if (MODE == MODE_QUERY) {
+            for (int m = threadIdx.x; m < M; m += blockDim.x) {
+                const long long q = ray_first + m;
+                ta.qocc[q] = sigmoidf_(yb[m]);
+                if (ta.qrgb) {
+                    ta.qrgb[3 * q + 0] = sigmoidf_(yb[LD + m]);
+                    ta.qrgb[3 * q + 1] = sigmoidf_(yb[2 * LD + m]);
+                    ta.qrgb[3 * q + 2] = sigmoidf_(yb[3 * LD + m]);
+                }
+            }
+            continue;
+        }
+
+        // ---- rendering (Eq. 3), losses (Eq. 4-5) and their gradient -----------
+        if (MODE == MODE_EVAL) {
+            // S may exceed 32 here: one thread per ray, sequential
+            if (threadIdx.x < nr) {
+                const int r = threadIdx.x;
+                const float* d = rays + r * RAYF;
+                float Pr = 1.f, Dh = 0.f;
+                for (int i = 0; i < S; ++i) {
+                    const int m = r * S + i;
+                    const float o = sigmoidf_(yb[m]);
+                    Dh = fmaf(o * Pr, tsm[m], Dh);
+                    Pr = Pr * (1.f - o);
+                }
+                const bool hit = d[12] > d[11] && d[12] > 0.f;
+                ta.eval_out[ray_first + r] = hit ? Dh : 0.f;
+            }
+            continue;
+        }
+        const float invR = 1.f / (float)ta.obs[k].R;
+        for (int r = warp; r < nr; r += nwarps)
+            render_ray_warp<GRAD, LD>(sp, yb, tsm, rays + r * RAYF, r, S, invR);
+        // padded samples carry no gradient
+        for (int m = M + threadIdx.x; m < Mpad; m += blockDim.x) {
+            yb[m] = 0.f; yb[LD + m] = 0.f; yb[2 * LD + m] = 0.f; yb[3 * LD + m] = 0.f;
+        }
+        __syncthreads();
+        float* gp = ta.part + part;   // this run's slot
+        constexpr long long PC = param_count(H);
+        if (threadIdx.x == 0) {
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+            for (int r = 0; r < nr; ++r) {
+                s0 += rays[r * RAYF + 13]; s1 += rays[r * RAYF + 14]; s2 += rays[r * RAYF + 15];
+            }
+            acc_store(gp + PC + 0, s0, first);
+            acc_store(gp + PC + 1, s1, first);
+            acc_store(gp + PC + 2, s2, first);
+            if (first) { gp[PC + 3] = 0.f; gp[PC + 4] = 0.f; gp[PC + 5] = 0.f; }
+        }
+        if (MODE == MODE_FORWARD) {
+            __syncthreads();
+            continue;
+        }
+
+        // ---- backward -------------------------------------------------------
+        // layer 5: dW5 = dY^T h4, dZ4 = (dY W5) * [h4 > 0]
+        gemm_dw<NOUT, H>(yb, act + 3 * H * LD, LD, Mpad, red, gp + w_off(H, 4), H, gp + b_off(H, 4), first);
+        stage(ws, P + w_off(H, 4), NOUT * H);     // W5 [4][H] == B[k=out][n=in]
+        __syncthreads();
+        gemm_fwd<H, NOUT, 2>(yb, LD, ws, nullptr, act + 3 * H * LD, LD, Mpad);
+        __syncthreads();
+#pragma unroll 1
+        for (int l = 3; l >= 1; --l) {
+            // dW_{l+1} = dZ_{l+1}^T h_l ; dZ_l = (dZ_{l+1} W_{l+1}) * [h_l > 0]
+            float* hz = act + l * H * LD;
+            float* ha = act + (l - 1) * H * LD;
+            gemm_dw<H, H>(hz, ha, LD, Mpad, red, gp + w_off(H, l), H, gp + b_off(H, l), first);
+            stage(ws, P + w_off(H, l), H * H);
+            __syncthreads();
+            gemm_fwd<H, H, 2>(hz, LD, ws, nullptr, ha, LD, Mpad);
+            __syncthreads();
+        }
+        if (!SM::GSEP) {
+            // the encoding was overwritten by hidden layers 2-4: recompute it
+            for (int m = threadIdx.x; m < Mpad; m += blockDim.x) {
+                float x0 = 0.f, x1 = 0.f, x2 = 0.f;
+                if (m < M) {
+                    const int r = m / S;
+                    const float* d = rays + r * RAYF;
+                    const float t = tsm[m];
+                    x0 = (fmaf(t, d[3], d[0]) - cx) / sc;
+                    x1 = (fmaf(t, d[4], d[1]) - cy) / sc;
+                    x2 = (fmaf(t, d[5], d[2]) - cz) / sc;
+                }
+                g[0 * LD + m] = x0;
+                g[1 * LD + m] = x1;
+                g[2 * LD + m] = x2;
+            }
+            __syncthreads();
+            encode<LD>(sp, g, Mpad);
+            __syncthreads();
+        }
+        // layer 1: dW1 = dZ1^T gamma
+        gemm_dw<H, DINP>(act, g, LD, Mpad, red, gp + w_off(H, 0), DIN, gp + b_off(H, 0), first);
+        if (MODE == MODE_GRAD_CENTER) {
+            // encoding backward, one thread per sample:
+            //   dgamma_j = sum_n dZ1[n] W1[n][j]
+            //   dx~ = dgamma_xyz + sum_j B_j (cos_j dgamma_sin_j - sin_j dgamma_cos_j)
+            //   dL/dc = -sum_samples dx~ / s
+            __syncthreads();
+            stage_w1_rows<H>(ws, P + w_off(H, 0));
+            __syncthreads();
+            float* acc3 = yb;  // [3][LD], free after the layer-5 backward
+            for (int m = threadIdx.x; m < Mpad; m += blockDim.x) {
+                float d0 = 0.f, d1 = 0.f, d2 = 0.f;
+                if (m < M) {
+                    for (int n = 0; n < H; ++n) {
+                        const float z = act[n * LD + m];
+                        d0 = fmaf(z, ws[n * DINP + 0], d0);
+                        d1 = fmaf(z, ws[n * DINP + 1], d1);
+                        d2 = fmaf(z, ws[n * DINP + 2], d2);
+                    }
+                    for (int j = 0; j < NF; ++j) {
+                        float ds = 0.f, dc = 0.f;
+                        for (int n = 0; n < H; ++n) {
+                            const float z = act[n * LD + m];
+                            ds = fmaf(z, ws[n * DINP + 3 + j], ds);
+                            dc = fmaf(z, ws[n * DINP + 3 + NF + j], dc);
+                        }
+                        const float w = ds * g[(3 + NF + j) * LD + m] - dc * g[(3 + j) * LD + m];
+                        d0 = fmaf(w, sp.B[3 * j], d0);
+                        d1 = fmaf(w, sp.B[3 * j + 1], d1);
+                        d2 = fmaf(w, sp.B[3 * j + 2], d2);
+                    }
+                }
+                acc3[m] = d0; acc3[LD + m] = d1; acc3[2 * LD + m] = d2;
+            }
+            __syncthreads();
+            if (threadIdx.x < 3) {
+                float s = 0.f;
+                for (int m = 0; m < M; ++m) s += acc3[threadIdx.x * LD + m];
+                gp[PC + 3 + threadIdx.x] += -s / sc;
+            }
+        }
+        __syncthreads();
     }
 }
 

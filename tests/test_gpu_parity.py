@@ -184,8 +184,13 @@ def test_query_and_render_depth_match_oracle():
     vm.query_occupancy(0, torch.empty(0, 3, device="cuda"), torch.empty(0, device="cuda"))
 
 
-def test_together_equals_separate_bitwise():
-    """The paper's independence: N objects trained together = N separate runs."""
+def test_together_equals_separate():
+    """The paper's independence: N objects trained together = N separate runs.
+
+    The forward values and gradients of an object do not depend on the other
+    objects; only the order in which its tile gradients are added can (the
+    persistent CTAs split the batch differently), so the comparison is at
+    FP32 summation-order tolerance."""
     sc = vh.mixed_scene(seed=15)
     R = [o["rays"] for o in sc["objects"]]
     vm = vh.library_context(sc)
@@ -207,8 +212,10 @@ def test_together_equals_separate_bitwise():
         for s in range(3):
             vs1.sample_rays([R[k]])
             vs1.train_step(l1)
-            assert l1.item() == hist[s][k].item()
-        assert torch.equal(vs1.get_object_state(0)[0], vm.get_object_state(k)[0])
+            assert abs(l1.item() - hist[s][k].item()) <= 1e-6 * abs(hist[s][k].item())
+        errs = vh.layer_errors(vs1.get_object_state(0)[0].cpu().numpy(),
+                               vm.get_object_state(k)[0].cpu().numpy().astype(np.float64), o["H"])
+        assert max(errs) <= W_RTOL, errs
 
 
 def test_nonfinite_object_is_frozen_and_others_unaffected():
@@ -232,8 +239,10 @@ def test_nonfinite_object_is_frozen_and_others_unaffected():
     p, m, v, st = bad.get_object_state(1)
     assert st == 0 and torch.equal(p, p_before)
     for k in (0, 2):
-        assert lr_[k].item() == lb[k].item()
-        assert torch.equal(ref.get_object_state(k)[0], bad.get_object_state(k)[0])
+        assert abs(lr_[k].item() - lb[k].item()) <= 1e-6 * abs(lr_[k].item())
+        errs = vh.layer_errors(bad.get_object_state(k)[0].cpu().numpy(),
+                               ref.get_object_state(k)[0].cpu().numpy().astype(np.float64), 32)
+        assert max(errs) <= W_RTOL, errs
 
 
 def test_checkpoint_resume_is_bitwise():
@@ -374,3 +383,91 @@ def test_given_rays_and_host_step_match_oracle():
         assert np.all(np.abs(Ld[ok] - Lo[ok]) <= LOSS_RTOL * np.abs(Lo[ok]))
     for k in range(K):
         assert torch.equal(dev.get_object_state(k)[0], host.get_object_state(k)[0])
+
+
+def _train(vm, R, steps):
+    K = len(R)
+    out = []
+    loss = torch.empty(K, device="cuda")
+    for _ in range(steps):
+        vm.sample_rays(R)
+        vm.train_step(loss)
+        out.append(loss.clone())
+    return out
+
+
+def test_graph_replay_matches_eager_launches_bitwise():
+    """CUDA-graph replay runs the same kernels on the same device-built batch."""
+    sc = vh.mixed_scene(seed=18)
+    R = [o["rays"] for o in sc["objects"]]
+    a = vh.library_context(sc)
+    b = vh.library_context(sc)
+    b.set_graph(True)
+    la, lb = _train(a, R, 4), _train(b, R, 4)
+    for x, y in zip(la, lb):
+        assert torch.equal(x, y)
+    assert torch.equal(a.get_params(), b.get_params())
+
+
+def test_admission_mid_run_in_graph_mode():
+    """Objects added between graph replays are trained by the captured step
+    (no re-capture needed for a width class already present); an object that
+    joins late follows the same trajectory as the same object trained from
+    step 0 in a context of its own."""
+    sc = vh.mixed_scene(seed=19)
+    objs = sc["objects"]
+    R = [o["rays"] for o in objs]
+    from paper_2302_01838_b300.api import VMap
+    vm = VMap(max_objects=len(objs) + 2, max_rays_total=4 * sum(R),
+              max_pool_rays=sum(o["pool"].shape[0] for o in objs) + 8, B=sc["B"], seed=sc["seed"])
+    vm.set_graph(True)
+
+    def add(k):
+        o = objs[k]
+        return vm.add_object(o["pool"], hidden=o["H"], center=o["center"], scale=float(o["scale"]),
+                             n_surface=o["n_surface"], n_strat=o["n_strat"], init_params=o["init"],
+                             stream_id=k)
+    ids = [add(k) for k in range(4)]             # every width class is present from the start
+    late = []
+    for step in range(6):
+        if step in (2, 4):
+            late.append((add(4 + len(late)), step))
+        n = vm.num_objects()
+        vm.sample_rays([R[k] for k in range(n)])
+        vm.train_step()
+    for oid, start in late:
+        p, _, _, st = vm.get_object_state(oid)
+        assert st == 6 - start
+        one = dict(objects=[objs[oid]], B=sc["B"], seed=sc["seed"])
+        ref = VMap(max_objects=2, max_rays_total=4096, max_pool_rays=objs[oid]["pool"].shape[0] + 8,
+                   B=sc["B"], seed=sc["seed"])
+        o = objs[oid]
+        ref.add_object(o["pool"], hidden=o["H"], center=o["center"], scale=float(o["scale"]),
+                       n_surface=o["n_surface"], n_strat=o["n_strat"], init_params=o["init"], stream_id=oid)
+        for _ in range(6 - start):
+            ref.sample_rays([R[oid]])
+            ref.train_step()
+        errs = vh.layer_errors(p.cpu().numpy(), ref.get_object_state(0)[0].cpu().numpy().astype(np.float64), o["H"])
+        assert max(errs) <= W_RTOL, errs
+
+
+def test_autotuner_and_launch_shapes_keep_parity():
+    """Every launch shape the autotuner may pick computes the same step."""
+    sc = vh.mixed_scene(seed=20)
+    R = [o["rays"] for o in sc["objects"]]
+    cfg = vh.oracle_config(sc)
+    ost = vh.oracle_states(sc)
+    Lo = vs.train_step(cfg, ost, R)
+    for shape in ([1, 1, 1, 1], [3, 2, 2, 1], [32, 32, 32, 32]):
+        for gm in ([1, 1, 1, 1], [2, 2, 2, 2]):
+            vm = vh.library_context(sc)
+            vm.set_launch(shape, gm)
+            L = _train(vm, R, 1)[0].cpu().numpy()
+            assert np.all(np.abs(L - Lo) <= LOSS_RTOL * np.abs(Lo)), (shape, gm)
+    vm = vh.library_context(sc)
+    best = vm.autotune(R, reps=2)
+    assert all(b > 0 for b in best)
+    rt, gm = vm.get_launch()
+    assert all(1 <= x <= 32 for x in rt) and all(1 <= x <= 2 for x in gm)
+    L = _train(vm, R, 1)[0].cpu().numpy()
+    assert np.all(np.abs(L - Lo) <= LOSS_RTOL * np.abs(Lo))
