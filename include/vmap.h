@@ -247,6 +247,37 @@ vmap_status vmap_set_launch(vmap_ctx* ctx, const int* rays_per_tile, const int* 
  * Synchronises. */
 vmap_status vmap_autotune(vmap_ctx* ctx, const int* rays_per_object, int reps, float* best_ms);
 
+/* Gradient and loss of ONE object on caller-chosen rays, for callers that
+ * cannot allocate device memory: code running inside a memory pool or
+ * allocator it must not re-enter, real-time loops where a cudaMalloc could
+ * stall or fail, or hosts that pre-plan every device allocation. The paper
+ * has no counterpart; it is a convenience of this library.
+ *
+ * No context is needed and nothing is allocated: the scratch (batch tables,
+ * sample depths, transposed weights and gradient slots) lives in one
+ * file-scope device array of about 4.8 MB that every GPU loading the
+ * library keeps until the process exits. The computation equals
+ * vmap_sample_rays_given + vmap_forward + vmap_backward on a context holding
+ * the same object whose step count is `step` (same Philox draws), up to
+ * FP32 summation order.
+ *   cfg:    HOST; hyper-parameters, B and seed (capacities are ignored).
+ *   desc:   HOST; hidden, n_surface, n_strat, center, scale and stream as in
+ *           vmap_add_object; rays = DEVICE [n_rays][12] rays of this batch,
+ *           each used once; 1 <= n_rays <= 1024.
+ *   params: DEVICE [P(H)] canonical layout.
+ *   step:   the object's step count (the counter of its random draws).
+ *   grad:   DEVICE [P(H)] receives dL/dparams; loss: DEVICE [1] receives L.
+ *   cuda_stream: cudaStream_t the work is queued on (asynchronous).
+ * Returns VMAP_ERR_CAPACITY if n_rays exceeds 1024, VMAP_ERR_ARG for other
+ * invalid arguments (nothing is queued then), VMAP_ERR_CUDA if a launch fails.
+ * The first call on a device looks up the array's device address and sets
+ * kernel attributes; make that first call before any stream capture. All
+ * calls share the one array: calls whose work overlaps on the GPU (other
+ * streams, other threads) race; serialise them on one stream. */
+vmap_status vmap_object_grad_static(const vmap_config* cfg, const vmap_object_desc* desc,
+                                    const float* params, int step, float* grad, float* loss,
+                                    void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -94,6 +94,8 @@ SIGNATURES = {
     "vmap_batch_info": (_I, [_P, _IP, _LLP]),
     "vmap_get_samples": (_I, [_P, _P, _P]),
     "vmap_sync_status": (_I, [_P, _IP, _IP, _I]),
+    "vmap_object_grad_static": (_I, [ctypes.POINTER(VmapConfig), ctypes.POINTER(VmapObjectDesc), _P, _I,
+                                     _P, _P, _P]),
 }
 
 _lib = None
