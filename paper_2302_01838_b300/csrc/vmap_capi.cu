@@ -18,6 +18,7 @@
 #include "vmap_common.cuh"
 #include "vmap_optim.cuh"
 #include "vmap_sample.cuh"
+#include "vmap_tile_bf16.cuh"
 #include "vmap_tile_fp32.cuh"
 
 using namespace vmapk;
@@ -27,6 +28,7 @@ namespace {
 enum ProfSlot { PS_BUILD = 0, PS_SAMPLE = 1, PS_TILE = 2 /* + class */, PS_REDUCE = 6, PS_FINISH = 7, PS_N = 8 };
 const char* kProfNames[PS_N] = {"k_build",         "k_sample",         "k_tile_fp32<16>", "k_tile_fp32<32>",
                                 "k_tile_fp32<64>", "k_tile_fp32<128>", "k_reduce",        "k_finish"};
+const char* kProfNamesBf16[NCLASS] = {"k_tile_bf16<16>", "k_tile_bf16<32>", "k_tile_bf16<64>", "k_tile_fp32<128>"};
 
 int mmax_of(int c) {
     switch (c) {
@@ -98,6 +100,14 @@ struct vmap_ctx {
     // launch configuration (autotuned)
     int rt[NCLASS] = {RTMAX, RTMAX, RTMAX, RTMAX};
     int gmult[NCLASS] = {1, 1, 1, 1};
+
+    // BF16 tensor-core path: per-object operand images of the weights (H <= 64)
+    bool bf16 = false;
+    __nv_bfloat16* img_d = nullptr;
+    long long* img_off_d = nullptr;
+    long long img_used = 0, img_cap = 0;
+    std::vector<long long> img_off;
+    int* err_d = nullptr;   // set by a kernel whose bounded wait gave up
 
     // CUDA graphs (captured on a private stream, replayed on the context stream)
     bool graph_on = false;
@@ -278,6 +288,43 @@ cudaError_t launch_tile_c(int c, int grid, cudaStream_t st, const StepParams& sp
     }
 }
 
+template <int H, int MODE>
+cudaError_t launch_tile_bf16(int grid, cudaStream_t st, const StepParams& sp, const Bf16Args& ba) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_tile_bf16<H, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)Bf16Cfg<H>::BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    if (grid <= 0) return cudaSuccess;
+    k_tile_bf16<H, MODE><<<grid, NTHREADS, Bf16Cfg<H>::BYTES, st>>>(sp, ba);
+    return cudaGetLastError();
+}
+
+bool uses_tc(vmap_ctx* ctx, int c) { return ctx->bf16 && c < 3; }
+
+// one width class of the step's tile kernel (FP32 SIMT, or BF16 tensor cores)
+template <int MODE>
+cudaError_t launch_class(vmap_ctx* ctx, int c) {
+    TileArgs ta = base_args(ctx);
+    ta.tiles = ctx->tiles_d + (long long)c * ctx->tile_cap;
+    ta.n_tiles = ctx->counts_d + BC_TILES + c;
+    const int grid = grid_of(ctx, c);
+    if (uses_tc(ctx, c)) {
+        constexpr int BM = MODE == MODE_FORWARD ? MODE_FORWARD : MODE_TRAIN;
+        Bf16Args ba{ta, ctx->img_d, ctx->img_off_d, ctx->err_d};
+        switch (c) {
+            case 0: return launch_tile_bf16<16, BM>(grid, ctx->stream, ctx->sp, ba);
+            case 1: return launch_tile_bf16<32, BM>(grid, ctx->stream, ctx->sp, ba);
+            default: return launch_tile_bf16<64, BM>(grid, ctx->stream, ctx->sp, ba);
+        }
+    }
+    return launch_tile_c<MODE>(c, grid, ctx->stream, ctx->sp, ta);
+}
+
+int class_mmax(vmap_ctx* ctx, int c) { return uses_tc(ctx, c) ? TM : mmax_of(c); }
+
 // ---- the step's launches ------------------------------------------------------
 vmap_status launch_build_sample(vmap_ctx* ctx, int given) {
     BuildArgs a{};
@@ -289,7 +336,7 @@ vmap_status launch_build_sample(vmap_ctx* ctx, int given) {
     a.given = given;
     for (int c = 0; c < NCLASS; ++c) {
         a.rt[c] = ctx->rt[c];
-        a.mmax[c] = mmax_of(c);
+        a.mmax[c] = class_mmax(ctx, c);
         a.grid[c] = grid_of(ctx, c);
         a.part_base[c] = ctx->part_base[c];
     }
@@ -317,13 +364,10 @@ vmap_status launch_build_sample(vmap_ctx* ctx, int given) {
 
 template <int MODE>
 vmap_status launch_tiles(vmap_ctx* ctx, int mask) {
-    TileArgs ta = base_args(ctx);
     for (int c = 0; c < NCLASS; ++c) {
         if (!(mask & (1 << c))) continue;
-        ta.tiles = ctx->tiles_d + (long long)c * ctx->tile_cap;
-        ta.n_tiles = ctx->counts_d + BC_TILES + c;
         const int pi = MODE == MODE_TRAIN ? prof_begin(ctx, PS_TILE + c) : -1;
-        cudaError_t e = launch_tile_c<MODE>(c, grid_of(ctx, c), ctx->stream, ctx->sp, ta);
+        cudaError_t e = launch_class<MODE>(ctx, c);
         prof_end(ctx, pi);
         if (e != cudaSuccess)
             return fail(ctx, VMAP_ERR_CUDA, "tile kernel (H=%d) failed: %s", hidden_of(c), cudaGetErrorString(e));
@@ -337,7 +381,8 @@ vmap_status launch_reduce(vmap_ctx* ctx, int mode, const float* grad_loss, float
     k_reduce<<<ctx->n_sm * 4, 256, 0, ctx->stream>>>(ctx->sp, ctx->objs_d, ctx->ob_d, ctx->bobj_d, ctx->items_d,
                                                      ctx->counts_d, ctx->part_d, ctx->params_d, ctx->wt_d,
                                                      ctx->m_d, ctx->v_d, ctx->steps_d, ctx->status_d, mode,
-                                                     grad_loss, grad_out, loss_out, dcenter_out);
+                                                     grad_loss, grad_out, loss_out, dcenter_out,
+                                                     ctx->bf16 ? ctx->img_d : nullptr, ctx->img_off_d);
     prof_end(ctx, pi);
     CHECK_LAUNCH("k_reduce");
     return VMAP_OK;
@@ -403,7 +448,7 @@ vmap_status sample_impl(vmap_ctx* ctx, const int* rays_per_object, const float* 
         const int R = ob.active ? rays_per_object[k] : 0;
         if (R == 0) continue;
         const int c = class_of(ob.hidden);
-        const int rt = std::max(1, std::min(std::min(ctx->rt[c], RTMAX), mmax_of(c) / ob.S));
+        const int rt = std::max(1, std::min(std::min(ctx->rt[c], RTMAX), class_mmax(ctx, c) / ob.S));
         rays += R;
         samples += (long long)R * ob.S;
         tiles[c] += (R + rt - 1) / rt;
@@ -465,7 +510,7 @@ vmap_status vmap_init_objects(vmap_ctx** out, const vmap_config* cfg, void* cuda
     *out = nullptr;
     if (cfg->max_objects <= 0 || cfg->max_rays_total <= 0 || cfg->max_pool_rays <= 0 || !cfg->B)
         return VMAP_ERR_ARG;
-    if (cfg->precision != VMAP_FP32) return VMAP_ERR_ARG;
+    if (cfg->precision != VMAP_FP32 && cfg->precision != VMAP_BF16) return VMAP_ERR_ARG;
     vmap_ctx* ctx = new vmap_ctx();
     ctx->cfg = *cfg;
     ctx->cfg.B = nullptr;
@@ -483,6 +528,7 @@ vmap_status vmap_init_objects(vmap_ctx** out, const vmap_config* cfg, void* cuda
     ctx->sp.eps = cfg->eps;
     ctx->sp.key0 = (uint32_t)(cfg->seed & 0xFFFFFFFFull);
     ctx->sp.key1 = (uint32_t)(cfg->seed >> 32);
+    ctx->bf16 = cfg->precision == VMAP_BF16;
 
     auto bail = [&](vmap_status s) {
         vmap_destroy(ctx);
@@ -531,12 +577,20 @@ vmap_status vmap_init_objects(vmap_ctx** out, const vmap_config* cfg, void* cuda
     ALLOC(ctx->counts_d, sizeof(int) * BC_N);
     ALLOC(ctx->given_d, sizeof(float) * REC * (size_t)cfg->max_rays_total);
     ALLOC(ctx->loss_d, sizeof(float) * K);
+    ALLOC(ctx->err_d, sizeof(int));
+    ALLOC(ctx->img_off_d, sizeof(long long) * K);
+    if (ctx->bf16) {
+        ctx->img_cap = (long long)K * ((img_count(64) + 63) & ~63LL);
+        ALLOC(ctx->img_d, sizeof(__nv_bfloat16) * ctx->img_cap);
+    }
 #undef ALLOC
     e = cudaMemsetAsync(ctx->steps_d, 0, sizeof(int) * K, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->status_d, 0, sizeof(int) * K, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->req_d, 0, sizeof(int) * K, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->n_obj_d, 0, sizeof(int), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->counts_d, 0, sizeof(int) * BC_N, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->err_d, 0, sizeof(int), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->img_off_d, 0xFF, sizeof(long long) * K, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return bail(VMAP_ERR_CUDA);
     *out = ctx;
@@ -551,7 +605,8 @@ vmap_status vmap_destroy(vmap_ctx* ctx) {
     void* ptrs[] = {ctx->objs_d,   ctx->ob_d,     ctx->n_obj_d,  ctx->steps_d, ctx->status_d, ctx->req_d,
                     ctx->params_d, ctx->wt_d,     ctx->m_d,      ctx->v_d,     ctx->pool_d,   ctx->pick_d,
                     ctx->t_d,      ctx->bobj_d,   ctx->bray_d,   ctx->tiles_d, ctx->flags_d,  ctx->part_d,
-                    ctx->items_d,  ctx->counts_d, ctx->given_d,  ctx->loss_d};
+                    ctx->items_d,  ctx->counts_d, ctx->given_d,  ctx->loss_d,  ctx->err_d,  ctx->img_off_d,
+                    ctx->img_d};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& p : ctx->pending) {
@@ -610,6 +665,16 @@ vmap_status vmap_add_object(vmap_ctx* ctx, const vmap_object_desc* d, const floa
     }
     k_shadow<<<16, 256, 0, ctx->stream>>>(ctx->params_d + poff, ctx->wt_d + woff, d->hidden);
     CHECK_LAUNCH("k_shadow");
+    long long ioff = -1;
+    if (ctx->bf16 && d->hidden <= 64) {
+        ioff = ctx->img_used;
+        if (ioff + img_count(d->hidden) > ctx->img_cap) return fail(ctx, VMAP_ERR_CAPACITY, "weight image arena full");
+        k_image<<<1, 256, 0, ctx->stream>>>(ctx->params_d + poff, ctx->img_d + ioff, d->hidden);
+        CHECK_LAUNCH("k_image");
+        ctx->img_used = (ioff + img_count(d->hidden) + 63) & ~63LL;
+    }
+    CU(cudaMemcpyAsync(ctx->img_off_d + id, &ioff, sizeof(long long), cudaMemcpyHostToDevice, ctx->stream));
+    ctx->img_off.push_back(ioff);
     CU(cudaMemsetAsync(ctx->m_d + poff, 0, sizeof(float) * P, ctx->stream));
     CU(cudaMemsetAsync(ctx->v_d + poff, 0, sizeof(float) * P, ctx->stream));
     CU(cudaMemsetAsync(ctx->steps_d + id, 0, sizeof(int), ctx->stream));
@@ -683,6 +748,8 @@ vmap_status vmap_forward(vmap_ctx* ctx, float* out_loss) {
 vmap_status vmap_backward(vmap_ctx* ctx, const float* grad_loss, float* grad_params, float* grad_center) {
     if (!ctx || !grad_params) return fail(ctx, VMAP_ERR_ARG, "null argument");
     if (!ctx->batch_ready) return fail(ctx, VMAP_ERR_STATE, "backward needs a drawn batch");
+    if (grad_center && ctx->bf16)
+        return fail(ctx, VMAP_ERR_ARG, "the centre gradient needs an FP32 context");
     const int mask = class_mask(ctx);
     vmap_status s = grad_center ? launch_tiles<MODE_GRAD_CENTER>(ctx, mask) : launch_tiles<MODE_TRAIN>(ctx, mask);
     if (s) return s;
@@ -756,6 +823,10 @@ vmap_status vmap_set_object_state(vmap_ctx* ctx, int obj, const float* params, c
         CU(cudaMemcpyAsync(ctx->params_d + ob.param_off, params, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
         k_shadow<<<16, 256, 0, ctx->stream>>>(ctx->params_d + ob.param_off, ctx->wt_d + ob.wt_off, ob.hidden);
         CHECK_LAUNCH("k_shadow");
+        if (ctx->img_off[obj] >= 0) {
+            k_image<<<1, 256, 0, ctx->stream>>>(ctx->params_d + ob.param_off, ctx->img_d + ctx->img_off[obj], ob.hidden);
+            CHECK_LAUNCH("k_image");
+        }
     }
     if (m) CU(cudaMemcpyAsync(ctx->m_d + ob.param_off, m, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
     if (v) CU(cudaMemcpyAsync(ctx->v_d + ob.param_off, v, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -784,9 +855,14 @@ vmap_status vmap_set_params(vmap_ctx* ctx, const float* arena) {
     if (!ctx->param_used) return VMAP_OK;
     CU(cudaMemcpyAsync(ctx->params_d, arena, sizeof(float) * ctx->param_used, cudaMemcpyDeviceToDevice,
                        ctx->stream));
-    for (const ObjDev& ob : ctx->objs) {
+    for (size_t k = 0; k < ctx->objs.size(); ++k) {
+        const ObjDev& ob = ctx->objs[k];
         k_shadow<<<16, 256, 0, ctx->stream>>>(ctx->params_d + ob.param_off, ctx->wt_d + ob.wt_off, ob.hidden);
         CHECK_LAUNCH("k_shadow");
+        if (ctx->img_off[k] >= 0) {
+            k_image<<<1, 256, 0, ctx->stream>>>(ctx->params_d + ob.param_off, ctx->img_d + ctx->img_off[k], ob.hidden);
+            CHECK_LAUNCH("k_image");
+        }
     }
     return VMAP_OK;
 }
@@ -851,6 +927,9 @@ vmap_status vmap_sync_status(vmap_ctx* ctx, int* n_faulted, int* ids, int max_id
     std::vector<int> st(K);
     if (K) CU(cudaMemcpyAsync(st.data(), ctx->status_d, sizeof(int) * K, cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
+    int timed_out = 0;
+    CU(cudaMemcpy(&timed_out, ctx->err_d, sizeof(int), cudaMemcpyDeviceToHost));
+    if (timed_out) return fail(ctx, VMAP_ERR_TIMEOUT, "a tensor-core wait gave up (MMA did not complete)");
     int nf = 0;
     for (int k = 0; k < K; ++k)
         if (st[k]) {
@@ -883,7 +962,8 @@ vmap_status vmap_profile_read(vmap_ctx* ctx, int slot, const char** name, long l
     if (!ctx) return VMAP_ERR_ARG;
     if (slot < 0 || slot >= PS_N) return VMAP_ERR_ARG;
     prof_flush(ctx);
-    if (name) *name = kProfNames[slot];
+    if (name) *name = (slot >= PS_TILE && slot < PS_TILE + NCLASS && ctx->bf16) ? kProfNamesBf16[slot - PS_TILE]
+                                                                               : kProfNames[slot];
     if (launches) *launches = ctx->prof_n[slot];
     if (total_ms) *total_ms = ctx->prof_ms[slot];
     return VMAP_OK;
@@ -939,7 +1019,7 @@ vmap_status vmap_autotune(vmap_ctx* ctx, const int* rays_per_object, int reps, f
         int Smin = SMAX;
         for (const ObjDev& o : ctx->objs)
             if (class_of(o.hidden) == c) Smin = std::min(Smin, o.S);
-        const int rt_hi = std::max(1, std::min(RTMAX, mmax_of(c) / Smin));
+        const int rt_hi = std::max(1, std::min(RTMAX, class_mmax(ctx, c) / Smin));
         float best = 1e30f;
         int best_rt = ctx->rt[c], best_g = ctx->gmult[c];
         for (int g = 1; g <= GMULT_MAX && status == VMAP_OK; ++g) {
@@ -948,14 +1028,10 @@ vmap_status vmap_autotune(vmap_ctx* ctx, const int* rays_per_object, int reps, f
                 ctx->gmult[c] = g;
                 status = sample_impl(ctx, rays_per_object, nullptr, cudaMemcpyDeviceToDevice);
                 if (status) break;
-                TileArgs ta = base_args(ctx);
-                ta.tiles = ctx->tiles_d + (long long)c * ctx->tile_cap;
-                ta.n_tiles = ctx->counts_d + BC_TILES + c;
                 // the tile kernel only writes partial slots: timing it changes no state
-                cudaError_t e = launch_tile_c<MODE_TRAIN>(c, grid_of(ctx, c), ctx->stream, ctx->sp, ta);
+                cudaError_t e = launch_class<MODE_TRAIN>(ctx, c);
                 if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
-                for (int r = 0; r < reps && e == cudaSuccess; ++r)
-                    e = launch_tile_c<MODE_TRAIN>(c, grid_of(ctx, c), ctx->stream, ctx->sp, ta);
+                for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_class<MODE_TRAIN>(ctx, c);
                 if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
                 if (e == cudaSuccess) e = cudaEventSynchronize(e1);
                 if (e != cudaSuccess) {

@@ -4,6 +4,7 @@
 // weights and the gradient run slots) carved out of one file-scope device
 // array instead of cudaMalloc'd memory. It launches the same kernels as the
 // context-based path (batch builder, sampler, fused tile kernel, reduce).
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -188,6 +189,6 @@ extern "C" vmap_status vmap_object_grad_static(const vmap_config* cfg, const vma
     if (e != cudaSuccess) return VMAP_ERR_CUDA;
     // the step slot holds `step`, the status slot 0: the reduce writes the gradient and the loss
     k_reduce<<<8, 256, 0, st>>>(sp, objs, ob, bobj, items, counts, part, nullptr, nullptr, nullptr, nullptr,
-                                ints + 3, ints + 2, RED_GRAD, nullptr, grad, loss, nullptr);
+                                ints + 3, ints + 2, RED_GRAD, nullptr, grad, loss, nullptr, nullptr, nullptr);
     return cudaGetLastError() == cudaSuccess ? VMAP_OK : VMAP_ERR_CUDA;
 }

@@ -1,12 +1,36 @@
 // Per-object gradient reduction + Adam, weight initialisation, and the
 // transposed-weight shadow that the forward GEMMs stage from.
 #pragma once
+#include <cuda_bf16.h>
+
 #include "vmap_build.cuh"
 #include "vmap_common.cuh"
+#include "vmap_tc.cuh"
 
 namespace vmapk {
 
 enum ReduceMode { RED_ADAM = 0, RED_GRAD = 1, RED_LOSS = 2 };
+
+// index (in bf16 elements) of canonical parameter p inside the object's
+// tensor-core weight image (W1 [H][96], W2..W4 [H][H], W5 [16][H], each a
+// core-matrix tile), or -1 for a bias
+__host__ __device__ inline long long img_index(int H, long long p) {
+    for (int l = 0; l < 5; ++l) {
+        const long long w0 = w_off(H, l);
+        const int K = l == 0 ? DIN : H;
+        const int N = l == 4 ? NOUT : H;
+        if (p >= w0 && p < w0 + (long long)N * K) {
+            const int n = (int)((p - w0) / K), k = (int)((p - w0) % K);
+            const long long base = l == 0 ? 0 : (long long)H * DINP + (long long)(l - 1) * H * H;
+            const int CC = l == 0 ? DINP : H;
+            return base + cm_off(n, k, CC) / 2;
+        }
+    }
+    return -1;
+}
+__host__ __device__ constexpr long long img_count(int H) { return (long long)H * DINP + 3LL * H * H + 16LL * H; }
+
+
 
 // index of canonical parameter p in the transposed shadow, or -1 for a bias
 __device__ __forceinline__ long long wt_index(int H, long long p) {
@@ -51,7 +75,8 @@ __global__ void __launch_bounds__(256) k_reduce(StepParams sp, const ObjDev* __r
                                                 int mode, const float* __restrict__ grad_loss,
                                                 float* __restrict__ grad_out,
                                                 float* __restrict__ loss_out,
-                                                float* __restrict__ dcenter_out) {
+                                                float* __restrict__ dcenter_out,
+                                                __nv_bfloat16* img, const long long* __restrict__ img_off) {
     const int n_items = counts[BC_ITEMS];
 #pragma unroll 1
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
@@ -106,6 +131,10 @@ __global__ void __launch_bounds__(256) k_reduce(StepParams sp, const ObjDev* __r
             params[q] = th;
             const long long w = wt_index(H, p);
             if (w >= 0) wt[ob.wt_off + w] = th;
+            if (img && img_off[k] >= 0) {          // BF16 tensor-core operand image
+                const long long wi = img_index(H, p);
+                if (wi >= 0) img[img_off[k] + wi] = __float2bfloat16(th);
+            }
         }
     }
 }

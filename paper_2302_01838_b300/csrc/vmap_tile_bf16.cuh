@@ -1,0 +1,443 @@
+// Persistent fused training kernel with the MLP GEMMs on the 5th-generation
+// tensor cores (tcgen05, BF16 operands, FP32 accumulation in tensor memory).
+// Hidden widths 16, 32 and 64.
+//
+// Per tile of whole rays (<= 128 samples, one MMA M = 128):
+//   encoding (FP32 math, BF16 operand tile)  -> 5 forward MMA layers, each
+//   epilogue (bias, ReLU) reading the FP32 accumulator from TMEM and writing
+//   the next BF16 operand tile -> FP32 rendering / loss / dL/dy (warp scans)
+//   -> backward: for every layer the weight gradient dW^T = A^T dZ as an MMA
+//   with M = fan-in (the activation tile read MN-major), accumulated in TMEM
+//   over all tiles of the run, and dZ_prev = (dZ W) * [a > 0] as an MMA.
+// Activation tiles carry an extra column of ones, so the weight-gradient MMA
+// also yields the bias gradient (sum over samples of dZ) in the lane of that
+// column. A run's gradient leaves TMEM once, when the CTA moves to another
+// object or ends. FP32 is kept for rendering (the transmittance product),
+// losses, master weights and Adam moments; only GEMM operands are BF16.
+#pragma once
+#include <cuda_bf16.h>
+
+#include "vmap_common.cuh"
+#include "vmap_optim.cuh"
+#include "vmap_tc.cuh"
+#include "vmap_tile_fp32.cuh"
+
+namespace vmapk {
+
+constexpr int TM = 128;                       // samples per tile (MMA M)
+constexpr long long MMA_WAIT_LIMIT = 1LL << 26;
+
+template <int H> struct Bf16Cfg {
+    static_assert(H == 16 || H == 32 || H == 64, "tensor-core path: hidden 16, 32 or 64");
+    static constexpr int CH = H + 8;          // activation tile columns: H values, ones, zeros
+    static constexpr int NFWD = H < 16 ? 16 : H;  // forward accumulator columns
+    static constexpr int C_FWD = 0;
+    static constexpr int C_DX = NFWD;
+    static constexpr int C_DW5 = 2 * NFWD;
+    static constexpr int C_DW1 = C_DW5 + 16;  // dW1..dW4 at C_DW1 + l * H
+    static constexpr int NCOLS_USED = C_DW1 + 4 * H;
+    static constexpr int NCOLS = NCOLS_USED <= 128 ? 128 : NCOLS_USED <= 256 ? 256 : 512;
+    static constexpr int CTAS = H == 64 ? 1 : 2;
+    // shared memory (bytes)
+    static constexpr int G0 = 0;                                  // [128][96] bf16 encoding
+    static constexpr int HA = G0 + TM * DINP * 2;                 // 4 x [128][CH]
+    static constexpr int HA_BYTES = TM * CH * 2;
+    static constexpr int DZ = HA + 4 * HA_BYTES;                  // 2 x [128][H]
+    static constexpr int DZ_BYTES = TM * H * 2;
+    static constexpr int DY = DZ + 2 * DZ_BYTES;                  // [128][16]
+    static constexpr int WIMG = DY + TM * 16 * 2;                 // weight image
+    static constexpr int W1B = H * DINP * 2, WHB = H * H * 2, W5B = 16 * H * 2;
+    static constexpr int WIMG_BYTES = W1B + 3 * WHB + W5B;
+    static constexpr int GUARD = WIMG + WIMG_BYTES;               // tail room for MN-major over-reads
+    static constexpr int F32 = GUARD + 4096;
+    static constexpr int XT = F32;                                // [3][128] f32
+    static constexpr int TSO = XT + 3 * TM * 4;                   // [128]
+    static constexpr int YB = TSO + TM * 4;                       // [4][128]
+    static constexpr int RAYS = YB + 4 * TM * 4;                  // [32][16]
+    static constexpr int LOSS = RAYS + RTMAX * RAYF * 4;          // [4]
+    static constexpr int MBAR = LOSS + 16;
+    static constexpr int TSLOT = MBAR + 8;
+    static constexpr int BYTES = TSLOT + 8;
+};
+
+__device__ __forceinline__ void st_bf16x8(unsigned char* tile, int off, const float (&v)[8]) {
+    __nv_bfloat162 p[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) p[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+    *reinterpret_cast<uint4*>(tile + off) = *reinterpret_cast<uint4*>(p);
+}
+__device__ __forceinline__ void ld_bf16x8(const unsigned char* tile, int off, float (&v)[8]) {
+    const uint4 u = *reinterpret_cast<const uint4*>(tile + off);
+    const __nv_bfloat162* p = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float2 f = __bfloat1622float2(p[i]);
+        v[2 * i] = f.x;
+        v[2 * i + 1] = f.y;
+    }
+}
+
+// sin / cos after reduction to [-pi, pi] (the hardware approximations are
+// accurate there; the result is rounded to BF16 anyway)
+__device__ __forceinline__ float red2pi(float p) { return fmaf(-6.28318530717958647692f, rintf(p * 0.15915494309189533577f), p); }
+
+struct Bf16Args {
+    TileArgs t;
+    const __nv_bfloat16* img;   // tensor-core weight images (arena)
+    const long long* img_off;   // per object: element offset of its image
+    int* err;                   // set to 1 when a bounded wait gives up
+};
+
+template <int H, int MODE>
+__global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepParams sp, Bf16Args ba) {
+    using C = Bf16Cfg<H>;
+    constexpr int CH = C::CH;
+    constexpr bool GRAD = MODE == MODE_TRAIN;
+    const TileArgs& ta = ba.t;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char* G0 = sm + C::G0;
+    unsigned char* HA[4] = {sm + C::HA, sm + C::HA + C::HA_BYTES, sm + C::HA + 2 * C::HA_BYTES,
+                            sm + C::HA + 3 * C::HA_BYTES};
+    unsigned char* DZ[2] = {sm + C::DZ, sm + C::DZ + C::DZ_BYTES};
+    unsigned char* DYt = sm + C::DY;
+    unsigned char* W1 = sm + C::WIMG;
+    unsigned char* Wh[3] = {W1 + C::W1B, W1 + C::W1B + C::WHB, W1 + C::W1B + 2 * C::WHB};
+    unsigned char* W5 = W1 + C::W1B + 3 * C::WHB;
+    float* xt = reinterpret_cast<float*>(sm + C::XT);
+    float* tsm = reinterpret_cast<float*>(sm + C::TSO);
+    float* yb = reinterpret_cast<float*>(sm + C::YB);
+    float* rays = reinterpret_cast<float*>(sm + C::RAYS);
+    float* lossacc = reinterpret_cast<float*>(sm + C::LOSS);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + C::MBAR);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + C::TSLOT);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q = warp & 3, hf = warp >> 2;   // TMEM lane quadrant, column half
+    const int row = q * 32 + lane;            // the sample (or fan-in lane) this thread reads
+
+    // ---- set-up: barrier, tensor memory, constant columns ---------------------
+    if (tid == 0) mbar_init(mbar, 1);
+    if (warp == 0) tmem_alloc(tslot, C::NCOLS);
+    for (int i = tid; i < 4 * TM; i += blockDim.x) {
+        const int l = i / TM, r = i % TM;
+        float v[8] = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        st_bf16x8(HA[l], cm_off(r, H, CH), v);   // column H = 1 (bias gradient lane)
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    uint32_t phase = 0;
+    bool abort = false;
+
+    auto wait_mma = [&]() {
+        const bool ok = mbar_wait(mbar, phase, MMA_WAIT_LIMIT);
+        phase ^= 1;
+        if (__syncthreads_or(!ok)) {
+            abort = true;
+            if (tid == 0) atomicExch(ba.err, 1);
+        }
+        tc_fence_after();
+    };
+    auto sync_for_mma = [&]() {   // smem operand writes and TMEM reads done -> MMA may start
+        tmem_ld_wait();
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+    };
+
+    const long long n_tiles = *ta.n_tiles;
+    const long long t0 = (long long)blockIdx.x * n_tiles / gridDim.x;
+    const long long t1 = (long long)(blockIdx.x + 1) * n_tiles / gridDim.x;
+    constexpr long long PC = param_count(H);
+
+    // flush a finished run: TMEM gradient accumulators and loss sums -> its slot
+    auto flush_run = [&](long long part) {
+        float* gp = ta.part + part;
+        tc_fence_after();
+        // dW1 (lanes = fan-in 0..95, lane 93 = bias)
+#pragma unroll
+        for (int c0 = 0; c0 < H / 2; c0 += 8) {
+            float v[8];
+            tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + C::C_DW1 + hf * (H / 2) + c0, v);
+            tmem_ld_wait();
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int n = hf * (H / 2) + c0 + j;
+                if (row < DIN) gp[w_off(H, 0) + n * DIN + row] = v[j];
+                else if (row == DIN) gp[b_off(H, 0) + n] = v[j];
+            }
+        }
+#pragma unroll
+        for (int l = 1; l < 4; ++l) {
+#pragma unroll
+            for (int c0 = 0; c0 < H / 2; c0 += 8) {
+                float v[8];
+                tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + C::C_DW1 + l * H + hf * (H / 2) + c0, v);
+                tmem_ld_wait();
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int n = hf * (H / 2) + c0 + j;
+                    if (row < H) gp[w_off(H, l) + n * H + row] = v[j];
+                    else if (row == H) gp[b_off(H, l) + n] = v[j];
+                }
+            }
+        }
+        {
+            float v[8];
+            tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + C::C_DW5 + hf * 8, v);
+            tmem_ld_wait();
+            if (hf == 0) {
+#pragma unroll
+                for (int j = 0; j < NOUT; ++j) {
+                    if (row < H) gp[w_off(H, 4) + j * H + row] = v[j];
+                    else if (row == H) gp[b_off(H, 4) + j] = v[j];
+                }
+            }
+        }
+        if (tid == 0) {
+            gp[PC + 0] = lossacc[0];
+            gp[PC + 1] = lossacc[1];
+            gp[PC + 2] = lossacc[2];
+            gp[PC + 3] = 0.f;
+            gp[PC + 4] = 0.f;
+            gp[PC + 5] = 0.f;
+        }
+    };
+
+#pragma unroll 1
+    for (long long tl = t0; tl < t1 && !abort; ++tl) {
+        const TileDev td = ta.tiles[tl];
+        const int k = td.obj, nr = td.nr;
+        const bool first = tl == t0 || ta.tiles[tl - 1].obj != k;
+        const bool last = tl + 1 == t1 || ta.tiles[tl + 1].obj != k;
+        const ObjDev& ob = ta.objs[k];
+        const int S = ob.S, M = nr * S;
+        const long long sbase = ta.obs[k].sample_off + (long long)(td.ray0 - ta.obs[k].ray_off) * S;
+        const float* P = ta.params + ob.param_off;
+        const float cx = ob.c[0], cy = ob.c[1], cz = ob.c[2], sc = ob.scale;
+
+        // ---- rays, depths, points; weights at the start of a run ---------------
+        for (int r = tid; r < nr; r += blockDim.x) {
+            const float* rec = ta.pool + (ta.obs[k].src_off + ta.pick[td.ray0 + r]) * REC;
+            float* d = rays + r * RAYF;
+#pragma unroll
+            for (int u = 0; u < 11; ++u) d[u] = rec[u];
+        }
+        if (first) {
+            const uint4* src = reinterpret_cast<const uint4*>(ba.img + ba.img_off[k]);
+            uint4* dst = reinterpret_cast<uint4*>(W1);
+            for (int i = tid; i < C::WIMG_BYTES / 16; i += blockDim.x) dst[i] = src[i];
+            if (tid < 4) lossacc[tid] = 0.f;
+        }
+        __syncthreads();
+        for (int m = tid; m < TM; m += blockDim.x) {
+            float x0 = 0.f, x1 = 0.f, x2 = 0.f, t = 0.f;
+            if (m < M) {
+                const int r = m / S;
+                const float* d = rays + r * RAYF;
+                t = ta.tbuf[sbase + m];
+                x0 = (fmaf(t, d[3], d[0]) - cx) / sc;
+                x1 = (fmaf(t, d[4], d[1]) - cy) / sc;
+                x2 = (fmaf(t, d[5], d[2]) - cz) / sc;
+            }
+            tsm[m] = t;
+            xt[m] = x0;
+            xt[TM + m] = x1;
+            xt[2 * TM + m] = x2;
+        }
+        __syncthreads();
+        // ---- encoding -> G0 (BF16, 12 chunks of 8 features per sample) -----------
+        for (int f = tid; f < TM * (DINP / 8); f += blockDim.x) {
+            const int m = f % TM, ch = f / TM;
+            const float x0 = xt[m], x1 = xt[TM + m], x2 = xt[2 * TM + m];
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int c = ch * 8 + u;
+                float val;
+                if (c < 3) {
+                    val = c == 0 ? x0 : c == 1 ? x1 : x2;
+                } else if (c < DIN) {
+                    const int j = c < 3 + NF ? c - 3 : c - 3 - NF;
+                    const float p = red2pi(fmaf(sp.B[3 * j + 2], x2, fmaf(sp.B[3 * j + 1], x1, sp.B[3 * j] * x0)));
+                    val = c < 3 + NF ? __sinf(p) : __cosf(p);
+                } else {
+                    val = c == DIN ? 1.f : 0.f;   // column 93: ones (bias gradient of layer 1)
+                }
+                v[u] = val;
+            }
+            st_bf16x8(G0, cm_off(m, ch * 8, DINP), v);
+        }
+        sync_for_mma();
+
+        // ---- forward ------------------------------------------------------------
+        // layer 1: [128 x 96] x W1^T -> C_FWD
+        if (tid == 0) {
+#pragma unroll
+            for (int kc = 0; kc < DINP / 16; ++kc)
+                mma_bf16(tmem + C::C_FWD, desc_kmajor(G0, DINP, 16 * kc), desc_kmajor(W1, DINP, 16 * kc),
+                         idesc_bf16(TM, H, 0, 0), kc > 0);
+            mma_commit(mbar);
+        }
+        wait_mma();
+        if (abort) break;
+#pragma unroll 1
+        for (int l = 0; l < 4; ++l) {
+            // epilogue of layer l + 1: bias, ReLU, BF16 -> HA[l]
+            const float* bias = P + b_off(H, l);
+#pragma unroll
+            for (int c0 = 0; c0 < H / 2; c0 += 8) {
+                float v[8];
+                tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + C::C_FWD + hf * (H / 2) + c0, v);
+                tmem_ld_wait();
+#pragma unroll
+                for (int j = 0; j < 8; ++j) v[j] = fmaxf(v[j] + bias[hf * (H / 2) + c0 + j], 0.f);
+                st_bf16x8(HA[l], cm_off(row, hf * (H / 2) + c0, CH), v);
+            }
+            sync_for_mma();
+            if (tid == 0) {
+                if (l < 3) {
+#pragma unroll
+                    for (int kc = 0; kc < H / 16; ++kc)
+                        mma_bf16(tmem + C::C_FWD, desc_kmajor(HA[l], CH, 16 * kc), desc_kmajor(Wh[l], H, 16 * kc),
+                                 idesc_bf16(TM, H, 0, 0), kc > 0);
+                } else {
+#pragma unroll
+                    for (int kc = 0; kc < H / 16; ++kc)
+                        mma_bf16(tmem + C::C_FWD, desc_kmajor(HA[3], CH, 16 * kc), desc_kmajor(W5, H, 16 * kc),
+                                 idesc_bf16(TM, 16, 0, 0), kc > 0);
+                }
+                mma_commit(mbar);
+            }
+            wait_mma();
+            if (abort) break;
+        }
+        if (abort) break;
+        // layer-5 epilogue: y = acc + b5 -> yb (FP32, feature-major)
+        {
+            float v[8];
+            tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + C::C_FWD + hf * 8, v);
+            tmem_ld_wait();
+            if (hf == 0) {
+                const float* b5 = P + b_off(H, 4);
+#pragma unroll
+                for (int j = 0; j < NOUT; ++j) yb[j * TM + row] = v[j] + b5[j];
+            }
+        }
+        __syncthreads();
+
+        // ---- rendering, loss, dL/dy (FP32) ----------------------------------------
+        const float invR = 1.f / (float)ta.obs[k].R;
+        for (int r = warp; r < nr; r += NTHREADS / 32)
+            render_ray_warp<GRAD, TM>(sp, yb, tsm, rays + r * RAYF, r, S, invR);
+        for (int m = M + tid; m < TM; m += blockDim.x) {
+            yb[m] = 0.f; yb[TM + m] = 0.f; yb[2 * TM + m] = 0.f; yb[3 * TM + m] = 0.f;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+            for (int r = 0; r < nr; ++r) {
+                s0 += rays[r * RAYF + 13]; s1 += rays[r * RAYF + 14]; s2 += rays[r * RAYF + 15];
+            }
+            lossacc[0] += s0; lossacc[1] += s1; lossacc[2] += s2;
+        }
+        if (!GRAD) {
+            __syncthreads();
+            if (last) flush_run(td.part);
+            __syncthreads();
+            continue;
+        }
+        // dY -> BF16 tile [128][16] (columns 4..15 zero)
+        for (int m = tid; m < TM * 2; m += blockDim.x) {
+            const int r = m % TM, half = m / TM;
+            float v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = (half == 0 && j < NOUT) ? yb[j * TM + r] : 0.f;
+            st_bf16x8(DYt, cm_off(r, half * 8, 16), v);
+        }
+        sync_for_mma();
+
+        // ---- backward -------------------------------------------------------------
+        // layer 5: dW5^T += HA[3]^T dY ; dZ4 = (dY W5) * [h4 > 0]
+        if (tid == 0) {
+#pragma unroll
+            for (int kc = 0; kc < TM / 16; ++kc)
+                mma_bf16(tmem + C::C_DW5, desc_mnmajor(HA[3], CH, 16 * kc), desc_mnmajor(DYt, 16, 16 * kc),
+                         idesc_bf16(TM, 16, 1, 1), !first || kc > 0);
+            mma_bf16(tmem + C::C_DX, desc_kmajor(DYt, 16, 0), desc_mnmajor(W5, H, 0), idesc_bf16(TM, H, 0, 1), false);
+            mma_commit(mbar);
+        }
+        wait_mma();
+        if (abort) break;
+        int cur = 0;
+        // dX epilogue of layer lp (activation mask from HA[lp - 1]) into DZ[cur]
+        auto dx_epilogue = [&](int src_ha, unsigned char* dst) {
+#pragma unroll
+            for (int c0 = 0; c0 < H / 2; c0 += 8) {
+                float v[8], a[8];
+                tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + C::C_DX + hf * (H / 2) + c0, v);
+                tmem_ld_wait();
+                ld_bf16x8(HA[src_ha], cm_off(row, hf * (H / 2) + c0, CH), a);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) v[j] = a[j] > 0.f ? v[j] : 0.f;
+                st_bf16x8(dst, cm_off(row, hf * (H / 2) + c0, H), v);
+            }
+        };
+        dx_epilogue(3, DZ[cur]);
+        sync_for_mma();
+#pragma unroll 1
+        for (int l = 3; l >= 1; --l) {
+            // dW_{l+1}^T += HA[l-1]^T dZ_{l+1} ; dZ_l = (dZ_{l+1} W_{l+1}) * [h_l > 0]
+            if (tid == 0) {
+#pragma unroll
+                for (int kc = 0; kc < TM / 16; ++kc)
+                    mma_bf16(tmem + C::C_DW1 + l * H, desc_mnmajor(HA[l - 1], CH, 16 * kc),
+                             desc_mnmajor(DZ[cur], H, 16 * kc), idesc_bf16(TM, H, 1, 1), !first || kc > 0);
+#pragma unroll
+                for (int kc = 0; kc < H / 16; ++kc)
+                    mma_bf16(tmem + C::C_DX, desc_kmajor(DZ[cur], H, 16 * kc), desc_mnmajor(Wh[l - 1], H, 16 * kc),
+                             idesc_bf16(TM, H, 0, 1), kc > 0);
+                mma_commit(mbar);
+            }
+            wait_mma();
+            if (abort) break;
+            dx_epilogue(l - 1, DZ[cur ^ 1]);
+            cur ^= 1;
+            sync_for_mma();
+        }
+        if (abort) break;
+        // layer 1: dW1^T += G0^T dZ1
+        if (tid == 0) {
+#pragma unroll
+            for (int kc = 0; kc < TM / 16; ++kc)
+                mma_bf16(tmem + C::C_DW1, desc_mnmajor(G0, DINP, 16 * kc), desc_mnmajor(DZ[cur], H, 16 * kc),
+                         idesc_bf16(TM, H, 1, 1), !first || kc > 0);
+            mma_commit(mbar);
+        }
+        wait_mma();
+        if (abort) break;
+        if (last) flush_run(td.part);
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, C::NCOLS);
+}
+
+// rebuild an object's tensor-core weight image from its canonical parameters
+__global__ void k_image(const float* __restrict__ params, __nv_bfloat16* img, int H) {
+    const long long n = img_count(H);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        img[i] = __float2bfloat16(0.f);
+    __syncthreads();   // single-block launch: zero fill, then scatter
+    const long long P = param_count(H);
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+        const long long w = img_index(H, p);
+        if (w >= 0) img[w] = __float2bfloat16(params[p]);
+    }
+}
+
+}  // namespace vmapk
