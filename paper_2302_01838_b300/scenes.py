@@ -114,13 +114,17 @@ def random_view(rng, center, dist=2.0):
     return eye, look_at(eye, center)
 
 
-def object_pool(rng, prims, center, n_views=5, per_view=1024, dist=2.0, extra_views=0):
+def object_pool(rng, prims, center, n_views=5, per_view=1024, dist=2.0, extra_views=0, offmask=0.0):
     """Ray pool of one object: hit pixels from ``n_views`` random views.
 
-    Returns float32 [n, 12] records (mask = 1 for every ray)."""
+    Returns float32 [n, 12] records (mask = 1). With offmask > 0, up to
+    offmask * per_view further pixels of the object's 2D box that miss it are
+    added per training view with mask 0 (the paper's rays inside the box but
+    outside the mask), their depth that of a background wall 1 m behind the
+    object centre and their colour 0."""
     radius = bound_radius(prims)
     recs = []
-    for _ in range(n_views + extra_views):
+    for vi in range(n_views + extra_views):
         eye, Rwc = random_view(rng, center, dist)
         half = FOCAL * radius / max(dist - radius, 1e-3) + 2.0
         n_cand = per_view * 3
@@ -129,25 +133,75 @@ def object_pool(rng, prims, center, n_views=5, per_view=1024, dist=2.0, extra_vi
         o, d = camera_rays(Rwc, eye, u, v)
         t, rgb = cast(prims, center, o, d)
         hit = np.isfinite(t)
-        o, d, t, rgb = o[hit][:per_view], d[hit][:per_view], t[hit][:per_view], rgb[hit][:per_view]
-        rec = np.zeros((o.shape[0], REC), np.float32)
-        rec[:, 0:3], rec[:, 3:6], rec[:, 6], rec[:, 7:10], rec[:, 10] = o, d, t, rgb, 1.0
+        oh, dh, th, rgbh = o[hit][:per_view], d[hit][:per_view], t[hit][:per_view], rgb[hit][:per_view]
+        rec = np.zeros((oh.shape[0], REC), np.float32)
+        rec[:, 0:3], rec[:, 3:6], rec[:, 6], rec[:, 7:10], rec[:, 10] = oh, dh, th, rgbh, 1.0
+        if offmask > 0 and vi < n_views:
+            nm = int(offmask * per_view)
+            om, dm = o[~hit][:nm], d[~hit][:nm]
+            miss = np.zeros((om.shape[0], REC), np.float32)
+            miss[:, 0:3], miss[:, 3:6], miss[:, 6] = om, dm, dist + 1.0
+            rec = np.concatenate([rec, miss])
         recs.append(rec)
     return recs
 
 
 def make_object(rng, n_prims=(1, 1), rmin=0.1, rmax=0.4, spread=0.0, H=32,
-                n_views=5, per_view=1024, room=(2.0, 2.0, 0.6)):
-    """One object: shape, world centre, PE scale, ray pool (first n_views views)."""
+                n_views=5, per_view=1024, room=(2.0, 2.0, 0.6), heldout_views=0, offmask=0.0):
+    """One object: shape, world centre, PE scale, ray pool (first n_views views)
+    and, with heldout_views > 0, the rays of further views kept apart ("eval")."""
     k = int(rng.integers(n_prims[0], n_prims[1] + 1))
     prims = random_shape(rng, k, rmin, rmax, spread)
     center = np.array([rng.uniform(-room[0], room[0]), rng.uniform(-room[1], room[1]),
                        1.0 + rng.uniform(-room[2], room[2])])
-    views = object_pool(rng, prims, center, n_views=n_views, per_view=per_view)
-    pool = np.concatenate(views, axis=0)
+    views = object_pool(rng, prims, center, n_views=n_views, per_view=per_view,
+                        extra_views=heldout_views, offmask=offmask)
+    pool = np.concatenate(views[:n_views], axis=0)
     scale = 1.1 * bound_radius(prims)
-    return dict(prims=prims, center=center.astype(np.float32), scale=np.float32(scale),
-                pool=pool, H=H)
+    out = dict(prims=prims, center=center.astype(np.float32), scale=np.float32(scale),
+               pool=pool, H=H)
+    if heldout_views:
+        out["eval"] = np.concatenate(views[n_views:], axis=0)
+    return out
+
+
+def first_keyframe_samples(rng, obj, n=256, view=0, per_view=1024):
+    """Set-encoder input of an object: n (x~, occupancy, rgb) samples from the
+    rays of its first keyframe (the first view of the pool): n/2 surface hits
+    (occupancy 1, the hit colour) and n/2 free-space points before the hit
+    (occupancy 0, colour 0), x~ = (x - c) / s. Returns float32 [n, 7]."""
+    pool = obj["pool"]
+    rays = pool[view * per_view:(view + 1) * per_view] if pool.shape[0] >= per_view else pool
+    rays = rays[rays[:, 10] > 0]          # in-mask pixels of the keyframe
+    h = n // 2
+    i = rng.integers(0, rays.shape[0], h)
+    j = rng.integers(0, rays.shape[0], n - h)
+    hit = rays[i, 0:3] + rays[i, 6:7] * rays[i, 3:6]
+    frac = rng.uniform(0.2, 0.9, (n - h, 1))
+    free = rays[j, 0:3] + frac * rays[j, 6:7] * rays[j, 3:6]
+    x = (np.concatenate([hit, free]) - obj["center"]) / obj["scale"]
+    occ = np.concatenate([np.ones(h), np.zeros(n - h)])[:, None]
+    rgb = np.concatenate([rays[i, 7:10], np.zeros((n - h, 3))])
+    return np.concatenate([x, occ, rgb], axis=1).astype(np.float32)
+
+
+def scene_shapes(seed, n_objects, heldout_views=1, per_view=512, offmask=0.0):
+    """Shapes for the warm-start experiments: unions of 1-3 primitives,
+    hidden 32, 120 rays per step, one held-out view per object; every object
+    starts from the same seeded initial weights (so converged weights share
+    one basin)."""
+    rng = np.random.default_rng(seed)
+    init = init_weights(np.random.default_rng(12345), 32)
+    objs = []
+    for _ in range(n_objects):
+        o = make_object(rng, (1, 3), 0.1, 0.3, 0.25, H=32, per_view=per_view, heldout_views=heldout_views,
+                        offmask=offmask)
+        o["init"] = init
+        o["rays"] = 120
+        o["n_surface"], o["n_strat"] = 10, 12
+        o["set_input"] = first_keyframe_samples(rng, o, per_view=per_view)
+        objs.append(o)
+    return dict(objects=objs, B=make_B(1000 + 5), seed=seed)
 
 
 def background_object(rng, half=(3.0, 3.0, 1.5), n_views=5, per_view=2048, H=128, scale=2.5):
