@@ -35,8 +35,11 @@ FP32_LANES_PER_SM = 128      # FFMA lanes per SM (4 SMSPs x 32)
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=1500)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--precision", choices=["fp32", "bf16"], default="fp32",
+                    help="fp32: plain FP32 SIMT path; bf16: tcgen05 BF16 GEMMs (hidden <= 64)")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=12, help="oracle steps of the CPU baseline sample")
@@ -78,27 +81,27 @@ def measured_peaks():
     return {}
 
 
-def kernel_source_hash():
+def source_hash(files):
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2302_01838_b300", "csrc")
-    for fn in sorted(os.listdir(d)):
+    for fn in files:
         with open(os.path.join(d, fn), "rb") as f:
             h.update(fn.encode() + f.read())
     return h.hexdigest()[:16]
 
 
-def traffic_for(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if taken on the
-    current kernel sources (else None)."""
+def traffic_for(kernel, launches_scale=1.0):
+    """DRAM bytes per launch from the committed ncu summary, if the counters
+    were taken on the kernel's current source files (else None)."""
     p = os.path.join(ROOT, "profiles", "dram_traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         t = json.load(f)
     e = t.get(kernel)
-    if not e or e.get("source_hash") != kernel_source_hash():
+    if not e or e.get("source_hash") != source_hash(e.get("sources", [])):
         return None
-    return e.get("bytes_per_launch")
+    return int(e["bytes_per_launch"] * launches_scale)
 
 
 class ClockSampler:
@@ -216,6 +219,7 @@ def run_ours(args):
     import torch
     import torch.distributed as dist
     from paper_2302_01838_b300.api import VMap
+    from paper_2302_01838_b300.native import VMAP_BF16, VMAP_FP32
 
     rank, world, local = dist_env()
     if world > 1:
@@ -225,14 +229,19 @@ def run_ours(args):
     objs = sc["objects"]
     R = [o["rays"] for o in objs]
     K = len(objs)
+    prec = VMAP_BF16 if args.precision == "bf16" else VMAP_FP32
     vm = VMap(max_objects=K + 8, max_rays_total=2 * sum(R), max_pool_rays=sum(o["pool"].shape[0] for o in objs) + 16,
-              B=sc["B"], seed=sc["seed"])
+              B=sc["B"], seed=sc["seed"], precision=prec)
     for k, o in enumerate(objs):
         vm.add_object(o["pool"], hidden=o["H"], center=o["center"], scale=float(o["scale"]),
                       n_surface=o["n_surface"], n_strat=o["n_strat"], init_params=o["init"], stream_id=k)
     sps = samples_per_step(sc)
     loss = torch.empty(K, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, device="cuda")
+    launch = None
+    if not args.no_autotune:
+        vm.autotune(R, reps=3)
+        launch = vm.get_launch()
     for _ in range(max(args.warmup, 3)):
         vm.sample_rays(R)
         vm.train_step(loss)
@@ -251,6 +260,8 @@ def run_ours(args):
         vm.sample_rays(R)
         vm.train_step(loss)
         ev[i][1].record()
+        if i % 250 == 249:
+            vm.profile()                 # fold the pending kernel events (synchronises, outside the intervals)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -301,20 +312,29 @@ def run_ours(args):
         launches, dom_ms = tiles[dom]
         achieved = flops / (dom_ms / launches * 1e-3) / 1e12
         traffic = traffic_for(dom)
+        tensor = dom.startswith("k_tile_bf16")
+        if tensor:
+            peak, bound = peaks.get("bf16_tflops", 1800.0), "tensor"
+            peak_note = "measured cuBLAS BF16 burst (MEASURED_PEAKS.json bf16_tflops)"
+        else:
+            peak, bound = fp32_peak, "alu"
+            peak_note = f"FP32 FFMA: {props.multi_processor_count} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_max:.0f} MHz"
         value = world * sps * args.steps / (ms_max * 1e-3)
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16+f32",
+            "data": "synthetic",
             "steps_per_s": 1e3 * args.steps / ms_max,
             "config": {"workload": "room50: 50 objects (hidden 32, 32-600 rays) + background (hidden 128, 1200 rays), "
-                                   "22 samples/ray, FP32, all objects present",
+                                   f"22 samples/ray, {args.precision.upper()}, all objects present",
+                       "precision": args.precision, "launch_shape": launch,
                        "objects_per_gpu": K, "samples_per_step_per_gpu": sps,
                        "rays_per_step_per_gpu": sum(R), "l2": "flushed (512 MB write) between timed steps",
                        "parallelism": f"objects sharded, {world} independent scene(s), no collective"},
-            "roofline": {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": fp32_peak,
-                         "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
-                         "peak_note": f"FP32 FFMA: {props.multi_processor_count} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_max:.0f} MHz",
+            "roofline": {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                         "peak_note": peak_note,
                          "flops_per_launch": flops, "avg_launch_ms": dom_ms / launches},
             "kernels": {k: {"launches": n, "total_ms": round(t_, 4), "share": round(t_ / sum(v[1] for v in prof.values()), 4)}
                         for k, (n, t_) in prof.items()},

@@ -63,6 +63,7 @@ extern "C" {
 #define VMAP_MAX_SAMPLES 32
 
 typedef struct vmap_ctx vmap_ctx;
+typedef struct vmap_hyper vmap_hyper;
 
 typedef enum {
     VMAP_OK = 0,
@@ -217,8 +218,9 @@ vmap_status vmap_get_samples(vmap_ctx* ctx, int* pick, float* t);
 vmap_status vmap_sync_status(vmap_ctx* ctx, int* n_faulted, int* ids, int max_ids);
 
 /* Tracing: with profiling enabled, every kernel launch is bracketed by CUDA
- * events on the context stream. vmap_profile_read synchronises and returns,
- * for kernel slot `slot` (0 .. until VMAP_ERR_ARG), its name (static
+ * events on the context stream (in graph mode, every graph replay, as the
+ * slots "graph:sample" and "graph:train"). vmap_profile_read synchronises and
+ * returns, for slot `slot` (0 .. until VMAP_ERR_ARG), its name (static
  * string), launch count and summed device milliseconds since the last reset. */
 vmap_status vmap_profile_enable(vmap_ctx* ctx, int on);
 vmap_status vmap_profile_reset(vmap_ctx* ctx);
@@ -246,6 +248,42 @@ vmap_status vmap_set_launch(vmap_ctx* ctx, const int* rays_per_tile, const int* 
  * NULL, the best per-launch milliseconds per class (0 for absent classes).
  * Synchronises. */
 vmap_status vmap_autotune(vmap_ctx* ctx, const int* rays_per_object, int reps, float* best_ms);
+
+/* ---------------------------------------------------------------------------
+ * Warm-start set-encoder hypernetwork (not in the paper: this library's
+ * learned extension). From n_points samples (x~ = (x - c_k)/s_k, occupancy,
+ * rgb: 7 floats each) of a newly seen object's first keyframe it predicts
+ * initial weights for the object's MLP (canonical layout, P(hidden) floats):
+ *   per point  h1 = ReLU(W1 x + b1), h2 = ReLU(W2 h1 + b2), h3 = ReLU(W3 h2 + b3)
+ *   per set    z = channel-wise max of h3 over the points (ties: lowest index)
+ *   head       u = Wa z + ba (rank `rank`), theta = Wb u + bb
+ * Trained on (samples, converged weights) pairs with the mean squared error
+ * L = sum (theta - target)^2 / (batch P). Parameters (flat, in this order):
+ * W1 [width][7], b1, W2 [width][width], b2, W3, b3, Wa [rank][width], ba,
+ * Wb [P][rank], bb [P]. All calls are asynchronous on the stream given to
+ * vmap_hyper_create. Inputs X: DEVICE [batch][n_points][7]; targets T and
+ * outputs: DEVICE [batch][P]; grad: DEVICE [n_params]; loss: DEVICE [1]
+ * or NULL. batch > max_batch gives VMAP_ERR_CAPACITY. */
+vmap_status vmap_hyper_create(vmap_hyper** out, int n_points, int width, int rank, int hidden,
+                              int max_batch, unsigned long long seed, void* cuda_stream);
+vmap_status vmap_hyper_destroy(vmap_hyper* h);
+const char* vmap_hyper_last_error(const vmap_hyper* h);
+/* HOST outputs: number of hypernetwork parameters, and P (outputs per object). */
+vmap_status vmap_hyper_param_count(vmap_hyper* h, long long* n_params, int* out_params);
+vmap_status vmap_hyper_get_params(vmap_hyper* h, float* flat);
+/* Setting the parameters also resets the Adam moments and step count. */
+vmap_status vmap_hyper_set_params(vmap_hyper* h, const float* flat);
+vmap_status vmap_hyper_predict(vmap_hyper* h, int batch, const float* X, float* out);
+/* Loss and gradient without an update. */
+vmap_status vmap_hyper_grad(vmap_hyper* h, int batch, const float* X, const float* T, float* grad,
+                            float* loss);
+/* One Adam step (betas 0.9, 0.999, eps 1e-8) on one batch. */
+vmap_status vmap_hyper_train_step(vmap_hyper* h, int batch, const float* X, const float* T, float lr,
+                                  float* loss);
+/* Warm start: predict object obj's weights from X (DEVICE [n_points][7]) and
+ * install them with zero Adam moments and step count 0. The hypernetwork's
+ * output count must equal the object's P(H). Synchronises the device. */
+vmap_status vmap_warmstart(vmap_ctx* ctx, int obj, vmap_hyper* h, const float* X);
 
 /* Gradient and loss of ONE object on caller-chosen rays, for callers that
  * cannot allocate device memory: code running inside a memory pool or

@@ -136,6 +136,10 @@ class VMap:
             slot += 1
         return out
 
+    def warmstart(self, obj, hyper, X):
+        """Install hypernetwork-predicted weights for object obj (X: [n_points, 7] CUDA)."""
+        self._check(self.lib.vmap_warmstart(self.h, int(obj), hyper.h, _ptr(X.contiguous())))
+
     def set_graph(self, on=True):
         self._check(self.lib.vmap_set_graph(self.h, int(bool(on))))
 
@@ -261,3 +265,60 @@ class VMapLoss(torch.autograd.Function):
         gc = torch.zeros(vm.num_objects(), 3, device="cuda")
         vm.backward(gp, grad_loss=grad_loss.contiguous(), grad_center=gc)
         return None, gp, gc
+
+
+class HyperNet:
+    """Warm-start set-encoder hypernetwork (C ABI vmap_hyper_*)."""
+
+    def __init__(self, n_points=256, width=128, rank=16, hidden=32, max_batch=256, seed=0, stream=None):
+        self.lib = native.load()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        st = self.lib.vmap_hyper_create(ctypes.byref(h), n_points, width, rank, hidden, max_batch, seed,
+                                        ctypes.c_void_p(self.stream.cuda_stream))
+        if st != 0:
+            raise VmapError(st, "vmap_hyper_create failed")
+        self.h = h
+        n, P = ctypes.c_longlong(), ctypes.c_int()
+        self.lib.vmap_hyper_param_count(h, ctypes.byref(n), ctypes.byref(P))
+        self.n_params, self.P = n.value, P.value
+        self.n_points = n_points
+
+    def _check(self, st):
+        if st != 0:
+            raise VmapError(st, self.lib.vmap_hyper_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.vmap_hyper_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self):
+        out = torch.empty(self.n_params, device="cuda")
+        self._check(self.lib.vmap_hyper_get_params(self.h, _ptr(out)))
+        return out
+
+    def set_params(self, flat):
+        self._check(self.lib.vmap_hyper_set_params(self.h, _ptr(flat.contiguous())))
+
+    def predict(self, X):
+        out = torch.empty(X.shape[0], self.P, device="cuda")
+        self._check(self.lib.vmap_hyper_predict(self.h, X.shape[0], _ptr(X.contiguous()), _ptr(out)))
+        return out
+
+    def grad(self, X, T):
+        g = torch.empty(self.n_params, device="cuda")
+        loss = torch.empty(1, device="cuda")
+        self._check(self.lib.vmap_hyper_grad(self.h, X.shape[0], _ptr(X.contiguous()), _ptr(T.contiguous()),
+                                             _ptr(g), _ptr(loss)))
+        return g, loss
+
+    def train_step(self, X, T, lr, loss=None):
+        self._check(self.lib.vmap_hyper_train_step(self.h, X.shape[0], _ptr(X.contiguous()), _ptr(T.contiguous()),
+                                                   ctypes.c_float(lr), _ptr(loss)))

@@ -5,7 +5,8 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-SOURCES = [os.path.join(HERE, "csrc", "vmap_capi.cu"), os.path.join(HERE, "csrc", "vmap_noalloc.cu")]
+SOURCES = [os.path.join(HERE, "csrc", "vmap_capi.cu"), os.path.join(HERE, "csrc", "vmap_noalloc.cu"),
+           os.path.join(HERE, "csrc", "vmap_hyper.cu")]
 OUT = os.path.join(HERE, "libvmap.so")
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-shared", "-Xcompiler", "-fPIC", "-diag-suppress", "128,177",

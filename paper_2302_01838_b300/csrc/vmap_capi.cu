@@ -25,9 +25,11 @@ using namespace vmapk;
 
 namespace {
 
-enum ProfSlot { PS_BUILD = 0, PS_SAMPLE = 1, PS_TILE = 2 /* + class */, PS_REDUCE = 6, PS_FINISH = 7, PS_N = 8 };
+enum ProfSlot { PS_BUILD = 0, PS_SAMPLE = 1, PS_TILE = 2 /* + class */, PS_REDUCE = 6, PS_FINISH = 7,
+                PS_GRAPH_SAMPLE = 8, PS_GRAPH_TRAIN = 9, PS_N = 10 };
 const char* kProfNames[PS_N] = {"k_build",         "k_sample",         "k_tile_fp32<16>", "k_tile_fp32<32>",
-                                "k_tile_fp32<64>", "k_tile_fp32<128>", "k_reduce",        "k_finish"};
+                                "k_tile_fp32<64>", "k_tile_fp32<128>", "k_reduce",        "k_finish",
+                                "graph:sample",    "graph:train"};
 const char* kProfNamesBf16[NCLASS] = {"k_tile_bf16<16>", "k_tile_bf16<32>", "k_tile_bf16<64>", "k_tile_fp32<128>"};
 
 int mmax_of(int c) {
@@ -115,13 +117,12 @@ struct vmap_ctx {
     cudaGraphExec_t g_sample[2] = {nullptr, nullptr};   // [given]
     cudaGraphExec_t g_train = nullptr;
     int g_classes = -1;                 // class mask the train graph was captured for
-    std::vector<ProfPair> g_prof[3];    // profile pairs recorded inside each graph
 
     // profiling
     bool prof_on = false;
     std::vector<cudaEvent_t> ev_free;
     std::vector<ProfPair> pending;
-    std::vector<ProfPair>* capture_prof = nullptr;   // set while capturing
+    bool capturing = false;
     double prof_ms[PS_N] = {0};
     long long prof_n[PS_N] = {0};
 };
@@ -166,30 +167,20 @@ cudaEvent_t take_event(vmap_ctx* ctx) {
 }
 
 int prof_begin(vmap_ctx* ctx, int slot) {
-    if (!ctx->prof_on) return -1;
+    if (!ctx->prof_on || ctx->capturing) return -1;
     ProfPair p{slot, take_event(ctx), take_event(ctx)};
     if (!p.a || !p.b) return -1;
     cudaEventRecord(p.a, ctx->stream);
-    std::vector<ProfPair>& dst = ctx->capture_prof ? *ctx->capture_prof : ctx->pending;
-    dst.push_back(p);
-    return (int)dst.size() - 1;
+    ctx->pending.push_back(p);
+    return (int)ctx->pending.size() - 1;
 }
 
 void prof_end(vmap_ctx* ctx, int idx) {
     if (idx < 0) return;
-    std::vector<ProfPair>& dst = ctx->capture_prof ? *ctx->capture_prof : ctx->pending;
-    cudaEventRecord(dst[idx].b, ctx->stream);
+    cudaEventRecord(ctx->pending[idx].b, ctx->stream);
 }
 
-bool graph_owned(vmap_ctx* ctx, cudaEvent_t e) {
-    for (auto& gv : ctx->g_prof)
-        for (auto& q : gv)
-            if (q.a == e || q.b == e) return true;
-    return false;
-}
-
-// synchronise and accumulate every pending pair; pairs owned by a graph are
-// read but kept (the graph records them again at its next replay)
+// synchronise and accumulate every pending pair
 void prof_flush(vmap_ctx* ctx) {
     if (ctx->pending.empty()) return;
     cudaStreamSynchronize(ctx->stream);
@@ -199,20 +190,10 @@ void prof_flush(vmap_ctx* ctx) {
             ctx->prof_ms[p.slot] += ms;
             ctx->prof_n[p.slot] += 1;
         }
-        if (!graph_owned(ctx, p.a)) {
-            ctx->ev_free.push_back(p.a);
-            ctx->ev_free.push_back(p.b);
-        }
-    }
-    ctx->pending.clear();
-}
-
-void release_graph_prof(vmap_ctx* ctx, std::vector<ProfPair>& gv) {
-    for (auto& p : gv) {
         ctx->ev_free.push_back(p.a);
         ctx->ev_free.push_back(p.b);
     }
-    gv.clear();
+    ctx->pending.clear();
 }
 
 void drop_graphs(vmap_ctx* ctx) {
@@ -226,7 +207,6 @@ void drop_graphs(vmap_ctx* ctx) {
         cudaGraphExecDestroy(ctx->g_train);
         ctx->g_train = nullptr;
     }
-    for (auto& gv : ctx->g_prof) release_graph_prof(ctx, gv);
     ctx->g_classes = -1;
 }
 
@@ -401,7 +381,7 @@ vmap_status launch_train(vmap_ctx* ctx, int mask) {
 
 // capture fn() into an executable graph on the context stream
 template <typename F>
-vmap_status capture(vmap_ctx* ctx, cudaGraphExec_t* out, std::vector<ProfPair>* prof, F fn) {
+vmap_status capture(vmap_ctx* ctx, cudaGraphExec_t* out, F fn) {
     cudaGraph_t g = nullptr;
     if (!ctx->cap_stream) CU(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
     // the context stream may be the legacy default stream, which cannot be captured
@@ -409,9 +389,9 @@ vmap_status capture(vmap_ctx* ctx, cudaGraphExec_t* out, std::vector<ProfPair>* 
     CU(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaStream_t user = ctx->stream;
     ctx->stream = ctx->cap_stream;
-    ctx->capture_prof = prof;
+    ctx->capturing = true;
     vmap_status s = fn();
-    ctx->capture_prof = nullptr;
+    ctx->capturing = false;
     ctx->stream = user;
     cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
     if (s) {
@@ -425,11 +405,11 @@ vmap_status capture(vmap_ctx* ctx, cudaGraphExec_t* out, std::vector<ProfPair>* 
     return VMAP_OK;
 }
 
-vmap_status replay(vmap_ctx* ctx, cudaGraphExec_t g, std::vector<ProfPair>& prof) {
-    if (ctx->prof_on) prof_flush(ctx);   // the replay records the graph's events again
+// with profiling on, a replay is timed as a whole (slot graph:sample / graph:train)
+vmap_status replay(vmap_ctx* ctx, cudaGraphExec_t g, int slot) {
+    const int pi = prof_begin(ctx, slot);
     CU(cudaGraphLaunch(g, ctx->stream));
-    if (ctx->prof_on)
-        for (auto& p : prof) ctx->pending.push_back(p);
+    prof_end(ctx, pi);
     return VMAP_OK;
 }
 
@@ -464,11 +444,10 @@ vmap_status sample_impl(vmap_ctx* ctx, const int* rays_per_object, const float* 
     const int gi = given ? 1 : 0;
     if (ctx->graph_on) {
         if (!ctx->g_sample[gi]) {
-            vmap_status s = capture(ctx, &ctx->g_sample[gi], &ctx->g_prof[gi],
-                                    [&] { return launch_build_sample(ctx, gi); });
+            vmap_status s = capture(ctx, &ctx->g_sample[gi], [&] { return launch_build_sample(ctx, gi); });
             if (s) return s;
         }
-        if (vmap_status s = replay(ctx, ctx->g_sample[gi], ctx->g_prof[gi])) return s;
+        if (vmap_status s = replay(ctx, ctx->g_sample[gi], PS_GRAPH_SAMPLE)) return s;
     } else {
         if (vmap_status s = launch_build_sample(ctx, gi)) return s;
     }
@@ -707,17 +686,15 @@ vmap_status vmap_train_step(vmap_ctx* ctx, float* out_loss) {
     const int mask = class_mask(ctx);
     if (ctx->graph_on) {
         if (ctx->g_train && ctx->g_classes != mask) {
-            prof_flush(ctx);
             cudaGraphExecDestroy(ctx->g_train);
             ctx->g_train = nullptr;
-            release_graph_prof(ctx, ctx->g_prof[2]);
         }
         if (!ctx->g_train) {
-            vmap_status s = capture(ctx, &ctx->g_train, &ctx->g_prof[2], [&] { return launch_train(ctx, mask); });
+            vmap_status s = capture(ctx, &ctx->g_train, [&] { return launch_train(ctx, mask); });
             if (s) return s;
             ctx->g_classes = mask;
         }
-        if (vmap_status s = replay(ctx, ctx->g_train, ctx->g_prof[2])) return s;
+        if (vmap_status s = replay(ctx, ctx->g_train, PS_GRAPH_TRAIN)) return s;
     } else {
         if (vmap_status s = launch_train(ctx, mask)) return s;
     }
@@ -943,7 +920,6 @@ vmap_status vmap_sync_status(vmap_ctx* ctx, int* n_faulted, int* ids, int max_id
 vmap_status vmap_profile_enable(vmap_ctx* ctx, int on) {
     if (!ctx) return VMAP_ERR_ARG;
     prof_flush(ctx);
-    if ((on != 0) != ctx->prof_on) drop_graphs(ctx);   // graphs carry (or not) the event records
     ctx->prof_on = on != 0;
     return VMAP_OK;
 }
@@ -966,6 +942,34 @@ vmap_status vmap_profile_read(vmap_ctx* ctx, int slot, const char** name, long l
                                                                                : kProfNames[slot];
     if (launches) *launches = ctx->prof_n[slot];
     if (total_ms) *total_ms = ctx->prof_ms[slot];
+    return VMAP_OK;
+}
+
+vmap_status vmap_warmstart(vmap_ctx* ctx, int obj, vmap_hyper* h, const float* X) {
+    if (vmap_status s = check_obj(ctx, obj)) return s;
+    if (!h || !X) return fail(ctx, VMAP_ERR_ARG, "null argument");
+    const ObjDev& ob = ctx->objs[obj];
+    int P = 0;
+    vmap_hyper_param_count(h, nullptr, &P);
+    if (P != (int)param_count(ob.hidden))
+        return fail(ctx, VMAP_ERR_ARG, "hypernetwork emits %d parameters, object %d has %lld", P, obj,
+                    param_count(ob.hidden));
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (vmap_status s = vmap_hyper_predict(h, 1, X, ctx->params_d + ob.param_off))
+        return fail(ctx, s, "hypernetwork predict failed: %s", vmap_hyper_last_error(h));
+    CU(cudaDeviceSynchronize());
+    const size_t bytes = sizeof(float) * param_count(ob.hidden);
+    k_shadow<<<16, 256, 0, ctx->stream>>>(ctx->params_d + ob.param_off, ctx->wt_d + ob.wt_off, ob.hidden);
+    CHECK_LAUNCH("k_shadow");
+    if (ctx->img_off[obj] >= 0) {
+        k_image<<<1, 256, 0, ctx->stream>>>(ctx->params_d + ob.param_off, ctx->img_d + ctx->img_off[obj], ob.hidden);
+        CHECK_LAUNCH("k_image");
+    }
+    CU(cudaMemsetAsync(ctx->m_d + ob.param_off, 0, bytes, ctx->stream));
+    CU(cudaMemsetAsync(ctx->v_d + ob.param_off, 0, bytes, ctx->stream));
+    CU(cudaMemsetAsync(ctx->steps_d + obj, 0, sizeof(int), ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    ctx->batch_ready = false;
     return VMAP_OK;
 }
 

@@ -94,6 +94,16 @@ SIGNATURES = {
     "vmap_batch_info": (_I, [_P, _IP, _LLP]),
     "vmap_get_samples": (_I, [_P, _P, _P]),
     "vmap_sync_status": (_I, [_P, _IP, _IP, _I]),
+    "vmap_hyper_create": (_I, [ctypes.POINTER(_P), _I, _I, _I, _I, _I, ctypes.c_ulonglong, _P]),
+    "vmap_hyper_destroy": (_I, [_P]),
+    "vmap_hyper_last_error": (ctypes.c_char_p, [_P]),
+    "vmap_hyper_param_count": (_I, [_P, _LLP, _IP]),
+    "vmap_hyper_get_params": (_I, [_P, _P]),
+    "vmap_hyper_set_params": (_I, [_P, _P]),
+    "vmap_hyper_predict": (_I, [_P, _I, _P, _P]),
+    "vmap_hyper_grad": (_I, [_P, _I, _P, _P, _P, _P]),
+    "vmap_hyper_train_step": (_I, [_P, _I, _P, _P, ctypes.c_float, _P]),
+    "vmap_warmstart": (_I, [_P, _I, _P, _P]),
     "vmap_object_grad_static": (_I, [ctypes.POINTER(VmapConfig), ctypes.POINTER(VmapObjectDesc), _P, _I,
                                      _P, _P, _P]),
 }
