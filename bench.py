@@ -218,6 +218,7 @@ def run_ours(args):
     import numpy as np
     import torch
     import torch.distributed as dist
+    from paper_2302_01838_b300 import sharding
     from paper_2302_01838_b300.api import VMap
     from paper_2302_01838_b300.native import VMAP_BF16, VMAP_FP32
 
@@ -268,11 +269,7 @@ def run_ours(args):
     clk = clocks.stop()
     vm.profile_enable(False)
     prof = vm.profile()
-    ms = sum(a.elapsed_time(b) for a, b in ev)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = sharding.max_over_ranks(sum(a.elapsed_time(b) for a, b in ev))
     assert np.all(np.isfinite(loss.cpu().numpy())), "non-finite loss"
 
     # ---- end to end through the C ABI with host buffers --------------------
@@ -293,10 +290,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         vm.train_step_host(host_batches[i % n_batches], R, loss_h)
         e2e_s += time.perf_counter() - t0
-    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_s = float(e2e_t.item())
+    e2e_s = sharding.max_over_ranks(e2e_s)
 
     if rank == 0:
         peaks = measured_peaks()

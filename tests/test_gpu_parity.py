@@ -471,3 +471,33 @@ def test_autotuner_and_launch_shapes_keep_parity():
     assert all(1 <= x <= 32 for x in rt) and all(1 <= x <= 2 for x in gm)
     L = _train(vm, R, 1)[0].cpu().numpy()
     assert np.all(np.abs(L - Lo) <= LOSS_RTOL * np.abs(Lo))
+
+
+def test_full_objective_with_off_mask_rays_matches_oracle():
+    """Eq. 5 with the occupancy term (lambda_2 = 10): pools that hold off-mask
+    rays (mask 0, so they add only to the occupancy term), hidden 32 and 64,
+    10 steps against the oracle."""
+    rng = np.random.default_rng(21)
+    objs = []
+    for H in (32, 64, 32):
+        o = scenes.make_object(rng, (1, 2), 0.1, 0.3, 0.2, H=H, per_view=200, offmask=0.5)
+        assert np.any(o["pool"][:, 10] == 0) and np.any(o["pool"][:, 10] == 1)
+        o["init"] = scenes.init_weights(rng, H)
+        o["n_surface"], o["n_strat"] = 10, 12
+        o["rays"] = 150
+        objs.append(o)
+    sc = dict(objects=objs, B=scenes.make_B(1021), seed=21)
+    vm = vh.library_context(sc, lambda_occ=10.0)
+    cfg = vh.oracle_config(sc, lambda_occ=10.0)
+    ost = vh.oracle_states(sc)
+    K = len(ost)
+    loss = torch.empty(K, device="cuda")
+    for step in range(10):
+        vm.sample_rays([150] * K)
+        vm.train_step(loss)
+        Lo = vs.train_step(cfg, ost, [150] * K)
+        rel = np.abs(loss.cpu().numpy().astype(np.float64) - Lo) / np.abs(Lo)
+        assert np.all(rel <= LOSS_RTOL), f"step {step}: loss rel err {rel}"
+    for k in range(K):
+        errs = vh.layer_errors(vm.get_object_state(k)[0].cpu().numpy(), ost[k].params, ost[k].H)
+        assert max(errs) <= W_RTOL, f"object {k}: weight errors {errs}"
