@@ -20,17 +20,18 @@
 #include "vmap_sample.cuh"
 #include "vmap_tile_bf16.cuh"
 #include "vmap_tile_fp32.cuh"
+#include "vmap_tile_wide.cuh"
 
 using namespace vmapk;
 
 namespace {
 
 enum ProfSlot { PS_BUILD = 0, PS_SAMPLE = 1, PS_TILE = 2 /* + class */, PS_REDUCE = 6, PS_FINISH = 7,
-                PS_GRAPH_SAMPLE = 8, PS_GRAPH_TRAIN = 9, PS_N = 10 };
+                PS_GRAPH_SAMPLE = 8, PS_GRAPH_TRAIN = 9, PS_WIDE_DW = 10, PS_N = 11 };
 const char* kProfNames[PS_N] = {"k_build",         "k_sample",         "k_tile_fp32<16>", "k_tile_fp32<32>",
                                 "k_tile_fp32<64>", "k_tile_fp32<128>", "k_reduce",        "k_finish",
-                                "graph:sample",    "graph:train"};
-const char* kProfNamesBf16[NCLASS] = {"k_tile_bf16<16>", "k_tile_bf16<32>", "k_tile_bf16<64>", "k_tile_fp32<128>"};
+                                "graph:sample",    "graph:train",      "k_wide_dw<128>"};
+const char* kProfNamesBf16[NCLASS] = {"k_tile_bf16<16>", "k_tile_bf16<32>", "k_tile_bf16<64>", "k_wide_fb<128>"};
 
 int mmax_of(int c) {
     switch (c) {
@@ -103,13 +104,19 @@ struct vmap_ctx {
     int rt[NCLASS] = {RTMAX, RTMAX, RTMAX, RTMAX};
     int gmult[NCLASS] = {1, 1, 1, 1};
 
-    // BF16 tensor-core path: per-object operand images of the weights (H <= 64)
+    // BF16 tensor-core path: per-object operand images of the weights
     bool bf16 = false;
     __nv_bfloat16* img_d = nullptr;
     long long* img_off_d = nullptr;
     long long img_used = 0, img_cap = 0;
     std::vector<long long> img_off;
     int* err_d = nullptr;   // set by a kernel whose bounded wait gave up
+    // width-128 tensor-core path: per-tile activation records, grown on demand;
+    // kernels read the buffer's address from act_pp_d, so captured graphs survive a regrowth
+    unsigned char* act_d = nullptr;
+    unsigned char** act_pp_d = nullptr;
+    long long act_cap = 0;          // tiles
+    float* tile_loss_d = nullptr;   // [tile_cap][4]
 
     // CUDA graphs (captured on a private stream, replayed on the context stream)
     bool graph_on = false;
@@ -229,7 +236,16 @@ int class_mask(vmap_ctx* ctx) {
     return m;
 }
 
-int grid_of(vmap_ctx* ctx, int c) { return ctx->n_sm * ctas_of(c) * ctx->gmult[c]; }
+bool uses_tc(vmap_ctx* ctx, int c) { return ctx->bf16 && c < 3; }
+bool uses_wide(vmap_ctx* ctx, int c) { return ctx->bf16 && c == 3; }
+
+// tile ranges of the width-128 weight-gradient kernel (WJOBS CTAs each)
+int wide_ranges(vmap_ctx* ctx) { return (ctx->n_sm + WJOBS - 1) / WJOBS * ctx->gmult[3]; }
+
+// CTA ranges that own a run slot (the builder's partition of the class's tiles)
+int grid_of(vmap_ctx* ctx, int c) {
+    return uses_wide(ctx, c) ? wide_ranges(ctx) : ctx->n_sm * ctas_of(c) * ctx->gmult[c];
+}
 
 TileArgs base_args(vmap_ctx* ctx) {
     TileArgs ta{};
@@ -282,7 +298,39 @@ cudaError_t launch_tile_bf16(int grid, cudaStream_t st, const StepParams& sp, co
     return cudaGetLastError();
 }
 
-bool uses_tc(vmap_ctx* ctx, int c) { return ctx->bf16 && c < 3; }
+WideArgs wide_args(vmap_ctx* ctx) {
+    TileArgs ta = base_args(ctx);
+    ta.tiles = ctx->tiles_d + 3LL * ctx->tile_cap;
+    ta.n_tiles = ctx->counts_d + BC_TILES + 3;
+    return WideArgs{ta, ctx->img_d, ctx->img_off_d, ctx->err_d, ctx->act_pp_d, ctx->tile_loss_d, 0};
+}
+
+template <int MODE>
+cudaError_t launch_wide_fb(vmap_ctx* ctx) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_wide_fb<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)WideFbCfg::BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    k_wide_fb<MODE><<<ctx->n_sm * ctx->gmult[3], NTHREADS, WideFbCfg::BYTES, ctx->stream>>>(ctx->sp, wide_args(ctx));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wide_dw(vmap_ctx* ctx, int loss_only) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_wide_dw, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)WideDwCfg::BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    WideArgs wa = wide_args(ctx);
+    wa.loss_only = loss_only;
+    k_wide_dw<<<WJOBS * wide_ranges(ctx), NTHREADS, WideDwCfg::BYTES, ctx->stream>>>(wa);
+    return cudaGetLastError();
+}
 
 // one width class of the step's tile kernel (FP32 SIMT, or BF16 tensor cores)
 template <int MODE>
@@ -291,6 +339,11 @@ cudaError_t launch_class(vmap_ctx* ctx, int c) {
     ta.tiles = ctx->tiles_d + (long long)c * ctx->tile_cap;
     ta.n_tiles = ctx->counts_d + BC_TILES + c;
     const int grid = grid_of(ctx, c);
+    if (uses_wide(ctx, c)) {
+        constexpr int BM = MODE == MODE_FORWARD ? MODE_FORWARD : MODE_TRAIN;
+        cudaError_t e = launch_wide_fb<BM>(ctx);
+        return e != cudaSuccess ? e : launch_wide_dw(ctx, BM == MODE_FORWARD);
+    }
     if (uses_tc(ctx, c)) {
         constexpr int BM = MODE == MODE_FORWARD ? MODE_FORWARD : MODE_TRAIN;
         Bf16Args ba{ta, ctx->img_d, ctx->img_off_d, ctx->err_d};
@@ -303,7 +356,7 @@ cudaError_t launch_class(vmap_ctx* ctx, int c) {
     return launch_tile_c<MODE>(c, grid, ctx->stream, ctx->sp, ta);
 }
 
-int class_mmax(vmap_ctx* ctx, int c) { return uses_tc(ctx, c) ? TM : mmax_of(c); }
+int class_mmax(vmap_ctx* ctx, int c) { return uses_tc(ctx, c) || uses_wide(ctx, c) ? TM : mmax_of(c); }
 
 // ---- the step's launches ------------------------------------------------------
 vmap_status launch_build_sample(vmap_ctx* ctx, int given) {
@@ -346,9 +399,22 @@ template <int MODE>
 vmap_status launch_tiles(vmap_ctx* ctx, int mask) {
     for (int c = 0; c < NCLASS; ++c) {
         if (!(mask & (1 << c))) continue;
-        const int pi = MODE == MODE_TRAIN ? prof_begin(ctx, PS_TILE + c) : -1;
-        cudaError_t e = launch_class<MODE>(ctx, c);
-        prof_end(ctx, pi);
+        cudaError_t e;
+        if (uses_wide(ctx, c)) {
+            constexpr int BM = MODE == MODE_FORWARD ? MODE_FORWARD : MODE_TRAIN;
+            int pi = MODE == MODE_TRAIN ? prof_begin(ctx, PS_TILE + c) : -1;
+            e = launch_wide_fb<BM>(ctx);
+            prof_end(ctx, pi);
+            if (e == cudaSuccess) {
+                pi = MODE == MODE_TRAIN ? prof_begin(ctx, PS_WIDE_DW) : -1;
+                e = launch_wide_dw(ctx, BM == MODE_FORWARD);
+                prof_end(ctx, pi);
+            }
+        } else {
+            const int pi = MODE == MODE_TRAIN ? prof_begin(ctx, PS_TILE + c) : -1;
+            e = launch_class<MODE>(ctx, c);
+            prof_end(ctx, pi);
+        }
         if (e != cudaSuccess)
             return fail(ctx, VMAP_ERR_CUDA, "tile kernel (H=%d) failed: %s", hidden_of(c), cudaGetErrorString(e));
     }
@@ -417,6 +483,22 @@ vmap_status replay(vmap_ctx* ctx, cudaGraphExec_t g, int slot) {
 // given == NULL the rays are picked from the objects' pools; otherwise given
 // holds sum_k R_k records (object-major, active objects with R_k > 0, in
 // index order) in memory of the kind `kind`, which are staged on the device.
+// Activation records of the width-128 path for `need` tiles. The buffer
+// only grows (by at least a quarter); its address is published through
+// act_pp_d, which captured graphs read at replay.
+vmap_status grow_act(vmap_ctx* ctx, long long need) {
+    const long long cap = std::max(need, ctx->act_cap + ctx->act_cap / 4) + 8;
+    CU(cudaStreamSynchronize(ctx->stream));   // no kernel still uses the old buffer
+    if (ctx->act_d) CU(cudaFree(ctx->act_d));
+    ctx->act_d = nullptr;
+    ctx->act_cap = 0;
+    CU(cudaMalloc((void**)&ctx->act_d, (size_t)cap * WideAct::BYTES));
+    ctx->act_cap = cap;
+    // pageable source: staged before the call returns
+    CU(cudaMemcpyAsync(ctx->act_pp_d, &ctx->act_d, sizeof(unsigned char*), cudaMemcpyHostToDevice, ctx->stream));
+    return VMAP_OK;
+}
+
 vmap_status sample_impl(vmap_ctx* ctx, const int* rays_per_object, const float* given, cudaMemcpyKind kind) {
     if (!ctx || !rays_per_object) return fail(ctx, VMAP_ERR_ARG, "null argument");
     const int K = (int)ctx->objs.size();
@@ -437,6 +519,8 @@ vmap_status sample_impl(vmap_ctx* ctx, const int* rays_per_object, const float* 
         return fail(ctx, VMAP_ERR_CAPACITY, "%lld rays exceed max_rays_total %d", rays, ctx->cfg.max_rays_total);
     for (int c = 0; c < NCLASS; ++c)
         if (tiles[c] > ctx->tile_cap) return fail(ctx, VMAP_ERR_CAPACITY, "too many tiles");
+    if (uses_wide(ctx, 3) && tiles[3] > ctx->act_cap)
+        if (vmap_status s = grow_act(ctx, tiles[3])) return s;
     ctx->req_h.assign(rays_per_object, rays_per_object + K);
     if (K) CU(cudaMemcpyAsync(ctx->req_d, ctx->req_h.data(), sizeof(int) * K, cudaMemcpyHostToDevice, ctx->stream));
     ctx->batch_given = given != nullptr;
@@ -559,8 +643,11 @@ vmap_status vmap_init_objects(vmap_ctx** out, const vmap_config* cfg, void* cuda
     ALLOC(ctx->err_d, sizeof(int));
     ALLOC(ctx->img_off_d, sizeof(long long) * K);
     if (ctx->bf16) {
-        ctx->img_cap = (long long)K * ((img_count(64) + 63) & ~63LL);
+        // img_count(H) - param_count(H) = 11 H - 4 <= 1408, plus 64-element alignment per object
+        ctx->img_cap = ctx->param_cap + 1536LL * K;
         ALLOC(ctx->img_d, sizeof(__nv_bfloat16) * ctx->img_cap);
+        ALLOC(ctx->act_pp_d, sizeof(unsigned char*));
+        ALLOC(ctx->tile_loss_d, sizeof(float) * 4 * (size_t)ctx->tile_cap);
     }
 #undef ALLOC
     e = cudaMemsetAsync(ctx->steps_d, 0, sizeof(int) * K, ctx->stream);
@@ -570,6 +657,7 @@ vmap_status vmap_init_objects(vmap_ctx** out, const vmap_config* cfg, void* cuda
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->counts_d, 0, sizeof(int) * BC_N, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->err_d, 0, sizeof(int), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->img_off_d, 0xFF, sizeof(long long) * K, ctx->stream);
+    if (e == cudaSuccess && ctx->act_pp_d) e = cudaMemsetAsync(ctx->act_pp_d, 0, sizeof(unsigned char*), ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return bail(VMAP_ERR_CUDA);
     *out = ctx;
@@ -585,7 +673,7 @@ vmap_status vmap_destroy(vmap_ctx* ctx) {
                     ctx->params_d, ctx->wt_d,     ctx->m_d,      ctx->v_d,     ctx->pool_d,   ctx->pick_d,
                     ctx->t_d,      ctx->bobj_d,   ctx->bray_d,   ctx->tiles_d, ctx->flags_d,  ctx->part_d,
                     ctx->items_d,  ctx->counts_d, ctx->given_d,  ctx->loss_d,  ctx->err_d,  ctx->img_off_d,
-                    ctx->img_d};
+                    ctx->img_d,    ctx->act_d,    ctx->act_pp_d, ctx->tile_loss_d};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& p : ctx->pending) {
@@ -645,7 +733,7 @@ vmap_status vmap_add_object(vmap_ctx* ctx, const vmap_object_desc* d, const floa
     k_shadow<<<16, 256, 0, ctx->stream>>>(ctx->params_d + poff, ctx->wt_d + woff, d->hidden);
     CHECK_LAUNCH("k_shadow");
     long long ioff = -1;
-    if (ctx->bf16 && d->hidden <= 64) {
+    if (ctx->bf16) {
         ioff = ctx->img_used;
         if (ioff + img_count(d->hidden) > ctx->img_cap) return fail(ctx, VMAP_ERR_CAPACITY, "weight image arena full");
         k_image<<<1, 256, 0, ctx->stream>>>(ctx->params_d + poff, ctx->img_d + ioff, d->hidden);

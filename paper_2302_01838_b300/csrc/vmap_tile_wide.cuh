@@ -1,0 +1,543 @@
+// Tensor-core training path for hidden width 128 (the background model of a
+// room, section 3.2 / 4.1), in two kernels.
+//
+// One CTA cannot hold a width-128 object's BF16 weights (124 KB), the four
+// hidden activation tiles the weight gradients need, and the gradient
+// accumulators (496 of the 512 TMEM columns) at once. The step is split:
+//
+//   k_wide_fb  per tile of <= 128 samples: encoding, forward MMAs (weights
+//              resident in shared memory), FP32 rendering and losses, and the
+//              backward input-gradient MMAs dZ_l = (dZ_{l+1} W_{l+1}) * [h_l > 0].
+//              Every GEMM operand it forms (encoding, h1..h4, dY, dZ1..dZ4;
+//              BF16, core-matrix layout) is streamed to an activation buffer,
+//              284 KB per tile, with the tile's loss sums.
+//   k_wide_dw  weight gradients dW_l = sum over samples of dZ_l^T h_{l-1} as
+//              split-K MMAs: CTA (range r, layer job j) streams job j's two
+//              operands of every tile in range r through a double-buffered
+//              stage and accumulates in TMEM; bias gradients are column sums
+//              of the same BF16 operand tiles, in FP32, in a fixed order. At
+//              the end of each object run the CTA writes its layer's slice of
+//              the run slot, which the reduce kernel sums in slot order.
+//
+// The MMA shapes and descriptor conventions are those of vmap_tc.cuh.
+#pragma once
+#include <cuda_bf16.h>
+
+#include "vmap_common.cuh"
+#include "vmap_tc.cuh"
+#include "vmap_tile_bf16.cuh"
+#include "vmap_tile_fp32.cuh"
+
+namespace vmapk {
+
+constexpr int WH = 128;       // hidden width of this path
+constexpr int WJOBS = 5;      // weight-gradient jobs: W1, W2, W3, W4, W5
+
+// per-tile activation record (bytes), every operand a core-matrix tile of 128 rows
+struct WideAct {
+    static constexpr int G0 = 0;                                  // encoding [128][96]
+    static constexpr int HL = G0 + TM * DINP * 2;                 // h1..h4 [128][128]
+    static constexpr int DY = HL + 4 * TM * WH * 2;               // dL/dy [128][16]
+    static constexpr int DZ = DY + TM * 16 * 2;                   // dZ1..dZ4 [128][128]
+    static constexpr long long BYTES = DZ + 4 * TM * WH * 2;      // 290,816
+    __host__ __device__ static constexpr int h(int l) { return HL + l * TM * WH * 2; }
+    __host__ __device__ static constexpr int dz(int l) { return DZ + l * TM * WH * 2; }
+};
+
+struct WideFbCfg {
+    static constexpr int W1B = WH * DINP * 2, WHB = WH * WH * 2, W5B = 16 * WH * 2;
+    static constexpr int WIMG = 0;                                // weight image (as in global memory)
+    static constexpr int WIMG_BYTES = W1B + 3 * WHB + W5B;        // 126,976
+    static constexpr int G0 = WIMG + WIMG_BYTES;                  // [128][96]; dY [128][16] after layer 1
+    static constexpr int HA = G0 + TM * DINP * 2;                 // current h [128][128]
+    static constexpr int DZ = HA + TM * WH * 2;                   // current dZ [128][128]
+    static constexpr int MASK = DZ + TM * WH * 2;                 // [4][128][4] u32: bits of h_l > 0
+    static constexpr int XT = MASK + 4 * TM * 16;                 // [3][128] f32
+    static constexpr int TSO = XT + 3 * TM * 4;                   // [128]
+    static constexpr int YB = TSO + TM * 4;                       // [4][128]
+    static constexpr int RAYS = YB + 4 * TM * 4;                  // [RTMAX][RAYF]
+    static constexpr int LOSS = RAYS + RTMAX * RAYF * 4;          // [4]
+    static constexpr int MBAR = LOSS + 16;
+    static constexpr int TSLOT = MBAR + 8;
+    static constexpr int BYTES = TSLOT + 8;
+    static constexpr int NCOLS = 128;
+    static_assert(BYTES <= 232448, "shared memory of one CTA");
+};
+
+struct WideDwCfg {
+    static constexpr int STAGE = 65536;                           // operand A at +0, operand B at +32 KB
+    static constexpr int NST = 2;
+    static constexpr int BSUM = NST * STAGE;                      // [16][128] f32 bias partials
+    static constexpr int MBAR = BSUM + 16 * 128 * 4;              // [NST]
+    static constexpr int TSLOT = MBAR + 8 * NST;
+    static constexpr int BYTES = TSLOT + 16;
+    static constexpr int NCOLS = 128;
+};
+
+struct WideArgs {
+    TileArgs t;
+    const __nv_bfloat16* img;     // tensor-core weight images (arena)
+    const long long* img_off;     // per object: element offset of its image
+    int* err;                     // set to 1 when a bounded wait gives up
+    unsigned char* const* act;    // device cell holding the activation buffer (tile-indexed)
+    float* tile_loss;             // [tiles][4]: depth, colour, occupancy sums of each tile
+    int loss_only;                // k_wide_dw: only fold the tile losses into the run slots
+};
+
+// bits (v[j] > 0) of 8 values, placed at bit offset `at` of a 64-bit word
+__device__ __forceinline__ unsigned long long pos_bits(const float (&v)[8], int at) {
+    unsigned b = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) b |= (v[j] > 0.f ? 1u : 0u) << j;
+    return (unsigned long long)b << at;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(NTHREADS, 1) k_wide_fb(StepParams sp, WideArgs wa) {
+    using C = WideFbCfg;
+    constexpr bool GRAD = MODE == MODE_TRAIN;
+    const TileArgs& ta = wa.t;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char* W1 = sm + C::WIMG;
+    unsigned char* Wh[3] = {W1 + C::W1B, W1 + C::W1B + C::WHB, W1 + C::W1B + 2 * C::WHB};
+    unsigned char* W5 = W1 + C::W1B + 3 * C::WHB;
+    unsigned char* G0 = sm + C::G0;
+    unsigned char* DYt = sm + C::G0;
+    unsigned char* HA = sm + C::HA;
+    unsigned char* DZ = sm + C::DZ;
+    uint32_t* mask = reinterpret_cast<uint32_t*>(sm + C::MASK);
+    float* xt = reinterpret_cast<float*>(sm + C::XT);
+    float* tsm = reinterpret_cast<float*>(sm + C::TSO);
+    float* yb = reinterpret_cast<float*>(sm + C::YB);
+    float* rays = reinterpret_cast<float*>(sm + C::RAYS);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + C::MBAR);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + C::TSLOT);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int q = warp & 3, hf = warp >> 2;
+    const int row = q * 32 + (tid & 31);
+    unsigned char* act = GRAD ? *wa.act : nullptr;
+
+    if (tid == 0) mbar_init(mbar, 1);
+    if (warp == 0) tmem_alloc(tslot, C::NCOLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t tl_lane = tmem + ((uint32_t)(q * 32) << 16);
+    uint32_t phase = 0;
+    bool abort = false;
+
+    auto wait_mma = [&]() {
+        const bool ok = mbar_wait(mbar, phase, MMA_WAIT_LIMIT);
+        phase ^= 1;
+        if (__syncthreads_or(!ok)) {
+            abort = true;
+            if (tid == 0) atomicExch(wa.err, 1);
+        }
+        tc_fence_after();
+    };
+    auto sync_for_mma = [&]() {
+        tmem_ld_wait();
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+    };
+    // this thread's 64 accumulator columns (lane = row, columns hf*64 ..)
+    auto load_acc = [&](float (&v)[64]) {
+        float a[16];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            tmem_ld16(tl_lane + hf * 64 + 16 * c, a);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[16 * c + i] = a[i];
+        }
+        tmem_ld_wait();
+    };
+
+    const long long n_tiles = *ta.n_tiles;
+    const long long t0 = (long long)blockIdx.x * n_tiles / gridDim.x;
+    const long long t1 = (long long)(blockIdx.x + 1) * n_tiles / gridDim.x;
+
+#pragma unroll 1
+    for (long long tl = t0; tl < t1 && !abort; ++tl) {
+        const TileDev td = ta.tiles[tl];
+        const int k = td.obj, nr = td.nr;
+        const bool first = tl == t0 || ta.tiles[tl - 1].obj != k;
+        const ObjDev& ob = ta.objs[k];
+        const int S = ob.S, M = nr * S;
+        const long long sbase = ta.obs[k].sample_off + (long long)(td.ray0 - ta.obs[k].ray_off) * S;
+        const float* P = ta.params + ob.param_off;
+        const float cx = ob.c[0], cy = ob.c[1], cz = ob.c[2], sc = ob.scale;
+        unsigned char* at = GRAD ? act + (long long)tl * WideAct::BYTES : nullptr;
+
+        for (int r = tid; r < nr; r += blockDim.x) {
+            const float* rec = ta.pool + (ta.obs[k].src_off + ta.pick[td.ray0 + r]) * REC;
+            float* d = rays + r * RAYF;
+#pragma unroll
+            for (int u = 0; u < 11; ++u) d[u] = rec[u];
+        }
+        if (first) {
+            const uint4* src = reinterpret_cast<const uint4*>(wa.img + wa.img_off[k]);
+            uint4* dst = reinterpret_cast<uint4*>(W1);
+            for (int i = tid; i < C::WIMG_BYTES / 16; i += blockDim.x) dst[i] = src[i];
+        }
+        __syncthreads();
+        for (int m = tid; m < TM; m += blockDim.x) {
+            float x0 = 0.f, x1 = 0.f, x2 = 0.f, t = 0.f;
+            if (m < M) {
+                const float* d = rays + (m / S) * RAYF;
+                t = ta.tbuf[sbase + m];
+                x0 = (fmaf(t, d[3], d[0]) - cx) / sc;
+                x1 = (fmaf(t, d[4], d[1]) - cy) / sc;
+                x2 = (fmaf(t, d[5], d[2]) - cz) / sc;
+            }
+            tsm[m] = t;
+            xt[m] = x0;
+            xt[TM + m] = x1;
+            xt[2 * TM + m] = x2;
+        }
+        __syncthreads();
+        // ---- encoding -> G0 (and the activation record) ----------------------
+        for (int f = tid; f < TM * (DINP / 8); f += blockDim.x) {
+            const int m = f % TM, ch = f / TM;
+            const float x0 = xt[m], x1 = xt[TM + m], x2 = xt[2 * TM + m];
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int c = ch * 8 + u;
+                float val;
+                if (c < 3) {
+                    val = c == 0 ? x0 : c == 1 ? x1 : x2;
+                } else if (c < DIN) {
+                    const int j = c < 3 + NF ? c - 3 : c - 3 - NF;
+                    const float p = red2pi(fmaf(sp.B[3 * j + 2], x2, fmaf(sp.B[3 * j + 1], x1, sp.B[3 * j] * x0)));
+                    val = c < 3 + NF ? __sinf(p) : __cosf(p);
+                } else {
+                    val = c == DIN ? 1.f : 0.f;
+                }
+                v[u] = val;
+            }
+            const int off = cm_off(m, ch * 8, DINP);
+            st_bf16x8(G0, off, v);
+            if (GRAD) *reinterpret_cast<uint4*>(at + WideAct::G0 + off) = *reinterpret_cast<const uint4*>(G0 + off);
+        }
+        sync_for_mma();
+
+        // ---- forward -----------------------------------------------------------
+        if (tid == 0) {
+#pragma unroll
+            for (int kc = 0; kc < DINP / 16; ++kc)
+                mma_bf16(tmem, desc_kmajor(G0, DINP, 16 * kc), desc_kmajor(W1, DINP, 16 * kc),
+                         idesc_bf16(TM, WH, 0, 0), kc > 0);
+            mma_commit(mbar);
+        }
+        wait_mma();
+        if (abort) break;
+#pragma unroll 1
+        for (int l = 0; l < 4; ++l) {
+            float v[64];
+            load_acc(v);
+            const float* bias = P + b_off(WH, l) + hf * 64;
+            unsigned long long bits = 0;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                float u[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) u[j] = fmaxf(v[8 * c + j] + bias[8 * c + j], 0.f);
+                bits |= pos_bits(u, 8 * c);
+                const int off = cm_off(row, hf * 64 + 8 * c, WH);
+                st_bf16x8(HA, off, u);
+                if (GRAD) *reinterpret_cast<uint4*>(at + WideAct::h(l) + off) = *reinterpret_cast<const uint4*>(HA + off);
+            }
+            *reinterpret_cast<uint2*>(mask + (l * TM + row) * 4 + hf * 2) =
+                make_uint2((uint32_t)bits, (uint32_t)(bits >> 32));
+            sync_for_mma();
+            if (tid == 0) {
+                if (l < 3) {
+#pragma unroll
+                    for (int kc = 0; kc < WH / 16; ++kc)
+                        mma_bf16(tmem, desc_kmajor(HA, WH, 16 * kc), desc_kmajor(Wh[l], WH, 16 * kc),
+                                 idesc_bf16(TM, WH, 0, 0), kc > 0);
+                } else {
+#pragma unroll
+                    for (int kc = 0; kc < WH / 16; ++kc)
+                        mma_bf16(tmem, desc_kmajor(HA, WH, 16 * kc), desc_kmajor(W5, WH, 16 * kc),
+                                 idesc_bf16(TM, 16, 0, 0), kc > 0);
+                }
+                mma_commit(mbar);
+            }
+            wait_mma();
+            if (abort) break;
+        }
+        if (abort) break;
+        {
+            float v[8];
+            tmem_ld8(tl_lane, v);
+            tmem_ld_wait();
+            if (hf == 0) {
+                const float* b5 = P + b_off(WH, 4);
+#pragma unroll
+                for (int j = 0; j < NOUT; ++j) yb[j * TM + row] = v[j] + b5[j];
+            }
+        }
+        __syncthreads();
+
+        // ---- rendering, loss, dL/dy (FP32) ---------------------------------------
+        const float invR = 1.f / (float)ta.obs[k].R;
+        for (int r = warp; r < nr; r += NTHREADS / 32)
+            render_ray_warp<GRAD, TM>(sp, yb, tsm, rays + r * RAYF, r, S, invR);
+        for (int m = M + tid; m < TM; m += blockDim.x) {
+            yb[m] = 0.f; yb[TM + m] = 0.f; yb[2 * TM + m] = 0.f; yb[3 * TM + m] = 0.f;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+            for (int r = 0; r < nr; ++r) {
+                s0 += rays[r * RAYF + 13]; s1 += rays[r * RAYF + 14]; s2 += rays[r * RAYF + 15];
+            }
+            *reinterpret_cast<float4*>(wa.tile_loss + 4 * tl) = make_float4(s0, s1, s2, 0.f);
+        }
+        if (!GRAD) {
+            __syncthreads();
+            continue;
+        }
+        // dY -> BF16 [128][16] (columns 4..15 zero), over the dead encoding tile
+        for (int m = tid; m < TM * 2; m += blockDim.x) {
+            const int r = m % TM, half = m / TM;
+            float v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = (half == 0 && j < NOUT) ? yb[j * TM + r] : 0.f;
+            const int off = cm_off(r, half * 8, 16);
+            st_bf16x8(DYt, off, v);
+            *reinterpret_cast<uint4*>(at + WideAct::DY + off) = *reinterpret_cast<const uint4*>(DYt + off);
+        }
+        sync_for_mma();
+
+        // ---- backward: input gradients ------------------------------------------
+        if (tid == 0) {
+            mma_bf16(tmem, desc_kmajor(DYt, 16, 0), desc_mnmajor(W5, WH, 0), idesc_bf16(TM, WH, 0, 1), false);
+            mma_commit(mbar);
+        }
+#pragma unroll 1
+        for (int l = 3; l >= 0; --l) {
+            // accumulator = dZ_{l+2} W_{l+2} (dY W5 for l = 3); dZ_{l+1} = acc * [h_{l+1} > 0]
+            wait_mma();
+            if (abort) break;
+            float v[64];
+            load_acc(v);
+            const uint2 mb = *reinterpret_cast<const uint2*>(mask + (l * TM + row) * 4 + hf * 2);
+            const unsigned long long bits = ((unsigned long long)mb.y << 32) | mb.x;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                float u[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) u[j] = (bits >> (8 * c + j)) & 1ull ? v[8 * c + j] : 0.f;
+                const int off = cm_off(row, hf * 64 + 8 * c, WH);
+                st_bf16x8(DZ, off, u);
+                *reinterpret_cast<uint4*>(at + WideAct::dz(l) + off) = *reinterpret_cast<const uint4*>(DZ + off);
+            }
+            sync_for_mma();
+            if (l == 0) break;
+            if (tid == 0) {
+#pragma unroll
+                for (int kc = 0; kc < WH / 16; ++kc)
+                    mma_bf16(tmem, desc_kmajor(DZ, WH, 16 * kc), desc_mnmajor(Wh[l - 1], WH, 16 * kc),
+                             idesc_bf16(TM, WH, 0, 1), kc > 0);
+                mma_commit(mbar);
+            }
+        }
+        if (abort) break;
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, C::NCOLS);
+}
+
+// Weight-gradient jobs: operand A (M side, 128 lanes) and B (N side) of job j
+// inside a tile's activation record, their column counts, and N.
+struct WideJob {
+    int a_off, a_cc, a_bytes, b_off, b_cc, b_bytes, n;
+};
+__device__ __forceinline__ WideJob wide_job(int j) {
+    // j = 0..3: dW_{j+1} [out][in] = dZ_{j+1}^T a_j   (a_0 = encoding, a_j = h_j)
+    // j = 4:    dW5^T   [in][out] = h4^T dY
+    if (j == 0) return {WideAct::dz(0), WH, TM * WH * 2, WideAct::G0, DINP, TM * DINP * 2, DINP};
+    if (j < 4) return {WideAct::dz(j), WH, TM * WH * 2, WideAct::h(j - 1), WH, TM * WH * 2, WH};
+    return {WideAct::h(3), WH, TM * WH * 2, WideAct::DY, 16, TM * 16 * 2, 16};
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1) k_wide_dw(WideArgs wa) {
+    using C = WideDwCfg;
+    const TileArgs& ta = wa.t;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    float* bsum = reinterpret_cast<float*>(sm + C::BSUM);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + C::MBAR);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + C::TSLOT);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int q = warp & 3, hf = warp >> 2;
+    const int row = q * 32 + (tid & 31);
+    const int ranges = gridDim.x / WJOBS;
+    const int rg = blockIdx.x / WJOBS, j = blockIdx.x % WJOBS;
+    if (wa.loss_only && j != 0) return;
+    const WideJob jb = wide_job(j);
+    const unsigned char* act = wa.loss_only ? nullptr : *wa.act;
+    constexpr long long PC = param_count(WH);
+
+    if (!wa.loss_only) {
+        if (tid == 0)
+            for (int s = 0; s < C::NST; ++s) mbar_init(mbar + s, 1);
+        if (warp == 0) tmem_alloc(tslot, C::NCOLS);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = wa.loss_only ? 0u : *tslot;
+    uint32_t phase[C::NST] = {0, 0};
+    bool pend[C::NST] = {false, false};
+    bool abort = false;
+    auto wait_stage = [&](int s) {
+        if (!pend[s]) return;
+        const bool ok = mbar_wait(mbar + s, phase[s], MMA_WAIT_LIMIT);
+        phase[s] ^= 1;
+        pend[s] = false;
+        if (__syncthreads_or(!ok)) {
+            abort = true;
+            if (tid == 0) atomicExch(wa.err, 1);
+        }
+        tc_fence_after();
+    };
+
+    // bias partial sums: thread = (8-column chunk, 8-row group) of the bias operand
+    const int bchunk = tid & 15, brg = tid >> 4;
+    const int b_cc = j < 4 ? jb.a_cc : jb.b_cc;
+    const int b_src = j < 4 ? 0 : 32768;   // operand holding dZ (A) or dY (B) in the stage
+    float bs[8];
+    float lacc[3] = {0.f, 0.f, 0.f};
+    int g = 0;
+
+    const long long n_tiles = *ta.n_tiles;
+    const long long t0 = (long long)rg * n_tiles / ranges;
+    const long long t1 = (long long)(rg + 1) * n_tiles / ranges;
+#pragma unroll 1
+    for (long long tl = t0; tl < t1 && !abort; ++tl) {
+        const int k = ta.tiles[tl].obj;
+        const bool first = tl == t0 || ta.tiles[tl - 1].obj != k;
+        const bool last = tl + 1 == t1 || ta.tiles[tl + 1].obj != k;
+        if (first) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) bs[i] = 0.f;
+            lacc[0] = lacc[1] = lacc[2] = 0.f;
+        }
+        if (j == 0 && tid == 0) {
+            const float4 l4 = *reinterpret_cast<const float4*>(wa.tile_loss + 4 * tl);
+            lacc[0] += l4.x; lacc[1] += l4.y; lacc[2] += l4.z;
+        }
+        float* gp = ta.part + ta.tiles[tl].part;
+        if (!wa.loss_only) {
+            const int s = g & 1;
+            wait_stage(s);   // the MMAs that last read this stage are done
+            if (abort) break;
+            unsigned char* st = sm + s * C::STAGE;
+            const unsigned char* src = act + tl * WideAct::BYTES;
+            {
+                constexpr int NV = 32768 / 16 / NTHREADS;   // 8 vectors per thread per operand, at most
+                uint4 va[NV], vb[NV];
+                const int na = jb.a_bytes / 16, nb = jb.b_bytes / 16;
+#pragma unroll
+                for (int i = 0; i < NV; ++i) {
+                    const int ia = tid + i * NTHREADS, ib = tid + i * NTHREADS;
+                    if (ia < na) va[i] = *reinterpret_cast<const uint4*>(src + jb.a_off + 16 * ia);
+                    if (ib < nb) vb[i] = *reinterpret_cast<const uint4*>(src + jb.b_off + 16 * ib);
+                }
+#pragma unroll
+                for (int i = 0; i < NV; ++i) {
+                    const int ia = tid + i * NTHREADS, ib = tid + i * NTHREADS;
+                    if (ia < na) *reinterpret_cast<uint4*>(st + 16 * ia) = va[i];
+                    if (ib < nb) *reinterpret_cast<uint4*>(st + 32768 + 16 * ib) = vb[i];
+                }
+            }
+            fence_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+            if (tid == 0) {
+#pragma unroll
+                for (int kc = 0; kc < TM / 16; ++kc)
+                    mma_bf16(tmem, desc_mnmajor(st, jb.a_cc, 16 * kc), desc_mnmajor(st + 32768, jb.b_cc, 16 * kc),
+                             idesc_bf16(TM, jb.n, 1, 1), !(first && kc == 0));
+                mma_commit(mbar + s);
+            }
+            pend[s] = true;
+            ++g;
+            // bias partials from the BF16 operand (dZ, or dY for job 4)
+            if (bchunk * 8 < b_cc) {
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    float v[8];
+                    ld_bf16x8(st + b_src, cm_off(brg * 8 + r, bchunk * 8, b_cc), v);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) bs[i] += v[i];
+                }
+            }
+        }
+        if (!last) continue;
+        // ---- run end: write this job's slice of the run slot --------------------
+        if (j == 0 && tid == 0) {
+            gp[PC + 0] = lacc[0]; gp[PC + 1] = lacc[1]; gp[PC + 2] = lacc[2];
+            gp[PC + 3] = 0.f; gp[PC + 4] = 0.f; gp[PC + 5] = 0.f;
+        }
+        if (wa.loss_only) continue;
+        wait_stage(g & 1);          // older stage first, then the newest
+        wait_stage((g + 1) & 1);
+        if (abort) break;
+        if (j < 4) {
+            const int fan = j == 0 ? DIN : WH;
+            float* w = gp + w_off(WH, j) + (long long)row * fan;
+            const int half = jb.n / 2;
+#pragma unroll 1
+            for (int c0 = 0; c0 < half; c0 += 16) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + hf * half + c0, v);
+                tmem_ld_wait();
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int in = hf * half + c0 + i;
+                    if (in < fan) w[in] = v[i];
+                }
+            }
+        } else {
+            float v[8];
+            tmem_ld8(tmem + ((uint32_t)(q * 32) << 16), v);
+            tmem_ld_wait();
+            if (hf == 0) {
+#pragma unroll
+                for (int o = 0; o < NOUT; ++o) gp[w_off(WH, 4) + o * WH + row] = v[o];
+            }
+        }
+        if (bchunk * 8 < b_cc) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) bsum[brg * 128 + bchunk * 8 + i] = bs[i];
+        }
+        __syncthreads();
+        const int nb = j < 4 ? WH : NOUT;
+        if (tid < nb) {
+            float s = 0.f;
+            for (int r = 0; r < 16; ++r) s += bsum[r * 128 + tid];
+            gp[b_off(WH, j) + tid] = s;
+        }
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+    }
+    if (!wa.loss_only) {
+        tc_fence_before();
+        __syncthreads();
+        if (warp == 0) tmem_dealloc(tmem, C::NCOLS);
+    }
+}
+
+}  // namespace vmapk

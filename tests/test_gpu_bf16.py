@@ -1,16 +1,25 @@
 """The BF16 tensor-core path (tcgen05 MMAs, FP32 accumulation, FP32 master
-weights, moments, rendering and losses) against the FP64 oracle.
+weights, moments, rendering and losses).
 
-Stated error bounds (BF16 operands carry 8 significant bits):
-  * per-step loss: 1e-3 relative on the first step (the forward rounds its
-    operands only), and within 2e-2 relative of the oracle over 60 steps;
-  * gradients: relative L2 error per weight / bias tensor <= 5e-2;
-  * hidden width 128 runs the FP32 kernel inside a BF16 context (exact
-    FP32 parity)."""
+Implementation parity: against the BF16 rounding model (oracle/bf16_model.py:
+the FP64 oracle with the path's GEMM operands rounded to BF16), loss within
+MODEL_LOSS_RTOL and every weight / bias gradient tensor within MODEL_G_RTOL
+(relative L2); what remains is FP32 accumulation order, FP32 sin/cos before
+rounding and the rare rounding or ReLU decision that these flip.
+
+Precision (BF16 operands carry 8 significant bits), against the FP64 oracle:
+  * per-step loss: 1e-3 relative on the first step, and within 2e-2 of the
+    oracle over 60 steps (30 for hidden 128);
+  * gradients: relative L2 error per tensor <= 1e-1 for any batch, <= 5e-2
+    on batches of 100 rays or more (the error of a sum over few samples is
+    larger; the rounding model shows the same numbers there).
+Hidden width 128 runs as two kernels (forward / input gradients, then
+split-K weight gradients) under the same bounds."""
 import numpy as np
 import pytest
 import torch
 
+from oracle import bf16_model as bm
 from oracle import vmap_step as vs
 from paper_2302_01838_b300 import scenes
 from paper_2302_01838_b300.native import VMAP_BF16
@@ -18,6 +27,25 @@ from paper_2302_01838_b300.native import VMAP_BF16
 import vmap_harness as vh
 
 pytestmark = pytest.mark.gpu
+
+MODEL_LOSS_RTOL = 1e-5
+MODEL_G_RTOL = 1e-2
+
+
+def _check_against_oracles(cfg, o, k, R, step, L, g):
+    args = (cfg, np.asarray(o["init"], np.float64), o["H"])
+    pk, tk = vs.sample_object(cfg, o["pool"], R, o["n_surface"], o["n_strat"], k, step)
+    rays = o["pool"][pk].astype(np.float64)
+    geo = (rays, tk, np.asarray(o["center"], np.float64), float(o["scale"]))
+    m = bm.object_forward_backward(*args, *geo)
+    assert abs(L - m["loss"]) <= MODEL_LOSS_RTOL * m["loss"], (k, L, m["loss"])
+    em = vh.layer_errors(g, m["grad"], o["H"])
+    assert max(em) <= MODEL_G_RTOL, (k, o["H"], em)
+    f = vs.object_forward_backward(*args, *geo)
+    assert abs(L - f["loss"]) <= 1e-3 * f["loss"], (k, L, f["loss"])
+    ef = vh.layer_errors(g, f["grad"], o["H"])
+    assert max(ef) <= (5e-2 if R >= 100 else 1e-1), (k, o["H"], R, ef)
+    return max(em), max(ef)
 
 
 def test_bf16_gradients_and_loss_vs_oracle():
@@ -34,18 +62,70 @@ def test_bf16_gradients_and_loss_vs_oracle():
     assert vm.sync_status() == []
     L, gp = L.cpu().numpy(), gp.cpu().numpy()
     for k, o in enumerate(sc["objects"]):
-        pk, tk = vs.sample_object(cfg, o["pool"], R[k], o["n_surface"], o["n_strat"], k, 0)
-        res = vs.object_forward_backward(cfg, np.asarray(o["init"], np.float64), o["H"],
-                                         o["pool"][pk].astype(np.float64), tk,
-                                         np.asarray(o["center"], np.float64), float(o["scale"]))
         info = vm.object_info(k)
         g = gp[info["param_offset"]:info["param_offset"] + info["param_count"]]
-        errs = vh.layer_errors(g, res["grad"], o["H"])
-        if o["H"] == 128:
-            assert abs(L[k] - res["loss"]) <= 1e-5 * res["loss"] and max(errs) <= 1e-4
-        else:
-            assert abs(L[k] - res["loss"]) <= 1e-3 * res["loss"], (k, L[k], res["loss"])
-            assert max(errs) <= 5e-2, (k, o["H"], errs)
+        _check_against_oracles(cfg, o, k, R[k], 0, L[k], g)
+
+
+def _wide_scene(seed, n_small=2, bg_rays=1200):
+    """A room background (hidden 128, bg_rays rays: hundreds of tiles spread
+    over every CTA range) and n_small hidden-32 objects."""
+    rng = np.random.default_rng(seed)
+    bg = scenes.background_object(rng)
+    bg["rays"] = bg_rays
+    objs = [bg]
+    for _ in range(n_small):
+        o = scenes.make_object(rng, (1, 2), 0.1, 0.3, 0.2, H=32, per_view=200)
+        o["rays"] = 100
+        objs.append(o)
+    for o in objs:
+        o["init"] = scenes.init_weights(rng, o["H"])
+        o["n_surface"], o["n_strat"] = 10, 12
+    return dict(objects=objs, B=scenes.make_B(seed + 1000), seed=seed)
+
+
+def test_bf16_width_128_background_gradients_vs_oracle():
+    sc = _wide_scene(45)
+    cfg = vh.oracle_config(sc)
+    K = len(sc["objects"])
+    R = [o["rays"] for o in sc["objects"]]
+    vm = vh.library_context(sc, precision=VMAP_BF16)
+    vm.sample_rays(R)
+    L = torch.empty(K, device="cuda")
+    vm.forward(L)
+    gp = torch.zeros(vm.arena_size(), device="cuda")
+    vm.backward(gp)
+    assert vm.sync_status() == []
+    L, gp = L.cpu().numpy(), gp.cpu().numpy()
+    for k, o in enumerate(sc["objects"]):
+        info = vm.object_info(k)
+        g = gp[info["param_offset"]:info["param_offset"] + info["param_count"]]
+        _check_against_oracles(cfg, o, k, R[k], 0, L[k], g)
+    # the training step's loss equals the forward's (same batch, before the update)
+    lt = torch.empty(K, device="cuda")
+    vm.train_step(lt)
+    assert np.array_equal(lt.cpu().numpy(), L)
+
+
+def test_bf16_width_128_training_follows_the_oracle():
+    sc = _wide_scene(46, n_small=1, bg_rays=150)
+    cfg = vh.oracle_config(sc)
+    ost = vh.oracle_states(sc)
+    vm = vh.library_context(sc, precision=VMAP_BF16)
+    K = len(ost)
+    R = [o["rays"] for o in sc["objects"]]
+    loss = torch.empty(K, device="cuda")
+    for step in range(30):
+        vm.sample_rays(R)
+        vm.train_step(loss)
+        Lo = vs.train_step(cfg, ost, R)
+        rel = np.abs(loss.cpu().numpy() - Lo) / np.abs(Lo)
+        assert np.all(rel <= 2e-2), (step, rel)
+    assert vm.sync_status() == []
+    for k in range(K):
+        p = vm.get_object_state(k)[0].cpu().numpy()
+        errs = vh.layer_errors(p, ost[k].params, ost[k].H)
+        assert max(errs) <= 5e-2, (k, errs)
 
 
 def test_bf16_training_follows_the_oracle():
@@ -81,6 +161,14 @@ def test_bf16_graph_replay_matches_eager_bitwise():
     for _ in range(3):
         a.sample_rays(R); a.train_step(la)
         b.sample_rays(R); b.train_step(lb)
+        assert torch.equal(la, lb)
+    assert torch.equal(a.get_params(), b.get_params())
+    # more width-128 rays than the activation buffer holds: it grows, and the
+    # captured graph (which reads the buffer's address from device memory) stays valid
+    R2 = [r * 6 if o["H"] == 128 else r for r, o in zip(R, sc["objects"])]
+    for _ in range(2):
+        a.sample_rays(R2); a.train_step(la)
+        b.sample_rays(R2); b.train_step(lb)
         assert torch.equal(la, lb)
     assert torch.equal(a.get_params(), b.get_params())
 
