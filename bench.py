@@ -1,12 +1,18 @@
 #!/usr/bin/env python
 """Throughput of the vectorised object-MLP training step (vMAP, section 3.2).
 
-Workload (default, "room50"): 50 object MLPs (hidden 32, rays per object
-log-uniform in 32-600) plus one background MLP (hidden 128, 1,200 rays), 22
-samples per ray, every object present (the steady state after the last
-incremental insertion), FP32. One step = ray picking + depth-guided sampling
-+ encoding + MLP forward + rendering + losses + backward + Adam for all 51
-objects.
+Workload ("room50"): 50 object MLPs (hidden 32, rays per object log-uniform
+in 32-600) plus one background MLP (hidden 128, 1,200 rays), 22 samples per
+ray, every object present (the steady state after the last incremental
+insertion). One step = ray picking + depth-guided sampling + encoding + MLP
+forward + rendering + losses + backward + Adam for all 51 objects.
+
+Default path: BF16 tensor-core GEMMs with FP32 accumulation, master weights,
+moments, rendering and losses, the step replayed as CUDA graphs, launch
+shapes autotuned. The same line reports the plain FP32 path on the same
+workload, a profiled kernel-by-kernel pass (per-kernel time and the roofline
+of the dominant kernel), and the time to a held-out depth-L1 target of
+plain FP32 vs BF16 + batched vs BF16 + batched + warm start.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -37,9 +43,13 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1500)
     ap.add_argument("--warmup", type=int, default=20)
-    ap.add_argument("--precision", choices=["fp32", "bf16"], default="fp32",
-                    help="fp32: plain FP32 SIMT path; bf16: tcgen05 BF16 GEMMs (hidden <= 64)")
+    ap.add_argument("--precision", choices=["fp32", "bf16"], default="bf16",
+                    help="bf16: tcgen05 BF16 GEMMs, FP32 accumulation (default); fp32: plain FP32 SIMT path")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="launch kernel by kernel instead of graph replay")
+    ap.add_argument("--prof-steps", type=int, default=200, help="steps of the profiled kernel-by-kernel pass")
+    ap.add_argument("--fp32-steps", type=int, default=300, help="steps of the FP32 comparison (0: skip)")
+    ap.add_argument("--no-ttd", action="store_true", help="skip the time-to-depth-L1 comparison")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=12, help="oracle steps of the CPU baseline sample")
@@ -65,12 +75,22 @@ def samples_per_step(scene):
     return sum(o["rays"] * (o["n_surface"] + o["n_strat"]) for o in scene["objects"])
 
 
-def flops_per_sample(H):
+def flops_per_sample(H, part="all"):
     """Algorithmic flops of one sample's forward + backward MLP GEMMs:
     forward F = 93H + 3H^2 + 4H MACs, weight gradient F MACs, input gradient
-    3H^2 + 4H MACs (layer 1 skipped); 2 flops per MAC."""
+    3H^2 + 4H MACs (layer 1 skipped); 2 flops per MAC. part = "fb" (forward
+    and input gradients) or "dw" (weight gradients) splits the sum the way
+    the width-128 path splits its two kernels."""
     F = 93 * H + 3 * H * H + 4 * H
-    return 2 * (2 * F + 3 * H * H + 4 * H)
+    fb, dw = 2 * (F + 3 * H * H + 4 * H), 2 * F
+    return {"all": fb + dw, "fb": fb, "dw": dw}[part]
+
+
+def kernel_flops(name, objs):
+    """Algorithmic flops of one launch of a tile kernel on the workload."""
+    H = int(name.split("<")[1].rstrip(">"))
+    part = "fb" if name.startswith("k_wide_fb") else "dw" if name.startswith("k_wide_dw") else "all"
+    return sum(o["rays"] * (o["n_surface"] + o["n_strat"]) * flops_per_sample(H, part) for o in objs if o["H"] == H)
 
 
 def measured_peaks():
@@ -214,13 +234,63 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def make_context(sc, precision, autotune, reps=3):
+    from paper_2302_01838_b300.api import VMap
+    from paper_2302_01838_b300.native import VMAP_BF16, VMAP_FP32
+    objs = sc["objects"]
+    R = [o["rays"] for o in objs]
+    prec = VMAP_BF16 if precision == "bf16" else VMAP_FP32
+    vm = VMap(max_objects=len(objs) + 8, max_rays_total=2 * sum(R),
+              max_pool_rays=sum(o["pool"].shape[0] for o in objs) + 16, B=sc["B"], seed=sc["seed"], precision=prec)
+    for k, o in enumerate(objs):
+        vm.add_object(o["pool"], hidden=o["H"], center=o["center"], scale=float(o["scale"]),
+                      n_surface=o["n_surface"], n_strat=o["n_strat"], init_params=o["init"], stream_id=k)
+    if autotune:
+        vm.autotune(R, reps=reps)
+    return vm
+
+
+def timed_steps(vm, R, steps, flush, loss):
+    """Device milliseconds of `steps` steps, L2 flushed between steps (outside the intervals)."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(float(i))
+        ev[i][0].record()
+        vm.sample_rays(R)
+        vm.train_step(loss)
+        ev[i][1].record()
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev)
+
+
+def time_to_depth(seed=100, n_train=1000, train_steps=1000, epochs=100, n_held=200, target=0.04):
+    """Reduced form of the warm-start experiment (paper_2302_01838_b300.warmstart):
+    steps and CUDA-event train time until the mean held-out depth-L1 < target."""
+    from paper_2302_01838_b300 import scenes, warmstart as ws
+    t0 = time.time()
+    X, T = ws.produce_dataset(n_train, seed, train_steps)
+    hyp = ws.train_hypernet(X, T, epochs=epochs)
+    prep = time.time() - t0
+    held = scenes.scene_shapes(seed + 10 ** 6, n_held, offmask=ws.OFFMASK)
+    out = {"target_m": target, "heldout_objects": n_held, "train_shapes": n_train,
+           "train_steps_per_shape": train_steps, "hypernet_epochs": epochs, "prep_s": round(prep, 2)}
+    for form in ("plain", "batched", "warm"):
+        r = ws.time_to_target(held["objects"], held["B"], seed, form, hyper=hyp if form == "warm" else None,
+                              target=target)
+        out[form] = {"reached": r["reached"], "steps": r["steps"], "train_ms": round(r["train_ms"], 2),
+                     "depth_l1_m": round(r["final_depth_l1"], 5)}
+    out["forms"] = {"plain": "FP32, kernel by kernel, seeded random init",
+                    "batched": "BF16 tensor cores, CUDA graphs, autotuned, seeded random init",
+                    "warm": "as batched, init predicted by the set-encoder hypernetwork"}
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
     import torch.distributed as dist
     from paper_2302_01838_b300 import sharding
-    from paper_2302_01838_b300.api import VMap
-    from paper_2302_01838_b300.native import VMAP_BF16, VMAP_FP32
 
     rank, world, local = dist_env()
     if world > 1:
@@ -230,47 +300,41 @@ def run_ours(args):
     objs = sc["objects"]
     R = [o["rays"] for o in objs]
     K = len(objs)
-    prec = VMAP_BF16 if args.precision == "bf16" else VMAP_FP32
-    vm = VMap(max_objects=K + 8, max_rays_total=2 * sum(R), max_pool_rays=sum(o["pool"].shape[0] for o in objs) + 16,
-              B=sc["B"], seed=sc["seed"], precision=prec)
-    for k, o in enumerate(objs):
-        vm.add_object(o["pool"], hidden=o["H"], center=o["center"], scale=float(o["scale"]),
-                      n_surface=o["n_surface"], n_strat=o["n_strat"], init_params=o["init"], stream_id=k)
     sps = samples_per_step(sc)
+    vm = make_context(sc, args.precision, not args.no_autotune)
+    launch = vm.get_launch() if not args.no_autotune else None
     loss = torch.empty(K, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, device="cuda")
-    launch = None
-    if not args.no_autotune:
-        vm.autotune(R, reps=3)
-        launch = vm.get_launch()
+
+    # ---- profiled kernel-by-kernel pass: per-kernel device time ----------------
+    for _ in range(3):
+        vm.sample_rays(R)
+        vm.train_step(loss)
+    vm.profile_reset()
+    vm.profile_enable(True)
+    timed_steps(vm, R, args.prof_steps, flush, loss)
+    vm.profile_enable(False)
+    prof = vm.profile()
+    launches_per_step = sum(n for n, _ in prof.values()) / args.prof_steps
+
+    # ---- the timed region -------------------------------------------------------
+    if not args.no_graph:
+        vm.set_graph(True)
     for _ in range(max(args.warmup, 3)):
         vm.sample_rays(R)
         vm.train_step(loss)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-
     clocks = ClockSampler(local)
     clocks.start()
-    vm.profile_reset()
-    vm.profile_enable(True)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for i in range(args.steps):
-        flush.fill_(float(i))            # L2 flush between timed steps (not timed)
-        ev[i][0].record()
-        vm.sample_rays(R)
-        vm.train_step(loss)
-        ev[i][1].record()
-        if i % 250 == 249:
-            vm.profile()                 # fold the pending kernel events (synchronises, outside the intervals)
-    torch.cuda.synchronize()
+    ms = timed_steps(vm, R, args.steps, flush, loss)
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    vm.profile_enable(False)
-    prof = vm.profile()
-    ms_max = sharding.max_over_ranks(sum(a.elapsed_time(b) for a, b in ev))
+    ms_max = sharding.max_over_ranks(ms)
     assert np.all(np.isfinite(loss.cpu().numpy())), "non-finite loss"
+    assert vm.sync_status() == [], "objects frozen during the bench"
 
     # ---- end to end through the C ABI with host buffers --------------------
     rng = np.random.default_rng(rank_seed(rank))
@@ -291,28 +355,41 @@ def run_ours(args):
         vm.train_step_host(host_batches[i % n_batches], R, loss_h)
         e2e_s += time.perf_counter() - t0
     e2e_s = sharding.max_over_ranks(e2e_s)
+    vm.close()
+
+    # ---- the plain FP32 path on the same workload --------------------------------
+    fp32 = None
+    if args.precision == "bf16" and args.fp32_steps > 0:
+        v32 = make_context(sc, "fp32", not args.no_autotune)
+        if not args.no_graph:
+            v32.set_graph(True)
+        for _ in range(3):
+            v32.sample_rays(R)
+            v32.train_step(loss)
+        ms32 = sharding.max_over_ranks(timed_steps(v32, R, args.fp32_steps, flush, loss))
+        v32.close()
+        fp32 = {"value": world * sps * args.fp32_steps / (ms32 * 1e-3), "unit": UNIT,
+                "ms_per_step": ms32 / args.fp32_steps, "steps_per_s": 1e3 * args.fp32_steps / ms32,
+                "steps": args.fp32_steps}
 
     if rank == 0:
         peaks = measured_peaks()
         props = torch.cuda.get_device_properties(local)
         sm_max = peaks.get("sm_max_mhz", 2032.0)
         fp32_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-        # dominant kernel by device time
-        tiles = {k: v for k, v in prof.items() if k.startswith("k_tile")}
+        tiles = {k: v for k, v in prof.items() if k.startswith(("k_tile", "k_wide"))}
         dom = max(tiles, key=lambda k: tiles[k][1])
-        Hd = int(dom.split("<")[1].rstrip(">"))
-        flops = sum(o["rays"] * (o["n_surface"] + o["n_strat"]) * flops_per_sample(o["H"])
-                    for o in objs if o["H"] == Hd)
-        launches, dom_ms = tiles[dom]
-        achieved = flops / (dom_ms / launches * 1e-3) / 1e12
-        traffic = traffic_for(dom)
-        tensor = dom.startswith("k_tile_bf16")
+        flops = kernel_flops(dom, objs)
+        n_l, dom_ms = tiles[dom]
+        achieved = flops / (dom_ms / n_l * 1e-3) / 1e12
+        tensor = dom.startswith(("k_tile_bf16", "k_wide"))
         if tensor:
             peak, bound = peaks.get("bf16_tflops", 1800.0), "tensor"
             peak_note = "measured cuBLAS BF16 burst (MEASURED_PEAKS.json bf16_tflops)"
         else:
             peak, bound = fp32_peak, "alu"
             peak_note = f"FP32 FFMA: {props.multi_processor_count} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_max:.0f} MHz"
+        total_prof = sum(v[1] for v in prof.values())
         value = world * sps * args.steps / (ms_max * 1e-3)
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -322,26 +399,29 @@ def run_ours(args):
             "steps_per_s": 1e3 * args.steps / ms_max,
             "config": {"workload": "room50: 50 objects (hidden 32, 32-600 rays) + background (hidden 128, 1200 rays), "
                                    f"22 samples/ray, {args.precision.upper()}, all objects present",
-                       "precision": args.precision, "launch_shape": launch,
+                       "precision": args.precision, "graph": not args.no_graph, "launch_shape": launch,
                        "objects_per_gpu": K, "samples_per_step_per_gpu": sps,
                        "rays_per_step_per_gpu": sum(R), "l2": "flushed (512 MB write) between timed steps",
                        "parallelism": f"objects sharded, {world} independent scene(s), no collective"},
             "roofline": {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-                         "peak_note": peak_note,
-                         "flops_per_launch": flops, "avg_launch_ms": dom_ms / launches},
-            "kernels": {k: {"launches": n, "total_ms": round(t_, 4), "share": round(t_ / sum(v[1] for v in prof.values()), 4)}
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic_for(dom),
+                         "peak_note": peak_note, "flops_per_launch": flops, "avg_launch_ms": dom_ms / n_l,
+                         "timing": f"CUDA events around each launch, {args.prof_steps}-step kernel-by-kernel pass"},
+            "kernels": {k: {"launches": n, "total_ms": round(t_, 4), "share": round(t_ / total_prof, 4)}
                         for k, (n, t_) in prof.items()},
-            "gpu_launches": int(sum(n for n, _ in prof.values())),
+            "gpu_launches": int(round(launches_per_step * args.steps)),
             "e2e": {"value": world * sps * args.e2e_steps / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": int(sum(R) * 48), "d2h_bytes_per_step": int(K * 4),
                     "api": "vmap_train_step_host (pinned host rays in, host losses out, synchronous)"},
             "clocks": clk,
         }
+        if fp32:
+            out["fp32"] = fp32
+        if world == 1 and not args.no_ttd:
+            out["time_to_depth_l1"] = time_to_depth()
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(sc, args.cpu_steps)
         print(json.dumps(out), flush=True)
-    vm.close()
     if world > 1:
         dist.destroy_process_group()
 

@@ -93,6 +93,8 @@ struct vmap_ctx {
     long long part_base[NCLASS] = {0, 0, 0, 0};
     int2* items_d = nullptr;
     int* counts_d = nullptr;
+    int* sig_d = nullptr;           // inputs of the last batch build ([0] = -1: rebuild)
+    long long build_key = -1;       // launch shape the last build ran with
     float* given_d = nullptr;
     float* loss_d = nullptr;
     bool batch_ready = false;
@@ -381,13 +383,14 @@ vmap_status launch_build_sample(vmap_ctx* ctx, int given) {
     a.bray = ctx->bray_d;
     a.items = ctx->items_d;
     a.counts = ctx->counts_d;
+    a.sig = ctx->sig_d;
     int pi = prof_begin(ctx, PS_BUILD);
     k_build<<<1, BUILD_THREADS, 0, ctx->stream>>>(a);
     prof_end(ctx, pi);
     CHECK_LAUNCH("k_build");
-    const int blocks = (ctx->cfg.max_rays_total + 127) / 128;
+    const int blocks = (ctx->cfg.max_rays_total + SAMPLE_RAYS_PER_BLOCK - 1) / SAMPLE_RAYS_PER_BLOCK;
     pi = prof_begin(ctx, PS_SAMPLE);
-    k_sample<<<blocks, 128, 0, ctx->stream>>>(ctx->sp, ctx->objs_d, ctx->ob_d, ctx->bobj_d, ctx->bray_d,
+    k_sample<<<blocks, 32 * SAMPLE_RAYS_PER_BLOCK, 0, ctx->stream>>>(ctx->sp, ctx->objs_d, ctx->ob_d, ctx->bobj_d, ctx->bray_d,
                                              ctx->counts_d, given ? ctx->given_d : ctx->pool_d, given,
                                              ctx->steps_d, ctx->pick_d, ctx->t_d);
     prof_end(ctx, pi);
@@ -521,6 +524,13 @@ vmap_status sample_impl(vmap_ctx* ctx, const int* rays_per_object, const float* 
         if (tiles[c] > ctx->tile_cap) return fail(ctx, VMAP_ERR_CAPACITY, "too many tiles");
     if (uses_wide(ctx, 3) && tiles[3] > ctx->act_cap)
         if (vmap_status s = grow_act(ctx, tiles[3])) return s;
+    // the builder skips unchanged layouts; a new launch shape invalidates its record
+    long long key = 0;
+    for (int c = 0; c < NCLASS; ++c) key = key * 64 + ctx->rt[c] * 4 + ctx->gmult[c];
+    if (key != ctx->build_key) {
+        CU(cudaMemsetAsync(ctx->sig_d, 0xFF, sizeof(int), ctx->stream));
+        ctx->build_key = key;
+    }
     ctx->req_h.assign(rays_per_object, rays_per_object + K);
     if (K) CU(cudaMemcpyAsync(ctx->req_d, ctx->req_h.data(), sizeof(int) * K, cudaMemcpyHostToDevice, ctx->stream));
     ctx->batch_given = given != nullptr;
@@ -638,6 +648,7 @@ vmap_status vmap_init_objects(vmap_ctx** out, const vmap_config* cfg, void* cuda
     ALLOC(ctx->part_d, sizeof(float) * part);
     ALLOC(ctx->items_d, sizeof(int2) * (size_t)K * ((param_count(128) + REDUCE_CHUNK - 1) / REDUCE_CHUNK));
     ALLOC(ctx->counts_d, sizeof(int) * BC_N);
+    ALLOC(ctx->sig_d, sizeof(int) * (2 + (size_t)K));
     ALLOC(ctx->given_d, sizeof(float) * REC * (size_t)cfg->max_rays_total);
     ALLOC(ctx->loss_d, sizeof(float) * K);
     ALLOC(ctx->err_d, sizeof(int));
@@ -655,6 +666,7 @@ vmap_status vmap_init_objects(vmap_ctx** out, const vmap_config* cfg, void* cuda
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->req_d, 0, sizeof(int) * K, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->n_obj_d, 0, sizeof(int), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->counts_d, 0, sizeof(int) * BC_N, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->sig_d, 0xFF, sizeof(int) * (2 + (size_t)K), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->err_d, 0, sizeof(int), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->img_off_d, 0xFF, sizeof(long long) * K, ctx->stream);
     if (e == cudaSuccess && ctx->act_pp_d) e = cudaMemsetAsync(ctx->act_pp_d, 0, sizeof(unsigned char*), ctx->stream);
@@ -673,7 +685,7 @@ vmap_status vmap_destroy(vmap_ctx* ctx) {
                     ctx->params_d, ctx->wt_d,     ctx->m_d,      ctx->v_d,     ctx->pool_d,   ctx->pick_d,
                     ctx->t_d,      ctx->bobj_d,   ctx->bray_d,   ctx->tiles_d, ctx->flags_d,  ctx->part_d,
                     ctx->items_d,  ctx->counts_d, ctx->given_d,  ctx->loss_d,  ctx->err_d,  ctx->img_off_d,
-                    ctx->img_d,    ctx->act_d,    ctx->act_pp_d, ctx->tile_loss_d};
+                    ctx->img_d,    ctx->act_d,    ctx->act_pp_d, ctx->tile_loss_d, ctx->sig_d};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& p : ctx->pending) {

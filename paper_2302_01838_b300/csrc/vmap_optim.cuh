@@ -77,6 +77,7 @@ __global__ void __launch_bounds__(256) k_reduce(StepParams sp, const ObjDev* __r
                                                 float* __restrict__ loss_out,
                                                 float* __restrict__ dcenter_out,
                                                 __nv_bfloat16* img, const long long* __restrict__ img_off) {
+    __shared__ float sh_loss;
     const int n_items = counts[BC_ITEMS];
 #pragma unroll 1
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
@@ -86,21 +87,28 @@ __global__ void __launch_bounds__(256) k_reduce(StepParams sp, const ObjDev* __r
         const ObjBatch& bt = obs[k];
         const int H = ob.hidden;
         const long long P = param_count(H);
+        const long long stride = P + NEXTRA;
         const long long p0 = (long long)item.y * REDUCE_CHUNK;
-        const float L = object_loss(sp, ob, bt, part);
         const bool frozen = status[k] != 0;
         const float gl = grad_loss ? grad_loss[k] : 1.f;
-        if (item.y == 0 && threadIdx.x == 0) {
-            if (loss_out) loss_out[k] = frozen ? __int_as_float(0x7fc00000) : L;
-            if (dcenter_out) {
-                float d[3] = {0.f, 0.f, 0.f};
-                for (int t = 0; t < bt.n_runs; ++t) {
-                    const float* e = part + bt.part_off + (long long)t * (P + NEXTRA) + P;
-                    d[0] += e[3]; d[1] += e[4]; d[2] += e[5];
+        __syncthreads();   // sh_loss of the previous item has been read
+        if (threadIdx.x == 0) {
+            const float L = object_loss(sp, ob, bt, part);
+            sh_loss = L;
+            if (item.y == 0) {
+                if (loss_out) loss_out[k] = frozen ? __int_as_float(0x7fc00000) : L;
+                if (dcenter_out) {
+                    float d[3] = {0.f, 0.f, 0.f};
+                    for (int t = 0; t < bt.n_runs; ++t) {
+                        const float* e = part + bt.part_off + (long long)t * stride + P;
+                        d[0] += e[3]; d[1] += e[4]; d[2] += e[5];
+                    }
+                    for (int a = 0; a < 3; ++a) dcenter_out[3 * k + a] = gl * d[a];
                 }
-                for (int a = 0; a < 3; ++a) dcenter_out[3 * k + a] = gl * d[a];
             }
         }
+        __syncthreads();
+        const float L = sh_loss;
         if (mode == RED_LOSS) continue;
         if (mode == RED_ADAM && (frozen || !isfinite(L))) {
             if (!frozen && item.y == 0 && threadIdx.x == 0) status[k] = 1;
@@ -110,10 +118,20 @@ __global__ void __launch_bounds__(256) k_reduce(StepParams sp, const ObjDev* __r
         const float bc1 = 1.f - powf(sp.beta1, (float)t1);
         const float bc2 = 1.f - powf(sp.beta2, (float)t1);
         const long long end = min(P, p0 + REDUCE_CHUNK);
+        const int nr = bt.n_runs;
         for (long long p = p0 + threadIdx.x; p < end; p += blockDim.x) {
+            // slots summed in slot order; loads issued eight at a time
             float g = 0.f;
             const float* src = part + bt.part_off + p;
-            for (int t = 0; t < bt.n_runs; ++t) g += src[(long long)t * (P + NEXTRA)];
+            int t = 0;
+            for (; t + 8 <= nr; t += 8) {
+                float v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = src[(long long)(t + u) * stride];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) g += v[u];
+            }
+            for (; t < nr; ++t) g += src[(long long)t * stride];
             if (mode == RED_GRAD) {
                 grad_out[ob.param_off + p] = gl * g;
                 continue;
