@@ -78,6 +78,22 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* m, uint32_t parity, long lon
     return false;
 }
 
+// arrive once on mbar and raise its pending transaction count by `bytes`
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* m, uint32_t bytes) {
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}" ::"r"(smem_u32(m)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// bulk (non-tensor) async copy global -> shared of `bytes` (multiple of 16,
+// both addresses 16-byte aligned); completes `bytes` transactions on mbar
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+                 : "memory");
+}
+
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot, int ncols) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
                  "r"(ncols));

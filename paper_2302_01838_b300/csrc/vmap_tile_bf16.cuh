@@ -81,6 +81,45 @@ __device__ __forceinline__ void ld_bf16x8(const unsigned char* tile, int off, fl
 // accurate there; the result is rounded to BF16 anyway)
 __device__ __forceinline__ float red2pi(float p) { return fmaf(-6.28318530717958647692f, rintf(p * 0.15915494309189533577f), p); }
 
+// Encoding of one sample into row m of a [128][96] BF16 core-matrix tile.
+// Half 0 writes columns 0..47 (x~, sin(B x~)), half 1 columns 48..95
+// (cos(B x~), the ones column 93, zero padding); every feature index is a
+// compile-time constant, so B is read as immediate constant-bank operands.
+// gcopy (may be NULL) receives the same bytes at the same offsets.
+__device__ __forceinline__ float enc_proj(const StepParams& sp, int j, float x0, float x1, float x2) {
+    return red2pi(fmaf(sp.B[3 * j + 2], x2, fmaf(sp.B[3 * j + 1], x1, sp.B[3 * j] * x0)));
+}
+__device__ __forceinline__ void encode_row_half(const StepParams& sp, float x0, float x1, float x2, int m, int half,
+                                                unsigned char* tile, unsigned char* gcopy) {
+    if (half == 0) {
+#pragma unroll
+        for (int ch = 0; ch < 6; ++ch) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int c = ch * 8 + u;
+                v[u] = c == 0 ? x0 : c == 1 ? x1 : c == 2 ? x2 : __sinf(enc_proj(sp, c - 3, x0, x1, x2));
+            }
+            const int off = cm_off(m, ch * 8, DINP);
+            st_bf16x8(tile, off, v);
+            if (gcopy) *reinterpret_cast<uint4*>(gcopy + off) = *reinterpret_cast<const uint4*>(tile + off);
+        }
+    } else {
+#pragma unroll
+        for (int ch = 6; ch < 12; ++ch) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int c = ch * 8 + u;
+                v[u] = c < DIN ? __cosf(enc_proj(sp, c - 3 - NF, x0, x1, x2)) : (c == DIN ? 1.f : 0.f);
+            }
+            const int off = cm_off(m, ch * 8, DINP);
+            st_bf16x8(tile, off, v);
+            if (gcopy) *reinterpret_cast<uint4*>(gcopy + off) = *reinterpret_cast<const uint4*>(tile + off);
+        }
+    }
+}
+
 struct Bf16Args {
     TileArgs t;
     const __nv_bfloat16* img;   // tensor-core weight images (arena)
@@ -247,27 +286,10 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
             xt[2 * TM + m] = x2;
         }
         __syncthreads();
-        // ---- encoding -> G0 (BF16, 12 chunks of 8 features per sample) -----------
-        for (int f = tid; f < TM * (DINP / 8); f += blockDim.x) {
-            const int m = f % TM, ch = f / TM;
-            const float x0 = xt[m], x1 = xt[TM + m], x2 = xt[2 * TM + m];
-            float v[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int c = ch * 8 + u;
-                float val;
-                if (c < 3) {
-                    val = c == 0 ? x0 : c == 1 ? x1 : x2;
-                } else if (c < DIN) {
-                    const int j = c < 3 + NF ? c - 3 : c - 3 - NF;
-                    const float p = red2pi(fmaf(sp.B[3 * j + 2], x2, fmaf(sp.B[3 * j + 1], x1, sp.B[3 * j] * x0)));
-                    val = c < 3 + NF ? __sinf(p) : __cosf(p);
-                } else {
-                    val = c == DIN ? 1.f : 0.f;   // column 93: ones (bias gradient of layer 1)
-                }
-                v[u] = val;
-            }
-            st_bf16x8(G0, cm_off(m, ch * 8, DINP), v);
+        // ---- encoding -> G0 (BF16; two threads per sample) ----------------------
+        for (int f = tid; f < 2 * TM; f += blockDim.x) {
+            const int m = f % TM;
+            encode_row_half(sp, xt[m], xt[TM + m], xt[2 * TM + m], m, f / TM, G0, nullptr);
         }
         sync_for_mma();
 

@@ -13,8 +13,9 @@
 //              284 KB per tile, with the tile's loss sums.
 //   k_wide_dw  weight gradients dW_l = sum over samples of dZ_l^T h_{l-1} as
 //              split-K MMAs: CTA (range r, layer job j) streams job j's two
-//              operands of every tile in range r through a double-buffered
-//              stage and accumulates in TMEM; bias gradients are column sums
+//              operands of every tile in range r through a three-stage ring
+//              filled by bulk async copies (cp.async.bulk, mbarrier transaction
+//              counts) and accumulates in TMEM; bias gradients are column sums
 //              of the same BF16 operand tiles, in FP32, in a fixed order. At
 //              the end of each object run the CTA writes its layer's slice of
 //              the run slot, which the reduce kernel sums in slot order.
@@ -66,12 +67,14 @@ struct WideFbCfg {
 
 struct WideDwCfg {
     static constexpr int STAGE = 65536;                           // operand A at +0, operand B at +32 KB
-    static constexpr int NST = 2;
+    static constexpr int NST = 3;
     static constexpr int BSUM = NST * STAGE;                      // [16][128] f32 bias partials
-    static constexpr int MBAR = BSUM + 16 * 128 * 4;              // [NST]
-    static constexpr int TSLOT = MBAR + 8 * NST;
+    static constexpr int FULL = BSUM + 16 * 128 * 4;              // [NST] mbarriers: stage loaded
+    static constexpr int EMPTY = FULL + 8 * NST;                  // [NST] mbarriers: stage's MMAs done
+    static constexpr int TSLOT = EMPTY + 8 * NST;
     static constexpr int BYTES = TSLOT + 16;
     static constexpr int NCOLS = 128;
+    static_assert(BYTES <= 232448, "shared memory of one CTA");
 };
 
 struct WideArgs {
@@ -198,29 +201,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_wide_fb(StepParams sp, WideArgs
             xt[2 * TM + m] = x2;
         }
         __syncthreads();
-        // ---- encoding -> G0 (and the activation record) ----------------------
-        for (int f = tid; f < TM * (DINP / 8); f += blockDim.x) {
-            const int m = f % TM, ch = f / TM;
-            const float x0 = xt[m], x1 = xt[TM + m], x2 = xt[2 * TM + m];
-            float v[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int c = ch * 8 + u;
-                float val;
-                if (c < 3) {
-                    val = c == 0 ? x0 : c == 1 ? x1 : x2;
-                } else if (c < DIN) {
-                    const int j = c < 3 + NF ? c - 3 : c - 3 - NF;
-                    const float p = red2pi(fmaf(sp.B[3 * j + 2], x2, fmaf(sp.B[3 * j + 1], x1, sp.B[3 * j] * x0)));
-                    val = c < 3 + NF ? __sinf(p) : __cosf(p);
-                } else {
-                    val = c == DIN ? 1.f : 0.f;
-                }
-                v[u] = val;
-            }
-            const int off = cm_off(m, ch * 8, DINP);
-            st_bf16x8(G0, off, v);
-            if (GRAD) *reinterpret_cast<uint4*>(at + WideAct::G0 + off) = *reinterpret_cast<const uint4*>(G0 + off);
+        // ---- encoding -> G0 (and the activation record); two threads per sample --
+        for (int f = tid; f < 2 * TM; f += blockDim.x) {
+            const int m = f % TM;
+            encode_row_half(sp, xt[m], xt[TM + m], xt[2 * TM + m], m, f / TM, G0, GRAD ? at + WideAct::G0 : nullptr);
         }
         sync_for_mma();
 
@@ -375,7 +359,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_wide_dw(WideArgs wa) {
     const TileArgs& ta = wa.t;
     extern __shared__ __align__(1024) unsigned char sm[];
     float* bsum = reinterpret_cast<float*>(sm + C::BSUM);
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + C::MBAR);
+    uint64_t* full = reinterpret_cast<uint64_t*>(sm + C::FULL);
+    uint64_t* empty = reinterpret_cast<uint64_t*>(sm + C::EMPTY);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + C::TSLOT);
     const int tid = threadIdx.x, warp = tid >> 5;
     const int q = warp & 3, hf = warp >> 2;
@@ -384,116 +369,141 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_wide_dw(WideArgs wa) {
     const int rg = blockIdx.x / WJOBS, j = blockIdx.x % WJOBS;
     if (wa.loss_only && j != 0) return;
     const WideJob jb = wide_job(j);
-    const unsigned char* act = wa.loss_only ? nullptr : *wa.act;
     constexpr long long PC = param_count(WH);
-
-    if (!wa.loss_only) {
-        if (tid == 0)
-            for (int s = 0; s < C::NST; ++s) mbar_init(mbar + s, 1);
-        if (warp == 0) tmem_alloc(tslot, C::NCOLS);
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = wa.loss_only ? 0u : *tslot;
-    uint32_t phase[C::NST] = {0, 0};
-    bool pend[C::NST] = {false, false};
-    bool abort = false;
-    auto wait_stage = [&](int s) {
-        if (!pend[s]) return;
-        const bool ok = mbar_wait(mbar + s, phase[s], MMA_WAIT_LIMIT);
-        phase[s] ^= 1;
-        pend[s] = false;
-        if (__syncthreads_or(!ok)) {
-            abort = true;
-            if (tid == 0) atomicExch(wa.err, 1);
-        }
-        tc_fence_after();
-    };
-
-    // bias partial sums: thread = (8-column chunk, 8-row group) of the bias operand
-    const int bchunk = tid & 15, brg = tid >> 4;
-    const int b_cc = j < 4 ? jb.a_cc : jb.b_cc;
-    const int b_src = j < 4 ? 0 : 32768;   // operand holding dZ (A) or dY (B) in the stage
-    float bs[8];
-    float lacc[3] = {0.f, 0.f, 0.f};
-    int g = 0;
-
     const long long n_tiles = *ta.n_tiles;
     const long long t0 = (long long)rg * n_tiles / ranges;
     const long long t1 = (long long)(rg + 1) * n_tiles / ranges;
+    const int n = (int)(t1 - t0);
+
+    if (wa.loss_only) {
+        // fold the tile losses of every run into its slot, in tile order
+        if (tid == 0) {
+            float l0 = 0.f, l1 = 0.f, l2 = 0.f;
+            for (long long tl = t0; tl < t1; ++tl) {
+                const int k = ta.tiles[tl].obj;
+                if (tl == t0 || ta.tiles[tl - 1].obj != k) l0 = l1 = l2 = 0.f;
+                const float4 l4 = *reinterpret_cast<const float4*>(wa.tile_loss + 4 * tl);
+                l0 += l4.x; l1 += l4.y; l2 += l4.z;
+                if (tl + 1 == t1 || ta.tiles[tl + 1].obj != k) {
+                    float* gp = ta.part + ta.tiles[tl].part;
+                    gp[PC + 0] = l0; gp[PC + 1] = l1; gp[PC + 2] = l2;
+                    gp[PC + 3] = 0.f; gp[PC + 4] = 0.f; gp[PC + 5] = 0.f;
+                }
+            }
+        }
+        return;
+    }
+
+    const unsigned char* act = *wa.act;
+    if (tid == 0) {
+        for (int s = 0; s < C::NST; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, 1);
+        }
+    }
+    if (warp == 0) tmem_alloc(tslot, C::NCOLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    bool abort = false;
+    // thread 0 fills stage i % NST with tile t0 + i
+    auto issue_load = [&](int i) {
+        unsigned char* st = sm + (i % C::NST) * C::STAGE;
+        const unsigned char* src = act + (t0 + i) * WideAct::BYTES;
+        uint64_t* fb = full + i % C::NST;
+        mbar_expect_tx(fb, (uint32_t)(jb.a_bytes + jb.b_bytes));
+        bulk_load(st, src + jb.a_off, (uint32_t)jb.a_bytes, fb);
+        bulk_load(st + 32768, src + jb.b_off, (uint32_t)jb.b_bytes, fb);
+    };
+    int issued = 0;   // tiles whose loads were issued (thread 0's count; uniform by construction)
+    if (tid == 0)
+        for (; issued < min(C::NST, n); ++issued) issue_load(issued);
+    issued = min(C::NST, n);
+    int consumed = 0;   // tiles whose stage was seen loaded
+
+    // bias partial sums: thread = (column chunk c8, row r8 within a core matrix, strip parity sp2);
+    // a warp reads 512 contiguous bytes of the core-matrix tile (no bank conflicts)
+    const int c8 = (tid >> 3) & 15, r8 = tid & 7, sp2 = tid >> 7;
+    const int b_cc = j < 4 ? jb.a_cc : jb.b_cc;
+    const int b_src = j < 4 ? 0 : 32768;   // operand holding dZ (A) or dY (B) in the stage
+    const bool b_active = c8 * 8 < b_cc;
+    float bs[8];
+    float lacc[3] = {0.f, 0.f, 0.f};
+
 #pragma unroll 1
-    for (long long tl = t0; tl < t1 && !abort; ++tl) {
+    for (int i = 0; i < n; ++i) {
+        const long long tl = t0 + i;
+        const int s = i % C::NST;
+        const uint32_t par = (uint32_t)((i / C::NST) & 1);
         const int k = ta.tiles[tl].obj;
-        const bool first = tl == t0 || ta.tiles[tl - 1].obj != k;
-        const bool last = tl + 1 == t1 || ta.tiles[tl + 1].obj != k;
+        const bool first = i == 0 || ta.tiles[tl - 1].obj != k;
+        const bool last = i + 1 == n || ta.tiles[tl + 1].obj != k;
         if (first) {
 #pragma unroll
-            for (int i = 0; i < 8; ++i) bs[i] = 0.f;
+            for (int u = 0; u < 8; ++u) bs[u] = 0.f;
             lacc[0] = lacc[1] = lacc[2] = 0.f;
         }
         if (j == 0 && tid == 0) {
             const float4 l4 = *reinterpret_cast<const float4*>(wa.tile_loss + 4 * tl);
             lacc[0] += l4.x; lacc[1] += l4.y; lacc[2] += l4.z;
         }
-        float* gp = ta.part + ta.tiles[tl].part;
-        if (!wa.loss_only) {
-            const int s = g & 1;
-            wait_stage(s);   // the MMAs that last read this stage are done
-            if (abort) break;
-            unsigned char* st = sm + s * C::STAGE;
-            const unsigned char* src = act + tl * WideAct::BYTES;
-            {
-                constexpr int NV = 32768 / 16 / NTHREADS;   // 8 vectors per thread per operand, at most
-                uint4 va[NV], vb[NV];
-                const int na = jb.a_bytes / 16, nb = jb.b_bytes / 16;
-#pragma unroll
-                for (int i = 0; i < NV; ++i) {
-                    const int ia = tid + i * NTHREADS, ib = tid + i * NTHREADS;
-                    if (ia < na) va[i] = *reinterpret_cast<const uint4*>(src + jb.a_off + 16 * ia);
-                    if (ib < nb) vb[i] = *reinterpret_cast<const uint4*>(src + jb.b_off + 16 * ib);
-                }
-#pragma unroll
-                for (int i = 0; i < NV; ++i) {
-                    const int ia = tid + i * NTHREADS, ib = tid + i * NTHREADS;
-                    if (ia < na) *reinterpret_cast<uint4*>(st + 16 * ia) = va[i];
-                    if (ib < nb) *reinterpret_cast<uint4*>(st + 32768 + 16 * ib) = vb[i];
-                }
-            }
-            fence_async_smem();
-            tc_fence_before();
-            __syncthreads();
+        // stage s holds tile i
+        const bool ok = mbar_wait(full + s, par, MMA_WAIT_LIMIT);
+        if (__syncthreads_or(!ok)) {
+            abort = true;
+            if (tid == 0) atomicExch(wa.err, 1);
+            break;
+        }
+        consumed = i + 1;
+        unsigned char* st = sm + s * C::STAGE;
+        if (tid == 0) {
             tc_fence_after();
+#pragma unroll
+            for (int kc = 0; kc < TM / 16; ++kc)
+                mma_bf16(tmem, desc_mnmajor(st, jb.a_cc, 16 * kc), desc_mnmajor(st + 32768, jb.b_cc, 16 * kc),
+                         idesc_bf16(TM, jb.n, 1, 1), !(first && kc == 0));
+            mma_commit(empty + s);
+        }
+        if (b_active) {
+#pragma unroll
+            for (int strip = sp2; strip < TM / 8; strip += 2) {
+                float v[8];
+                ld_bf16x8(st + b_src, cm_off(strip * 8 + r8, c8 * 8, b_cc), v);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) bs[u] += v[u];
+            }
+        }
+        __syncthreads();   // every thread is done reading stage s
+        // refill stage s with tile i + NST once tile i's MMAs have read it
+        if (i + C::NST < n) {
+            bool okr = true;
             if (tid == 0) {
-#pragma unroll
-                for (int kc = 0; kc < TM / 16; ++kc)
-                    mma_bf16(tmem, desc_mnmajor(st, jb.a_cc, 16 * kc), desc_mnmajor(st + 32768, jb.b_cc, 16 * kc),
-                             idesc_bf16(TM, jb.n, 1, 1), !(first && kc == 0));
-                mma_commit(mbar + s);
+                okr = mbar_wait(empty + s, par, MMA_WAIT_LIMIT);
+                if (okr) issue_load(i + C::NST);
             }
-            pend[s] = true;
-            ++g;
-            // bias partials from the BF16 operand (dZ, or dY for job 4)
-            if (bchunk * 8 < b_cc) {
-#pragma unroll
-                for (int r = 0; r < 8; ++r) {
-                    float v[8];
-                    ld_bf16x8(st + b_src, cm_off(brg * 8 + r, bchunk * 8, b_cc), v);
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) bs[i] += v[i];
-                }
+            if (__syncthreads_or(!okr)) {
+                abort = true;
+                if (tid == 0) atomicExch(wa.err, 1);
+                break;
             }
+            ++issued;
         }
         if (!last) continue;
         // ---- run end: write this job's slice of the run slot --------------------
+        float* gp = ta.part + ta.tiles[tl].part;
         if (j == 0 && tid == 0) {
             gp[PC + 0] = lacc[0]; gp[PC + 1] = lacc[1]; gp[PC + 2] = lacc[2];
             gp[PC + 3] = 0.f; gp[PC + 4] = 0.f; gp[PC + 5] = 0.f;
         }
-        if (wa.loss_only) continue;
-        wait_stage(g & 1);          // older stage first, then the newest
-        wait_stage((g + 1) & 1);
-        if (abort) break;
+        // tile i's MMAs were the run's last (commit order = issue order)
+        const bool okf = mbar_wait(empty + s, par, MMA_WAIT_LIMIT);
+        if (__syncthreads_or(!okf)) {
+            abort = true;
+            if (tid == 0) atomicExch(wa.err, 1);
+            break;
+        }
+        tc_fence_after();
         if (j < 4) {
             const int fan = j == 0 ? DIN : WH;
             float* w = gp + w_off(WH, j) + (long long)row * fan;
@@ -504,9 +514,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_wide_dw(WideArgs wa) {
                 tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + hf * half + c0, v);
                 tmem_ld_wait();
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int in = hf * half + c0 + i;
-                    if (in < fan) w[in] = v[i];
+                for (int u = 0; u < 16; ++u) {
+                    const int in = hf * half + c0 + u;
+                    if (in < fan) w[in] = v[u];
                 }
             }
         } else {
@@ -518,26 +528,30 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_wide_dw(WideArgs wa) {
                 for (int o = 0; o < NOUT; ++o) gp[w_off(WH, 4) + o * WH + row] = v[o];
             }
         }
-        if (bchunk * 8 < b_cc) {
+        if (b_active) {
 #pragma unroll
-            for (int i = 0; i < 8; ++i) bsum[brg * 128 + bchunk * 8 + i] = bs[i];
+            for (int u = 0; u < 8; ++u) bsum[(sp2 * 8 + r8) * 128 + c8 * 8 + u] = bs[u];
         }
         __syncthreads();
         const int nb = j < 4 ? WH : NOUT;
         if (tid < nb) {
-            float s = 0.f;
-            for (int r = 0; r < 16; ++r) s += bsum[r * 128 + tid];
-            gp[b_off(WH, j) + tid] = s;
+            float sum = 0.f;
+            for (int r = 0; r < 16; ++r) sum += bsum[r * 128 + tid];
+            gp[b_off(WH, j) + tid] = sum;
         }
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
     }
-    if (!wa.loss_only) {
-        tc_fence_before();
-        __syncthreads();
-        if (warp == 0) tmem_dealloc(tmem, C::NCOLS);
+    if (abort) {
+        // let the bulk copies still in flight land before the CTA exits (bounded)
+        if (tid == 0)
+            for (int u = consumed; u < issued; ++u)
+                mbar_wait(full + u % C::NST, (uint32_t)((u / C::NST) & 1), MMA_WAIT_LIMIT);
     }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, C::NCOLS);
 }
 
 }  // namespace vmapk
