@@ -94,6 +94,7 @@ struct vmap_ctx {
     int2* items_d = nullptr;
     int* counts_d = nullptr;
     int* sig_d = nullptr;           // inputs of the last batch build ([0] = -1: rebuild)
+    int* done_d = nullptr;          // blocks of the reduce that have finished (reset by the last)
     long long build_key = -1;       // launch shape the last build ran with
     float* given_d = nullptr;
     float* loss_d = nullptr;
@@ -241,8 +242,8 @@ int class_mask(vmap_ctx* ctx) {
 bool uses_tc(vmap_ctx* ctx, int c) { return ctx->bf16 && c < 3; }
 bool uses_wide(vmap_ctx* ctx, int c) { return ctx->bf16 && c == 3; }
 
-// tile ranges of the width-128 weight-gradient kernel (WJOBS CTAs each)
-int wide_ranges(vmap_ctx* ctx) { return (ctx->n_sm + WJOBS - 1) / WJOBS * ctx->gmult[3]; }
+// tile ranges of the width-128 weight-gradient kernel (WJOBS CTAs each; one wave of CTAs at gmult 1)
+int wide_ranges(vmap_ctx* ctx) { return std::max(1, ctx->n_sm / WJOBS) * ctx->gmult[3]; }
 
 // CTA ranges that own a run slot (the builder's partition of the class's tiles)
 int grid_of(vmap_ctx* ctx, int c) {
@@ -316,7 +317,7 @@ cudaError_t launch_wide_fb(vmap_ctx* ctx) {
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    k_wide_fb<MODE><<<ctx->n_sm * ctx->gmult[3], NTHREADS, WideFbCfg::BYTES, ctx->stream>>>(ctx->sp, wide_args(ctx));
+    k_wide_fb<MODE><<<ctx->n_sm * ctx->gmult[3], WIDE_THREADS, WideFbCfg::BYTES, ctx->stream>>>(ctx->sp, wide_args(ctx));
     return cudaGetLastError();
 }
 
@@ -427,11 +428,12 @@ vmap_status launch_tiles(vmap_ctx* ctx, int mask) {
 vmap_status launch_reduce(vmap_ctx* ctx, int mode, const float* grad_loss, float* grad_out, float* loss_out,
                           float* dcenter_out) {
     const int pi = prof_begin(ctx, PS_REDUCE);
-    k_reduce<<<ctx->n_sm * 4, 256, 0, ctx->stream>>>(ctx->sp, ctx->objs_d, ctx->ob_d, ctx->bobj_d, ctx->items_d,
+    k_reduce<<<ctx->n_sm * 16, REDUCE_CHUNK, 0, ctx->stream>>>(ctx->sp, ctx->objs_d, ctx->ob_d, ctx->bobj_d, ctx->items_d,
                                                      ctx->counts_d, ctx->part_d, ctx->params_d, ctx->wt_d,
                                                      ctx->m_d, ctx->v_d, ctx->steps_d, ctx->status_d, mode,
                                                      grad_loss, grad_out, loss_out, dcenter_out,
-                                                     ctx->bf16 ? ctx->img_d : nullptr, ctx->img_off_d);
+                                                     ctx->bf16 ? ctx->img_d : nullptr, ctx->img_off_d,
+                                                     ctx->done_d);
     prof_end(ctx, pi);
     CHECK_LAUNCH("k_reduce");
     return VMAP_OK;
@@ -440,12 +442,8 @@ vmap_status launch_reduce(vmap_ctx* ctx, int mode, const float* grad_loss, float
 vmap_status launch_train(vmap_ctx* ctx, int mask) {
     CU(cudaMemsetAsync(ctx->loss_d, 0xFF, sizeof(float) * ctx->cfg.max_objects, ctx->stream));
     if (vmap_status s = launch_tiles<MODE_TRAIN>(ctx, mask)) return s;
-    if (vmap_status s = launch_reduce(ctx, RED_ADAM, nullptr, nullptr, ctx->loss_d, nullptr)) return s;
-    const int pi = prof_begin(ctx, PS_FINISH);
-    k_finish<<<4, 256, 0, ctx->stream>>>(ctx->bobj_d, ctx->counts_d, ctx->steps_d, ctx->status_d);
-    prof_end(ctx, pi);
-    CHECK_LAUNCH("k_finish");
-    return VMAP_OK;
+    // the reduce's last block advances the step counts
+    return launch_reduce(ctx, RED_ADAM, nullptr, nullptr, ctx->loss_d, nullptr);
 }
 
 // capture fn() into an executable graph on the context stream
@@ -649,6 +647,7 @@ vmap_status vmap_init_objects(vmap_ctx** out, const vmap_config* cfg, void* cuda
     ALLOC(ctx->items_d, sizeof(int2) * (size_t)K * ((param_count(128) + REDUCE_CHUNK - 1) / REDUCE_CHUNK));
     ALLOC(ctx->counts_d, sizeof(int) * BC_N);
     ALLOC(ctx->sig_d, sizeof(int) * (2 + (size_t)K));
+    ALLOC(ctx->done_d, sizeof(int));
     ALLOC(ctx->given_d, sizeof(float) * REC * (size_t)cfg->max_rays_total);
     ALLOC(ctx->loss_d, sizeof(float) * K);
     ALLOC(ctx->err_d, sizeof(int));
@@ -667,6 +666,7 @@ vmap_status vmap_init_objects(vmap_ctx** out, const vmap_config* cfg, void* cuda
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->n_obj_d, 0, sizeof(int), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->counts_d, 0, sizeof(int) * BC_N, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->sig_d, 0xFF, sizeof(int) * (2 + (size_t)K), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->done_d, 0, sizeof(int), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->err_d, 0, sizeof(int), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->img_off_d, 0xFF, sizeof(long long) * K, ctx->stream);
     if (e == cudaSuccess && ctx->act_pp_d) e = cudaMemsetAsync(ctx->act_pp_d, 0, sizeof(unsigned char*), ctx->stream);
@@ -685,7 +685,7 @@ vmap_status vmap_destroy(vmap_ctx* ctx) {
                     ctx->params_d, ctx->wt_d,     ctx->m_d,      ctx->v_d,     ctx->pool_d,   ctx->pick_d,
                     ctx->t_d,      ctx->bobj_d,   ctx->bray_d,   ctx->tiles_d, ctx->flags_d,  ctx->part_d,
                     ctx->items_d,  ctx->counts_d, ctx->given_d,  ctx->loss_d,  ctx->err_d,  ctx->img_off_d,
-                    ctx->img_d,    ctx->act_d,    ctx->act_pp_d, ctx->tile_loss_d, ctx->sig_d};
+                    ctx->img_d,    ctx->act_d,    ctx->act_pp_d, ctx->tile_loss_d, ctx->sig_d,  ctx->done_d};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& p : ctx->pending) {

@@ -51,33 +51,48 @@ __device__ __forceinline__ long long wt_index(int H, long long p) {
 __device__ __forceinline__ float object_loss(const StepParams& sp, const ObjDev& ob, const ObjBatch& bt,
                                              const float* __restrict__ part) {
     const long long P = param_count(ob.hidden);
+    const long long stride = P + NEXTRA;
+    const float* e = part + bt.part_off + P;
     float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-    for (int t = 0; t < bt.n_runs; ++t) {
-        const float* e = part + bt.part_off + (long long)t * (P + NEXTRA) + P;
-        s0 += e[0]; s1 += e[1]; s2 += e[2];
+    int t = 0;
+    for (; t + 4 <= bt.n_runs; t += 4) {   // loads four slots at a time, sums in slot order
+        float a[4][3];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) a[u][c] = e[(long long)(t + u) * stride + c];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) { s0 += a[u][0]; s1 += a[u][1]; s2 += a[u][2]; }
+    }
+    for (; t < bt.n_runs; ++t) {
+        s0 += e[(long long)t * stride]; s1 += e[(long long)t * stride + 1]; s2 += e[(long long)t * stride + 2];
     }
     const float R = (float)bt.R;
     return s0 / R + sp.lam_c * (s1 / (3.f * R)) + sp.lam_o * (s2 / R);
 }
 
 // Fixed grid; each block takes reduce work items (batch object, chunk of
-// REDUCE_CHUNK parameters) from the builder's list. Sums the object's run
-// slots in slot order, then (RED_ADAM) applies Adam with the object's step
-// count + 1, or (RED_GRAD) writes grad_loss[k] * g.
-__global__ void __launch_bounds__(256) k_reduce(StepParams sp, const ObjDev* __restrict__ objs,
-                                                const ObjBatch* __restrict__ obs,
-                                                const int* __restrict__ bobj,
-                                                const int2* __restrict__ items,
-                                                const int* __restrict__ counts,
-                                                const float* __restrict__ part, float* params,
-                                                float* wt, float* mom, float* vel,
-                                                const int* __restrict__ steps, int* status,
-                                                int mode, const float* __restrict__ grad_loss,
-                                                float* __restrict__ grad_out,
-                                                float* __restrict__ loss_out,
-                                                float* __restrict__ dcenter_out,
-                                                __nv_bfloat16* img, const long long* __restrict__ img_off) {
+// REDUCE_CHUNK parameters, one per thread) from the builder's list. Sums the
+// object's run slots in slot order, then (RED_ADAM) applies Adam with the
+// object's step count + 1, or (RED_GRAD) writes grad_loss[k] * g. With
+// RED_ADAM and a `done` counter, the last block to finish advances the step
+// count of every object that was trained and resets the counter.
+__global__ void __launch_bounds__(REDUCE_CHUNK) k_reduce(StepParams sp, const ObjDev* __restrict__ objs,
+                                                         const ObjBatch* __restrict__ obs,
+                                                         const int* __restrict__ bobj,
+                                                         const int2* __restrict__ items,
+                                                         const int* __restrict__ counts,
+                                                         const float* __restrict__ part, float* params,
+                                                         float* wt, float* mom, float* vel,
+                                                         int* steps, int* status,
+                                                         int mode, const float* __restrict__ grad_loss,
+                                                         float* __restrict__ grad_out,
+                                                         float* __restrict__ loss_out,
+                                                         float* __restrict__ dcenter_out,
+                                                         __nv_bfloat16* img, const long long* __restrict__ img_off,
+                                                         int* done) {
     __shared__ float sh_loss;
+    __shared__ int sh_last;
     const int n_items = counts[BC_ITEMS];
 #pragma unroll 1
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
@@ -88,9 +103,25 @@ __global__ void __launch_bounds__(256) k_reduce(StepParams sp, const ObjDev* __r
         const int H = ob.hidden;
         const long long P = param_count(H);
         const long long stride = P + NEXTRA;
-        const long long p0 = (long long)item.y * REDUCE_CHUNK;
         const bool frozen = status[k] != 0;
         const float gl = grad_loss ? grad_loss[k] : 1.f;
+        const long long p = (long long)item.y * REDUCE_CHUNK + threadIdx.x;
+        // this thread's gradient: slots summed in slot order, loads issued eight
+        // at a time (independent of the loss, so it overlaps thread 0's loss sum)
+        float g = 0.f;
+        if (mode != RED_LOSS && p < P) {
+            const int nr = bt.n_runs;
+            const float* src = part + bt.part_off + p;
+            int t = 0;
+            for (; t + 8 <= nr; t += 8) {
+                float v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = src[(long long)(t + u) * stride];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) g += v[u];
+            }
+            for (; t < nr; ++t) g += src[(long long)t * stride];
+        }
         __syncthreads();   // sh_loss of the previous item has been read
         if (threadIdx.x == 0) {
             const float L = object_loss(sp, ob, bt, part);
@@ -114,57 +145,49 @@ __global__ void __launch_bounds__(256) k_reduce(StepParams sp, const ObjDev* __r
             if (!frozen && item.y == 0 && threadIdx.x == 0) status[k] = 1;
             continue;
         }
+        if (p >= P) continue;
+        if (mode == RED_GRAD) {
+            grad_out[ob.param_off + p] = gl * g;
+            continue;
+        }
+        if (!isfinite(g)) {            // leave the element, flag the object
+            atomicOr(status + k, 2);
+            continue;
+        }
         const int t1 = steps[k] + 1;
         const float bc1 = 1.f - powf(sp.beta1, (float)t1);
         const float bc2 = 1.f - powf(sp.beta2, (float)t1);
-        const long long end = min(P, p0 + REDUCE_CHUNK);
-        const int nr = bt.n_runs;
-        for (long long p = p0 + threadIdx.x; p < end; p += blockDim.x) {
-            // slots summed in slot order; loads issued eight at a time
-            float g = 0.f;
-            const float* src = part + bt.part_off + p;
-            int t = 0;
-            for (; t + 8 <= nr; t += 8) {
-                float v[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) v[u] = src[(long long)(t + u) * stride];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) g += v[u];
-            }
-            for (; t < nr; ++t) g += src[(long long)t * stride];
-            if (mode == RED_GRAD) {
-                grad_out[ob.param_off + p] = gl * g;
-                continue;
-            }
-            if (!isfinite(g)) {            // leave the element, flag the object
-                atomicOr(status + k, 2);
-                continue;
-            }
-            const long long q = ob.param_off + p;
-            const float m = sp.beta1 * mom[q] + (1.f - sp.beta1) * g;
-            const float v = sp.beta2 * vel[q] + (1.f - sp.beta2) * g * g;
-            mom[q] = m;
-            vel[q] = v;
-            const float th = params[q] - sp.lr * (m / bc1) / (sqrtf(v / bc2) + sp.eps);
-            params[q] = th;
-            const long long w = wt_index(H, p);
-            if (w >= 0) wt[ob.wt_off + w] = th;
-            if (img && img_off[k] >= 0) {          // BF16 tensor-core operand image
-                const long long wi = img_index(H, p);
-                if (wi >= 0) img[img_off[k] + wi] = __float2bfloat16(th);
-            }
+        const long long q = ob.param_off + p;
+        const float m = sp.beta1 * mom[q] + (1.f - sp.beta1) * g;
+        const float v = sp.beta2 * vel[q] + (1.f - sp.beta2) * g * g;
+        mom[q] = m;
+        vel[q] = v;
+        const float th = params[q] - sp.lr * (m / bc1) / (sqrtf(v / bc2) + sp.eps);
+        params[q] = th;
+        const long long w = wt_index(H, p);
+        if (w >= 0) wt[ob.wt_off + w] = th;
+        if (img && img_off[k] >= 0) {          // BF16 tensor-core operand image
+            const long long wi = img_index(H, p);
+            if (wi >= 0) img[img_off[k] + wi] = __float2bfloat16(th);
         }
     }
-}
-
-// after the update: advance the step count of every object that was trained
-__global__ void k_finish(const int* __restrict__ bobj, const int* __restrict__ counts, int* steps,
-                         const int* status) {
-    const int nb = counts[BC_NB];
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nb; j += gridDim.x * blockDim.x) {
-        const int k = bobj[j];
-        if (status[k] == 0) steps[k] += 1;
+    if (mode != RED_ADAM || !done) return;
+    // the last block to finish (every block has read the step counts it needs)
+    // advances the step count of each trained, unfrozen object
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        sh_last = atomicAdd(done, 1) == (int)gridDim.x - 1;
     }
+    __syncthreads();
+    if (!sh_last) return;
+    __threadfence();
+    const int nb = counts[BC_NB];
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+        const int k = bobj[j];
+        if (atomicAdd(status + k, 0) == 0) steps[k] += 1;
+    }
+    if (threadIdx.x == 0) *done = 0;
 }
 
 // seeded default init: parameter p draws word p % 4 of Philox block p / 4 with

@@ -28,13 +28,6 @@ __device__ __forceinline__ int upper_index(const int* off, int n, int i) {
 // ascending order is each value's rank (ties broken by slot).
 constexpr int SAMPLE_RAYS_PER_BLOCK = 8;
 
-__device__ __forceinline__ uint32_t ray_word(uint32_t ray, uint32_t step, uint32_t stream, uint32_t k0, uint32_t k1,
-                                             int w) {
-    const uint4 b = philox4x32_10(make_uint4(ray, (uint32_t)(w >> 2), step, stream), k0, k1);
-    const int l = w & 3;
-    return l == 0 ? b.x : l == 1 ? b.y : l == 2 ? b.z : b.w;
-}
-
 __global__ void __launch_bounds__(32 * SAMPLE_RAYS_PER_BLOCK) k_sample(
     StepParams sp, const ObjDev* __restrict__ objs, const ObjBatch* __restrict__ obs, const int* __restrict__ bobj,
     const int* __restrict__ bray_off, const int* __restrict__ counts, const float* __restrict__ src, int given,
@@ -49,10 +42,24 @@ __global__ void __launch_bounds__(32 * SAMPLE_RAYS_PER_BLOCK) k_sample(
     const ObjDev& ob = objs[k];
     const ObjBatch& bt = obs[k];
     const uint32_t r = (uint32_t)(i - bt.ray_off), step = (uint32_t)steps[k], stream = ob.stream;
+    const int Ns = ob.n_surface, Nc = ob.n_strat, S = ob.S;
 
+    // lane b computes Philox block b of the ray; words travel by shuffles
+    const int nblk = (1 + Nc + 2 * ((Ns + 1) / 2) + 3) / 4;
+    uint4 blk = make_uint4(0u, 0u, 0u, 0u);
+    if (lane < nblk) blk = philox4x32_10(make_uint4(r, (uint32_t)lane, step, stream), sp.key0, sp.key1);
+    auto word = [&](int w) {   // warp-collective: every lane asks for its own word w
+        const int src = w >> 2, c = w & 3;
+        const uint32_t x = __shfl_sync(0xffffffffu, blk.x, src), y = __shfl_sync(0xffffffffu, blk.y, src);
+        const uint32_t z = __shfl_sync(0xffffffffu, blk.z, src), ww = __shfl_sync(0xffffffffu, blk.w, src);
+        return c == 0 ? x : c == 1 ? y : c == 2 ? z : ww;
+    };
     // word 0 picks the ray; with caller-given rays it is drawn and dropped so
     // the depth draws keep their word positions
-    const uint32_t w0 = ray_word(r, step, stream, sp.key0, sp.key1, 0);
+    const uint32_t w0 = word(0);
+    const int p2 = lane >> 1;
+    const uint32_t wa = word(lane < Ns ? 1 + Nc + 2 * p2 : (lane < S ? 1 + (lane - Ns) : 0));
+    const uint32_t wb = word(lane < Ns ? 2 + Nc + 2 * p2 : 0);
     const long long pick = given ? (long long)r
                                  : (long long)(((unsigned long long)w0 * (unsigned long long)ob.pool_n) >> 32);
     if (lane == 0) pick_out[i] = (int)pick;
@@ -61,24 +68,21 @@ __global__ void __launch_bounds__(32 * SAMPLE_RAYS_PER_BLOCK) k_sample(
     const float lo = sp.t_near;
     const float span = ts + sp.depth_pad - lo;
 
-    const int Ns = ob.n_surface, Nc = ob.n_strat, S = ob.S;
     float t = INFINITY;
     if (lane < Ns) {
-        const int p = lane >> 1;
-        const float u1 = word_to_unit(ray_word(r, step, stream, sp.key0, sp.key1, 1 + Nc + 2 * p));
-        const float u2 = word_to_unit(ray_word(r, step, stream, sp.key0, sp.key1, 2 + Nc + 2 * p));
+        const float u1 = word_to_unit(wa);
+        const float u2 = word_to_unit(wb);
         const float rho = sqrtf(-2.0f * logf(u1));
         float sn, cs;
         sincospif(2.0f * u2, &sn, &cs);
         t = fmaxf(ts + sp.d_sigma * (rho * ((lane & 1) ? sn : cs)), lo);
     } else if (lane < S) {
         const int q = lane - Ns;
-        const float u = word_to_unit(ray_word(r, step, stream, sp.key0, sp.key1, 1 + q));
+        const float u = word_to_unit(wa);
         t = lo + ((float)q + u) / (float)Nc * span;
     }
     int rank = 0;
-#pragma unroll
-    for (int b = 0; b < SMAX; ++b) {
+    for (int b = 0; b < S; ++b) {
         const float o = __shfl_sync(0xffffffffu, t, b);
         rank += (o < t || (o == t && b < lane)) ? 1 : 0;
     }

@@ -128,4 +128,25 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
     for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// NC (8, 16 or 32) consecutive columns of this warp's 32 lanes, one wait
+template <int NC>
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, float (&v)[NC]) {
+    static_assert(NC == 8 || NC == 16 || NC == 32, "columns per thread");
+    if constexpr (NC == 8) {
+        tmem_ld8(taddr, v);
+    } else if constexpr (NC == 16) {
+        tmem_ld16(taddr, v);
+    } else {
+        float a[16], b[16];
+        tmem_ld16(taddr, a);
+        tmem_ld16(taddr + 16, b);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            v[i] = a[i];
+            v[16 + i] = b[i];
+        }
+    }
+    tmem_ld_wait();
+}
+
 }  // namespace vmapk

@@ -56,8 +56,10 @@ template <int H> struct Bf16Cfg {
     static constexpr int RAYS = YB + 4 * TM * 4;                  // [32][16]
     static constexpr int LOSS = RAYS + RTMAX * RAYF * 4;          // [4]
     static constexpr int MBAR = LOSS + 16;
-    static constexpr int TSLOT = MBAR + 8;
+    static constexpr int WBAR = MBAR + 8;                         // weight image loaded
+    static constexpr int TSLOT = WBAR + 8;
     static constexpr int BYTES = TSLOT + 8;
+    static_assert(WIMG_BYTES % 16 == 0, "bulk copy size");
 };
 
 __device__ __forceinline__ void st_bf16x8(unsigned char* tile, int off, const float (&v)[8]) {
@@ -148,13 +150,17 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
     float* rays = reinterpret_cast<float*>(sm + C::RAYS);
     float* lossacc = reinterpret_cast<float*>(sm + C::LOSS);
     uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + C::MBAR);
+    uint64_t* wbar = reinterpret_cast<uint64_t*>(sm + C::WBAR);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + C::TSLOT);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int q = warp & 3, hf = warp >> 2;   // TMEM lane quadrant, column half
     const int row = q * 32 + lane;            // the sample (or fan-in lane) this thread reads
 
     // ---- set-up: barrier, tensor memory, constant columns ---------------------
-    if (tid == 0) mbar_init(mbar, 1);
+    if (tid == 0) {
+        mbar_init(mbar, 1);
+        mbar_init(wbar, 1);
+    }
     if (warp == 0) tmem_alloc(tslot, C::NCOLS);
     for (int i = tid; i < 4 * TM; i += blockDim.x) {
         const int l = i / TM, r = i % TM;
@@ -165,8 +171,8 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-    uint32_t phase = 0;
-    bool abort = false;
+    uint32_t phase = 0, wphase = 0;
+    bool abort = false, wpend = false;   // wpend: a weight copy was issued and not yet seen complete
 
     auto wait_mma = [&]() {
         const bool ok = mbar_wait(mbar, phase, MMA_WAIT_LIMIT);
@@ -264,9 +270,12 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
             for (int u = 0; u < 11; ++u) d[u] = rec[u];
         }
         if (first) {
-            const uint4* src = reinterpret_cast<const uint4*>(ba.img + ba.img_off[k]);
-            uint4* dst = reinterpret_cast<uint4*>(W1);
-            for (int i = tid; i < C::WIMG_BYTES / 16; i += blockDim.x) dst[i] = src[i];
+            // the weight image arrives by bulk copy while the tile is encoded
+            if (tid == 0) {
+                mbar_expect_tx(wbar, (uint32_t)C::WIMG_BYTES);
+                bulk_load(W1, ba.img + ba.img_off[k], (uint32_t)C::WIMG_BYTES, wbar);
+                wpend = true;
+            }
             if (tid < 4) lossacc[tid] = 0.f;
         }
         __syncthreads();
@@ -294,6 +303,16 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
         sync_for_mma();
 
         // ---- forward ------------------------------------------------------------
+        if (first) {
+            const bool ok = mbar_wait(wbar, wphase, MMA_WAIT_LIMIT);
+            if (__syncthreads_or(!ok)) {
+                abort = true;
+                if (tid == 0) atomicExch(ba.err, 1);
+                break;
+            }
+            wphase ^= 1;
+            wpend = false;
+        }
         // layer 1: [128 x 96] x W1^T -> C_FWD
         if (tid == 0) {
 #pragma unroll
@@ -302,20 +321,30 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
                          idesc_bf16(TM, H, 0, 0), kc > 0);
             mma_commit(mbar);
         }
+        // this thread's H/2 bias values of layer l, loaded while the MMA runs
+        constexpr int NC = H / 2;
+        float bv[NC];
+        auto load_bias = [&](int l) {
+            const float* b = P + b_off(H, l) + hf * NC;
+#pragma unroll
+            for (int i = 0; i < NC; ++i) bv[i] = __ldg(b + i);
+        };
+        load_bias(0);
         wait_mma();
         if (abort) break;
 #pragma unroll 1
         for (int l = 0; l < 4; ++l) {
             // epilogue of layer l + 1: bias, ReLU, BF16 -> HA[l]
-            const float* bias = P + b_off(H, l);
+            {
+                float v[NC];
+                tmem_ld_cols<NC>(tmem + ((uint32_t)(q * 32) << 16) + C::C_FWD + hf * NC, v);
 #pragma unroll
-            for (int c0 = 0; c0 < H / 2; c0 += 8) {
-                float v[8];
-                tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + C::C_FWD + hf * (H / 2) + c0, v);
-                tmem_ld_wait();
+                for (int c0 = 0; c0 < NC; c0 += 8) {
+                    float u[8];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) v[j] = fmaxf(v[j] + bias[hf * (H / 2) + c0 + j], 0.f);
-                st_bf16x8(HA[l], cm_off(row, hf * (H / 2) + c0, CH), v);
+                    for (int j = 0; j < 8; ++j) u[j] = fmaxf(v[c0 + j] + bv[c0 + j], 0.f);
+                    st_bf16x8(HA[l], cm_off(row, hf * NC + c0, CH), u);
+                }
             }
             sync_for_mma();
             if (tid == 0) {
@@ -332,6 +361,7 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
                 }
                 mma_commit(mbar);
             }
+            if (l < 3) load_bias(l + 1);
             wait_mma();
             if (abort) break;
         }
@@ -381,46 +411,50 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
         sync_for_mma();
 
         // ---- backward -------------------------------------------------------------
-        // layer 5: dW5^T += HA[3]^T dY ; dZ4 = (dY W5) * [h4 > 0]
+        // layer 5: dZ4 = (dY W5) * [h4 > 0] ; dW5^T += HA[3]^T dY
+        // The input-gradient MMA is committed alone: the weight-gradient MMAs
+        // issued after it run while the epilogue works, and the next commit
+        // (which tracks every earlier MMA) covers them.
         if (tid == 0) {
+            mma_bf16(tmem + C::C_DX, desc_kmajor(DYt, 16, 0), desc_mnmajor(W5, H, 0), idesc_bf16(TM, H, 0, 1), false);
+            mma_commit(mbar);
 #pragma unroll
             for (int kc = 0; kc < TM / 16; ++kc)
                 mma_bf16(tmem + C::C_DW5, desc_mnmajor(HA[3], CH, 16 * kc), desc_mnmajor(DYt, 16, 16 * kc),
                          idesc_bf16(TM, 16, 1, 1), !first || kc > 0);
-            mma_bf16(tmem + C::C_DX, desc_kmajor(DYt, 16, 0), desc_mnmajor(W5, H, 0), idesc_bf16(TM, H, 0, 1), false);
-            mma_commit(mbar);
         }
         wait_mma();
         if (abort) break;
         int cur = 0;
         // dX epilogue of layer lp (activation mask from HA[lp - 1]) into DZ[cur]
         auto dx_epilogue = [&](int src_ha, unsigned char* dst) {
+            float v[NC];
+            tmem_ld_cols<NC>(tmem + ((uint32_t)(q * 32) << 16) + C::C_DX + hf * NC, v);
 #pragma unroll
-            for (int c0 = 0; c0 < H / 2; c0 += 8) {
-                float v[8], a[8];
-                tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + C::C_DX + hf * (H / 2) + c0, v);
-                tmem_ld_wait();
-                ld_bf16x8(HA[src_ha], cm_off(row, hf * (H / 2) + c0, CH), a);
+            for (int c0 = 0; c0 < NC; c0 += 8) {
+                float a[8], u[8];
+                ld_bf16x8(HA[src_ha], cm_off(row, hf * NC + c0, CH), a);
 #pragma unroll
-                for (int j = 0; j < 8; ++j) v[j] = a[j] > 0.f ? v[j] : 0.f;
-                st_bf16x8(dst, cm_off(row, hf * (H / 2) + c0, H), v);
+                for (int j = 0; j < 8; ++j) u[j] = a[j] > 0.f ? v[c0 + j] : 0.f;
+                st_bf16x8(dst, cm_off(row, hf * NC + c0, H), u);
             }
         };
         dx_epilogue(3, DZ[cur]);
         sync_for_mma();
 #pragma unroll 1
         for (int l = 3; l >= 1; --l) {
-            // dW_{l+1}^T += HA[l-1]^T dZ_{l+1} ; dZ_l = (dZ_{l+1} W_{l+1}) * [h_l > 0]
+            // dZ_l = (dZ_{l+1} W_{l+1}) * [h_l > 0] ; dW_{l+1}^T += HA[l-1]^T dZ_{l+1}
+            // (DZ[cur] is next written two rounds later, after a commit that covers these MMAs)
             if (tid == 0) {
-#pragma unroll
-                for (int kc = 0; kc < TM / 16; ++kc)
-                    mma_bf16(tmem + C::C_DW1 + l * H, desc_mnmajor(HA[l - 1], CH, 16 * kc),
-                             desc_mnmajor(DZ[cur], H, 16 * kc), idesc_bf16(TM, H, 1, 1), !first || kc > 0);
 #pragma unroll
                 for (int kc = 0; kc < H / 16; ++kc)
                     mma_bf16(tmem + C::C_DX, desc_kmajor(DZ[cur], H, 16 * kc), desc_mnmajor(Wh[l - 1], H, 16 * kc),
                              idesc_bf16(TM, H, 0, 1), kc > 0);
                 mma_commit(mbar);
+#pragma unroll
+                for (int kc = 0; kc < TM / 16; ++kc)
+                    mma_bf16(tmem + C::C_DW1 + l * H, desc_mnmajor(HA[l - 1], CH, 16 * kc),
+                             desc_mnmajor(DZ[cur], H, 16 * kc), idesc_bf16(TM, H, 1, 1), !first || kc > 0);
             }
             wait_mma();
             if (abort) break;
@@ -444,6 +478,8 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
         __syncthreads();
         tc_fence_after();
     }
+    // a weight copy whose wait gave up may still be in flight: give it one more bounded wait
+    if (abort && wpend) mbar_wait(wbar, wphase, MMA_WAIT_LIMIT);
     tc_fence_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, C::NCOLS);

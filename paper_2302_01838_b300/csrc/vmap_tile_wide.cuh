@@ -33,6 +33,7 @@ namespace vmapk {
 
 constexpr int WH = 128;       // hidden width of this path
 constexpr int WJOBS = 5;      // weight-gradient jobs: W1, W2, W3, W4, W5
+constexpr int WIDE_THREADS = 512;   // k_wide_fb: 16 warps, 32 accumulator columns per thread
 
 // per-tile activation record (bytes), every operand a core-matrix tile of 128 rows
 struct WideAct {
@@ -52,14 +53,15 @@ struct WideFbCfg {
     static constexpr int G0 = WIMG + WIMG_BYTES;                  // [128][96]; dY [128][16] after layer 1
     static constexpr int HA = G0 + TM * DINP * 2;                 // current h [128][128]
     static constexpr int DZ = HA + TM * WH * 2;                   // current dZ [128][128]
-    static constexpr int MASK = DZ + TM * WH * 2;                 // [4][128][4] u32: bits of h_l > 0
+    static constexpr int MASK = DZ + TM * WH * 2;                 // [4][128][4] u32: bits of h_l > 0 (word = 32 columns)
     static constexpr int XT = MASK + 4 * TM * 16;                 // [3][128] f32
     static constexpr int TSO = XT + 3 * TM * 4;                   // [128]
     static constexpr int YB = TSO + TM * 4;                       // [4][128]
     static constexpr int RAYS = YB + 4 * TM * 4;                  // [RTMAX][RAYF]
     static constexpr int LOSS = RAYS + RTMAX * RAYF * 4;          // [4]
     static constexpr int MBAR = LOSS + 16;
-    static constexpr int TSLOT = MBAR + 8;
+    static constexpr int WBAR = MBAR + 8;                         // weight image loaded
+    static constexpr int TSLOT = WBAR + 8;
     static constexpr int BYTES = TSLOT + 8;
     static constexpr int NCOLS = 128;
     static_assert(BYTES <= 232448, "shared memory of one CTA");
@@ -96,7 +98,7 @@ __device__ __forceinline__ unsigned long long pos_bits(const float (&v)[8], int 
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(NTHREADS, 1) k_wide_fb(StepParams sp, WideArgs wa) {
+__global__ void __launch_bounds__(WIDE_THREADS, 1) k_wide_fb(StepParams sp, WideArgs wa) {
     using C = WideFbCfg;
     constexpr bool GRAD = MODE == MODE_TRAIN;
     const TileArgs& ta = wa.t;
@@ -114,21 +116,28 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_wide_fb(StepParams sp, WideArgs
     float* yb = reinterpret_cast<float*>(sm + C::YB);
     float* rays = reinterpret_cast<float*>(sm + C::RAYS);
     uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + C::MBAR);
+    uint64_t* wbar = reinterpret_cast<uint64_t*>(sm + C::WBAR);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + C::TSLOT);
+    // 16 warps: warp w reads TMEM lane quadrant w % 4 (the hardware rule) and
+    // accumulator columns (w / 4) * 32 .. + 31
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int q = warp & 3, hf = warp >> 2;
+    const int q = warp & 3, qc = warp >> 2;
     const int row = q * 32 + (tid & 31);
+    const int col0 = qc * 32;
     unsigned char* act = GRAD ? *wa.act : nullptr;
 
-    if (tid == 0) mbar_init(mbar, 1);
+    if (tid == 0) {
+        mbar_init(mbar, 1);
+        mbar_init(wbar, 1);
+    }
     if (warp == 0) tmem_alloc(tslot, C::NCOLS);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
     const uint32_t tl_lane = tmem + ((uint32_t)(q * 32) << 16);
-    uint32_t phase = 0;
-    bool abort = false;
+    uint32_t phase = 0, wphase = 0;
+    bool abort = false, wpend = false;
 
     auto wait_mma = [&]() {
         const bool ok = mbar_wait(mbar, phase, MMA_WAIT_LIMIT);
@@ -146,12 +155,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_wide_fb(StepParams sp, WideArgs
         __syncthreads();
         tc_fence_after();
     };
-    // this thread's 64 accumulator columns (lane = row, columns hf*64 ..)
-    auto load_acc = [&](float (&v)[64]) {
+    // this thread's 32 accumulator columns
+    auto load_acc = [&](float (&v)[32]) {
         float a[16];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            tmem_ld16(tl_lane + hf * 64 + 16 * c, a);
+        for (int c = 0; c < 2; ++c) {
+            tmem_ld16(tl_lane + col0 + 16 * c, a);
 #pragma unroll
             for (int i = 0; i < 16; ++i) v[16 * c + i] = a[i];
         }
@@ -174,16 +183,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_wide_fb(StepParams sp, WideArgs
         const float cx = ob.c[0], cy = ob.c[1], cz = ob.c[2], sc = ob.scale;
         unsigned char* at = GRAD ? act + (long long)tl * WideAct::BYTES : nullptr;
 
+        if (first && tid == 0) {
+            // the weight image arrives by bulk copy while the tile is encoded
+            mbar_expect_tx(wbar, (uint32_t)C::WIMG_BYTES);
+            bulk_load(W1, wa.img + wa.img_off[k], (uint32_t)C::WIMG_BYTES, wbar);
+            wpend = true;
+        }
         for (int r = tid; r < nr; r += blockDim.x) {
             const float* rec = ta.pool + (ta.obs[k].src_off + ta.pick[td.ray0 + r]) * REC;
             float* d = rays + r * RAYF;
 #pragma unroll
             for (int u = 0; u < 11; ++u) d[u] = rec[u];
-        }
-        if (first) {
-            const uint4* src = reinterpret_cast<const uint4*>(wa.img + wa.img_off[k]);
-            uint4* dst = reinterpret_cast<uint4*>(W1);
-            for (int i = tid; i < C::WIMG_BYTES / 16; i += blockDim.x) dst[i] = src[i];
         }
         __syncthreads();
         for (int m = tid; m < TM; m += blockDim.x) {
@@ -207,6 +217,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_wide_fb(StepParams sp, WideArgs
             encode_row_half(sp, xt[m], xt[TM + m], xt[2 * TM + m], m, f / TM, G0, GRAD ? at + WideAct::G0 : nullptr);
         }
         sync_for_mma();
+        if (first) {
+            const bool ok = mbar_wait(wbar, wphase, MMA_WAIT_LIMIT);
+            if (__syncthreads_or(!ok)) {
+                abort = true;
+                if (tid == 0) atomicExch(wa.err, 1);
+                break;
+            }
+            wphase ^= 1;
+            wpend = false;
+        }
 
         // ---- forward -----------------------------------------------------------
         if (tid == 0) {
@@ -216,26 +236,32 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_wide_fb(StepParams sp, WideArgs
                          idesc_bf16(TM, WH, 0, 0), kc > 0);
             mma_commit(mbar);
         }
+        // this thread's 32 bias values of layer l, loaded while the MMA runs
+        float bv[32];
+        auto load_bias = [&](int l) {
+            const float* b = P + b_off(WH, l) + col0;
+#pragma unroll
+            for (int i = 0; i < 32; ++i) bv[i] = __ldg(b + i);
+        };
+        load_bias(0);
         wait_mma();
         if (abort) break;
 #pragma unroll 1
         for (int l = 0; l < 4; ++l) {
-            float v[64];
+            float v[32];
             load_acc(v);
-            const float* bias = P + b_off(WH, l) + hf * 64;
-            unsigned long long bits = 0;
+            unsigned bits = 0;
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
+            for (int c = 0; c < 4; ++c) {
                 float u[8];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) u[j] = fmaxf(v[8 * c + j] + bias[8 * c + j], 0.f);
-                bits |= pos_bits(u, 8 * c);
-                const int off = cm_off(row, hf * 64 + 8 * c, WH);
+                for (int j = 0; j < 8; ++j) u[j] = fmaxf(v[8 * c + j] + bv[8 * c + j], 0.f);
+                bits |= (unsigned)pos_bits(u, 8 * c);
+                const int off = cm_off(row, col0 + 8 * c, WH);
                 st_bf16x8(HA, off, u);
                 if (GRAD) *reinterpret_cast<uint4*>(at + WideAct::h(l) + off) = *reinterpret_cast<const uint4*>(HA + off);
             }
-            *reinterpret_cast<uint2*>(mask + (l * TM + row) * 4 + hf * 2) =
-                make_uint2((uint32_t)bits, (uint32_t)(bits >> 32));
+            mask[(l * TM + row) * 4 + qc] = bits;
             sync_for_mma();
             if (tid == 0) {
                 if (l < 3) {
@@ -251,6 +277,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_wide_fb(StepParams sp, WideArgs
                 }
                 mma_commit(mbar);
             }
+            if (l < 3) load_bias(l + 1);
             wait_mma();
             if (abort) break;
         }
@@ -259,7 +286,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_wide_fb(StepParams sp, WideArgs
             float v[8];
             tmem_ld8(tl_lane, v);
             tmem_ld_wait();
-            if (hf == 0) {
+            if (qc == 0) {
                 const float* b5 = P + b_off(WH, 4);
 #pragma unroll
                 for (int j = 0; j < NOUT; ++j) yb[j * TM + row] = v[j] + b5[j];
@@ -269,7 +296,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_wide_fb(StepParams sp, WideArgs
 
         // ---- rendering, loss, dL/dy (FP32) ---------------------------------------
         const float invR = 1.f / (float)ta.obs[k].R;
-        for (int r = warp; r < nr; r += NTHREADS / 32)
+        for (int r = warp; r < nr; r += blockDim.x / 32)
             render_ray_warp<GRAD, TM>(sp, yb, tsm, rays + r * RAYF, r, S, invR);
         for (int m = M + tid; m < TM; m += blockDim.x) {
             yb[m] = 0.f; yb[TM + m] = 0.f; yb[2 * TM + m] = 0.f; yb[3 * TM + m] = 0.f;
@@ -308,16 +335,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_wide_fb(StepParams sp, WideArgs
             // accumulator = dZ_{l+2} W_{l+2} (dY W5 for l = 3); dZ_{l+1} = acc * [h_{l+1} > 0]
             wait_mma();
             if (abort) break;
-            float v[64];
+            float v[32];
             load_acc(v);
-            const uint2 mb = *reinterpret_cast<const uint2*>(mask + (l * TM + row) * 4 + hf * 2);
-            const unsigned long long bits = ((unsigned long long)mb.y << 32) | mb.x;
+            const unsigned bits = mask[(l * TM + row) * 4 + qc];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
+            for (int c = 0; c < 4; ++c) {
                 float u[8];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) u[j] = (bits >> (8 * c + j)) & 1ull ? v[8 * c + j] : 0.f;
-                const int off = cm_off(row, hf * 64 + 8 * c, WH);
+                for (int j = 0; j < 8; ++j) u[j] = (bits >> (8 * c + j)) & 1u ? v[8 * c + j] : 0.f;
+                const int off = cm_off(row, col0 + 8 * c, WH);
                 st_bf16x8(DZ, off, u);
                 *reinterpret_cast<uint4*>(at + WideAct::dz(l) + off) = *reinterpret_cast<const uint4*>(DZ + off);
             }
@@ -336,6 +362,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_wide_fb(StepParams sp, WideArgs
         __syncthreads();
         tc_fence_after();
     }
+    if (abort && wpend) mbar_wait(wbar, wphase, MMA_WAIT_LIMIT);
     tc_fence_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, C::NCOLS);
@@ -475,12 +502,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_wide_dw(WideArgs wa) {
             }
         }
         __syncthreads();   // every thread is done reading stage s
-        // refill stage s with tile i + NST once tile i's MMAs have read it
-        if (i + C::NST < n) {
+        // refill the stage of tile i - 1 (its MMAs had this iteration to finish)
+        // with tile i - 1 + NST; tile i's own stage is refilled one iteration later
+        if (i >= 1 && i - 1 + C::NST < n) {
+            const int sp_ = (i - 1) % C::NST;
+            const uint32_t pp = (uint32_t)(((i - 1) / C::NST) & 1);
             bool okr = true;
             if (tid == 0) {
-                okr = mbar_wait(empty + s, par, MMA_WAIT_LIMIT);
-                if (okr) issue_load(i + C::NST);
+                okr = mbar_wait(empty + sp_, pp, MMA_WAIT_LIMIT);
+                if (okr) issue_load(i - 1 + C::NST);
             }
             if (__syncthreads_or(!okr)) {
                 abort = true;
