@@ -10,7 +10,10 @@
  *     keyframes);
  *   - draws N_c stratified depths in [t_near, t_s + depth_pad] (Eq. 1) and
  *     N_s depths ~ N(t_s, d_sigma^2) (Eq. 2), t_s = the ray's depth, or t_far
- *     when the depth is invalid (<= 0), sorted ascending;
+ *     when the depth is invalid (<= 0), sorted ascending; a ray off the
+ *     object's mask (M = 0) ends at the surface it hits (supplementary
+ *     material, depth-guided sampling): range [t_near, t_s], Gaussian
+ *     samples clamped above at t_s;
  *   - encodes x~ = (o + t d - c_k) / s_k (supplementary B, object-level
  *     scale) as [x~, sin(B x~), cos(B x~)] (93 features, B is 45 x 3);
  *   - runs the object's MLP 93 -> H -> H -> H -> H -> 4 (ReLU hidden units,

@@ -130,13 +130,17 @@ def sample_object(cfg, pool, n_rays, n_surface, n_strat, stream, step):
     the next words, in pairs (u1, u2), give Box-Muller normals
     z = sqrt(-2 ln u1) * (cos 2 pi u2, sin 2 pi u2), t = t_s + d_sigma z (Eq. 2),
     clamped below at t_n. Surface samples come first, then the stratified
-    ones, and a stable ascending sort orders them.
+    ones, and a stable ascending sort orders them. Rays off the object's mask
+    (M = 0) end where they hit a surface (supplementary "depth guided
+    sampling": rays through the box that do not belong to the object are
+    terminated at the surface they hit): their stratified range stops at t_s
+    and their Gaussian samples are clamped above at t_s.
     """
     n_words = words_per_ray(n_surface, n_strat)
     w = ray_words(cfg.seed, stream, step, np.arange(n_rays), n_words)
     pick = word_to_index(w[:, 0], pool.shape[0])
     depth = pool[pick, R_DEPTH].astype(np.float64)
-    return pick, sample_depths(cfg, depth, w, n_surface, n_strat)
+    return pick, sample_depths(cfg, depth, w, n_surface, n_strat, pool[pick, R_MASK])
 
 
 def sample_given(cfg, rays, n_surface, n_strat, stream, step):
@@ -144,15 +148,17 @@ def sample_given(cfg, rays, n_surface, n_strat, stream, step):
     ``sample_object`` with word 0 (the pick) unused."""
     n_words = words_per_ray(n_surface, n_strat)
     w = ray_words(cfg.seed, stream, step, np.arange(rays.shape[0]), n_words)
-    return sample_depths(cfg, rays[:, R_DEPTH].astype(np.float64), w, n_surface, n_strat)
+    return sample_depths(cfg, rays[:, R_DEPTH].astype(np.float64), w, n_surface, n_strat, rays[:, R_MASK])
 
 
-def sample_depths(cfg, depth, w, n_surface, n_strat):
-    """Eq. 1 and Eq. 2 for rays of the given depths from their Philox words w."""
+def sample_depths(cfg, depth, w, n_surface, n_strat, mask=None):
+    """Eq. 1 and Eq. 2 for rays of the given depths from their Philox words w;
+    rays with mask 0 are terminated at t_s (see ``sample_object``)."""
     n_rays = depth.shape[0]
+    on = np.ones(n_rays, bool) if mask is None else np.asarray(mask) > 0
     ts = np.where(depth > 0.0, depth, cfg.t_far)
     lo = cfg.t_near
-    hi = ts + cfg.depth_pad
+    hi = ts + np.where(on, cfg.depth_pad, 0.0)
     strat = np.empty((n_rays, n_strat))
     for j in range(n_strat):
         u = word_to_unit(w[:, 1 + j])
@@ -165,6 +171,7 @@ def sample_depths(cfg, depth, w, n_surface, n_strat):
         z[:, 2 * p] = rho * np.cos(2.0 * np.pi * u2)
         z[:, 2 * p + 1] = rho * np.sin(2.0 * np.pi * u2)
     surf = np.maximum(ts[:, None] + cfg.d_sigma * z[:, :n_surface], cfg.t_near)
+    surf = np.where(on[:, None], surf, np.minimum(surf, ts[:, None]))
     t = np.concatenate([surf, strat], axis=1)
     return np.sort(t, axis=1, kind="stable")
 

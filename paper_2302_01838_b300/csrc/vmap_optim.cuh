@@ -48,24 +48,24 @@ __device__ __forceinline__ long long wt_index(int H, long long p) {
     return -1;
 }
 
-__device__ __forceinline__ float object_loss(const StepParams& sp, const ObjDev& ob, const ObjBatch& bt,
-                                             const float* __restrict__ part) {
+// Loss of an object from its run slots' sums (Eq. 4-5 as means). Called by
+// a whole warp: lane l sums slots l, l + 32, ... in order, then a fixed
+// butterfly combines the lanes (deterministic).
+__device__ __forceinline__ float object_loss_warp(const StepParams& sp, const ObjDev& ob, const ObjBatch& bt,
+                                                  const float* __restrict__ part) {
     const long long P = param_count(ob.hidden);
     const long long stride = P + NEXTRA;
     const float* e = part + bt.part_off + P;
+    const int lane = threadIdx.x & 31;
     float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-    int t = 0;
-    for (; t + 4 <= bt.n_runs; t += 4) {   // loads four slots at a time, sums in slot order
-        float a[4][3];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) a[u][c] = e[(long long)(t + u) * stride + c];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) { s0 += a[u][0]; s1 += a[u][1]; s2 += a[u][2]; }
-    }
-    for (; t < bt.n_runs; ++t) {
+    for (int t = lane; t < bt.n_runs; t += 32) {
         s0 += e[(long long)t * stride]; s1 += e[(long long)t * stride + 1]; s2 += e[(long long)t * stride + 2];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
     }
     const float R = (float)bt.R;
     return s0 / R + sp.lam_c * (s1 / (3.f * R)) + sp.lam_o * (s2 / R);
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(REDUCE_CHUNK) k_reduce(StepParams sp, const Ob
             const int nr = bt.n_runs;
             const float* src = part + bt.part_off + p;
             int t = 0;
-            for (; t + 8 <= nr; t += 8) {
+            for (; t + 8 <= nr; t += 8) {   // eight loads in flight, added in slot order
                 float v[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u) v[u] = src[(long long)(t + u) * stride];
@@ -123,10 +123,10 @@ __global__ void __launch_bounds__(REDUCE_CHUNK) k_reduce(StepParams sp, const Ob
             for (; t < nr; ++t) g += src[(long long)t * stride];
         }
         __syncthreads();   // sh_loss of the previous item has been read
-        if (threadIdx.x == 0) {
-            const float L = object_loss(sp, ob, bt, part);
-            sh_loss = L;
-            if (item.y == 0) {
+        if (threadIdx.x < 32) {
+            const float L = object_loss_warp(sp, ob, bt, part);
+            if (threadIdx.x == 0) sh_loss = L;
+            if (threadIdx.x == 0 && item.y == 0) {
                 if (loss_out) loss_out[k] = frozen ? __int_as_float(0x7fc00000) : L;
                 if (dcenter_out) {
                     float d[3] = {0.f, 0.f, 0.f};

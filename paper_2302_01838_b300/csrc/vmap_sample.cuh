@@ -23,7 +23,11 @@ __device__ __forceinline__ int upper_index(const int* off, int n, int i) {
 //   words 1..N_c    -> u_j, t = t_n + (j + u_j) / N_c * (t_s + pad - t_n)      (Eq. 1)
 //   next word pairs -> Box-Muller z = sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2),
 //                      t = max(t_s + d_sigma z, t_n)                            (Eq. 2)
-// t_s is the ray's depth, or t_far when the depth is not positive. Slots
+// t_s is the ray's depth, or t_far when the depth is not positive. A ray off
+// the object's mask (M = 0) ends at the surface it hits (the supplementary
+// material's termination of rays that cross the box but belong to another
+// surface): its stratified range stops at t_s, its Gaussian samples are
+// clamped above at t_s. Slots
 // 0..N_s-1 hold the surface samples, N_s.. the stratified ones; the stable
 // ascending order is each value's rank (ties broken by slot).
 constexpr int SAMPLE_RAYS_PER_BLOCK = 8;
@@ -64,9 +68,10 @@ __global__ void __launch_bounds__(32 * SAMPLE_RAYS_PER_BLOCK) k_sample(
                                  : (long long)(((unsigned long long)w0 * (unsigned long long)ob.pool_n) >> 32);
     if (lane == 0) pick_out[i] = (int)pick;
     const float depth = src[(bt.src_off + pick) * REC + 6];
+    const bool on_mask = src[(bt.src_off + pick) * REC + 10] > 0.f;
     const float ts = depth > 0.f ? depth : sp.t_far;
     const float lo = sp.t_near;
-    const float span = ts + sp.depth_pad - lo;
+    const float span = ts + (on_mask ? sp.depth_pad : 0.f) - lo;
 
     float t = INFINITY;
     if (lane < Ns) {
@@ -76,6 +81,7 @@ __global__ void __launch_bounds__(32 * SAMPLE_RAYS_PER_BLOCK) k_sample(
         float sn, cs;
         sincospif(2.0f * u2, &sn, &cs);
         t = fmaxf(ts + sp.d_sigma * (rho * ((lane & 1) ? sn : cs)), lo);
+        if (!on_mask) t = fminf(t, ts);
     } else if (lane < S) {
         const int q = lane - Ns;
         const float u = word_to_unit(wa);

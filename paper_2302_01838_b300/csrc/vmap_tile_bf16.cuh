@@ -173,6 +173,8 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
     const uint32_t tmem = *tslot;
     uint32_t phase = 0, wphase = 0;
     bool abort = false, wpend = false;   // wpend: a weight copy was issued and not yet seen complete
+    bool pre = false;                    // this tile's rays and depths were prefetched
+    int npick = 0;                       // pick of the next tile's ray `tid`
 
     auto wait_mma = [&]() {
         const bool ok = mbar_wait(mbar, phase, MMA_WAIT_LIMIT);
@@ -263,11 +265,17 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
         const float cx = ob.c[0], cy = ob.c[1], cz = ob.c[2], sc = ob.scale;
 
         // ---- rays, depths, points; weights at the start of a run ---------------
-        for (int r = tid; r < nr; r += blockDim.x) {
-            const float* rec = ta.pool + (ta.obs[k].src_off + ta.pick[td.ray0 + r]) * REC;
-            float* d = rays + r * RAYF;
+        // (after the first tile of a training range, the previous tile's
+        // backward already brought this tile's rays and depths in by cp.async)
+        if (!pre) {
+            for (int r = tid; r < nr; r += blockDim.x) {
+                const float* rec = ta.pool + (ta.obs[k].src_off + ta.pick[td.ray0 + r]) * REC;
+                float* d = rays + r * RAYF;
 #pragma unroll
-            for (int u = 0; u < 11; ++u) d[u] = rec[u];
+                for (int u = 0; u < 11; ++u) d[u] = rec[u];
+            }
+        } else {
+            cp_async_wait_all();
         }
         if (first) {
             // the weight image arrives by bulk copy while the tile is encoded
@@ -284,7 +292,7 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
             if (m < M) {
                 const int r = m / S;
                 const float* d = rays + r * RAYF;
-                t = ta.tbuf[sbase + m];
+                t = pre ? tsm[m] : ta.tbuf[sbase + m];
                 x0 = (fmaf(t, d[3], d[0]) - cx) / sc;
                 x1 = (fmaf(t, d[4], d[1]) - cy) / sc;
                 x2 = (fmaf(t, d[5], d[2]) - cz) / sc;
@@ -330,6 +338,13 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
             for (int i = 0; i < NC; ++i) bv[i] = __ldg(b + i);
         };
         load_bias(0);
+        // the next tile of this range: its picks now, its rays and depths during the backward
+        const bool has_next = GRAD && tl + 1 < t1;
+        TileDev tdn{};
+        if (has_next) {
+            tdn = ta.tiles[tl + 1];
+            if (tid < tdn.nr) npick = ta.pick[tdn.ray0 + tid];
+        }
         wait_mma();
         if (abort) break;
 #pragma unroll 1
@@ -409,6 +424,23 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
             st_bf16x8(DYt, cm_off(r, half * 8, 16), v);
         }
         sync_for_mma();
+        // rays, depths and the loss terms of this tile are consumed: prefetch the next tile's
+        pre = false;
+        if (has_next) {
+            const ObjBatch& obn = ta.obs[tdn.obj];
+            const int Sn = ta.objs[tdn.obj].S;
+            if (tid < tdn.nr) {
+                const float* rec = ta.pool + (obn.src_off + npick) * REC;
+                float* d = rays + tid * RAYF;
+                cp_async16(d, rec);
+                cp_async16(d + 4, rec + 4);
+                cp_async16(d + 8, rec + 8);
+            }
+            const long long sb = obn.sample_off + (long long)(tdn.ray0 - obn.ray_off) * Sn;
+            if (tid < tdn.nr * Sn) cp_async4(tsm + tid, ta.tbuf + sb + tid);
+            cp_async_commit();
+            pre = true;
+        }
 
         // ---- backward -------------------------------------------------------------
         // layer 5: dZ4 = (dY W5) * [h4 > 0] ; dW5^T += HA[3]^T dY
@@ -480,6 +512,7 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
     }
     // a weight copy whose wait gave up may still be in flight: give it one more bounded wait
     if (abort && wpend) mbar_wait(wbar, wphase, MMA_WAIT_LIMIT);
+    cp_async_wait_all();   // prefetches issued before an abort land before the CTA exits
     tc_fence_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, C::NCOLS);

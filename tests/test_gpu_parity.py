@@ -475,8 +475,8 @@ def test_autotuner_and_launch_shapes_keep_parity():
 
 def test_full_objective_with_off_mask_rays_matches_oracle():
     """Eq. 5 with the occupancy term (lambda_2 = 10): pools that hold off-mask
-    rays (mask 0, so they add only to the occupancy term), hidden 32 and 64,
-    10 steps against the oracle."""
+    rays (mask 0: they add only to the occupancy term and are terminated at
+    the surface they hit), hidden 32 and 64, 10 steps against the oracle."""
     rng = np.random.default_rng(21)
     objs = []
     for H in (32, 64, 32):
@@ -494,6 +494,8 @@ def test_full_objective_with_off_mask_rays_matches_oracle():
     loss = torch.empty(K, device="cuda")
     for step in range(10):
         vm.sample_rays([150] * K)
+        if step < 2:   # off-mask rays end at their surface: draws bit-exact / to FP32 rounding
+            _check_samples(vm, sc, [150] * K, [step] * K)
         vm.train_step(loss)
         Lo = vs.train_step(cfg, ost, [150] * K)
         rel = np.abs(loss.cpu().numpy().astype(np.float64) - Lo) / np.abs(Lo)

@@ -133,3 +133,31 @@ def test_given_rays_reuse_the_pick_stream_layout():
     pick, t = vs.sample_object(cfg, pool, 64, 10, 12, stream=4, step=2)
     t2 = vs.sample_given(cfg, pool[pick], 10, 12, stream=4, step=2)
     assert np.array_equal(t, t2)
+
+
+def test_off_mask_rays_end_at_their_surface():
+    """Rays off the object's mask stop at the surface they hit: every sample
+    <= t_s, one stratified sample per stratum of [t_n, t_s]; rays on the mask
+    draw exactly what they draw without a mask column."""
+    from oracle import vmap_step as vs
+    from oracle.philox import ray_words
+    cfg = vs.Config(seed=9)
+    rng = np.random.default_rng(3)
+    depth = rng.uniform(0.5, 3.0, 400)
+    mask = (np.arange(400) % 3 != 0).astype(np.float64)
+    ns, nc = 10, 12
+    w = ray_words(cfg.seed, 4, 7, np.arange(400), vs.words_per_ray(ns, nc))
+    t = vs.sample_depths(cfg, depth, w, ns, nc, mask)
+    t_plain = vs.sample_depths(cfg, depth, w, ns, nc)
+    on = mask > 0
+    assert np.array_equal(t[on], t_plain[on])
+    off = ~on
+    assert np.all(t[off] <= depth[off, None]) and np.all(t[off] >= cfg.t_near)
+    # stratified samples of off-mask rays: u_j from words 1..N_c, t_j in stratum j of [t_n, t_s]
+    u = vs.word_to_unit(w[off, 1:1 + nc])
+    strat = cfg.t_near + (np.arange(nc) + u) / nc * (depth[off, None] - cfg.t_near)
+    for r in range(strat.shape[0]):
+        for j in range(nc):
+            assert np.any(np.isclose(t[off][r], strat[r, j], rtol=0, atol=1e-12))
+    # some Gaussian samples would have passed t_s: they sit exactly at t_s
+    assert np.sum(t[off] == depth[off, None]) > 0
