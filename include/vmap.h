@@ -185,6 +185,21 @@ vmap_status vmap_query_occupancy(vmap_ctx* ctx, int obj, const float* pts, long 
 vmap_status vmap_render_depth(vmap_ctx* ctx, int obj, const float* rays, long long n,
                               const float* box_half, int n_samples, float* depth);
 
+/* Compositional scene render (section 3.4): each listed object renders the
+ * rays inside its box c_k +- box_half[j] with n_samples midpoints (as
+ * vmap_render_depth), giving (O^, D^, C^) per ray; the objects a ray meets
+ * are ranked by their expected hit depth D^/O^ (ties: earlier list entry
+ * first; O^ = 0 skipped) and composed front to back as Eq. 3 composes
+ * samples: D = sum A_k D^_k, C = sum A_k C^_k, O = sum A_k O^_k with
+ * A_k = prod over earlier-ranked objects of (1 - O^_j).
+ *   rays: DEVICE [n][12] (origin and direction read); objs: HOST [m] object
+ *   indices, or NULL for objects 0..m-1; box_half: HOST [m][3];
+ *   depth: DEVICE [n]; rgb: DEVICE [n][3] or NULL; occ: DEVICE [n] or NULL.
+ * Keeps m * n * 5 floats of scratch in the context (grown on demand, which
+ * synchronises). n = 0 is a no-op. */
+vmap_status vmap_render_scene(vmap_ctx* ctx, const float* rays, long long n, const int* objs, int m,
+                              const float* box_half, int n_samples, float* depth, float* rgb, float* occ);
+
 /* Object state in canonical layout. Any DEVICE pointer may be NULL.
  * step: HOST, may be NULL (reading it synchronises). */
 vmap_status vmap_get_object_state(vmap_ctx* ctx, int obj, float* params, float* m, float* v,

@@ -175,6 +175,15 @@ class VMap:
         self._check(self.lib.vmap_query_occupancy(self.h, int(obj), _ptr(pts), pts.shape[0],
                                                   _ptr(occ), _ptr(rgb)))
 
+    def render_scene(self, rays, objs, box_half, n_samples, depth, rgb=None, occ=None):
+        """Occlusion-aware render of the listed objects (vmap_render_scene)."""
+        objs = list(objs)
+        oa = (ctypes.c_int * len(objs))(*objs)
+        hb = np.ascontiguousarray(np.asarray(box_half, np.float32).reshape(len(objs), 3))
+        self._check(self.lib.vmap_render_scene(self.h, _ptr(rays), rays.shape[0], oa, len(objs),
+                                               hb.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), int(n_samples),
+                                               _ptr(depth), _ptr(rgb), _ptr(occ)))
+
     def render_depth(self, obj, rays, box_half, n_samples, depth):
         hb = (ctypes.c_float * 3)(*[float(x) for x in box_half])
         self._check(self.lib.vmap_render_depth(self.h, int(obj), _ptr(rays), rays.shape[0], hb,

@@ -18,6 +18,7 @@
 #include "vmap_common.cuh"
 #include "vmap_optim.cuh"
 #include "vmap_sample.cuh"
+#include "vmap_scene.cuh"
 #include "vmap_tile_bf16.cuh"
 #include "vmap_tile_fp32.cuh"
 #include "vmap_tile_wide.cuh"
@@ -120,6 +121,9 @@ struct vmap_ctx {
     unsigned char** act_pp_d = nullptr;
     long long act_cap = 0;          // tiles
     float* tile_loss_d = nullptr;   // [tile_cap][4]
+    // scene rendering: per (object, ray) records, grown on demand
+    float* scene_d = nullptr;
+    long long scene_cap = 0;        // floats
 
     // CUDA graphs (captured on a private stream, replayed on the context stream)
     bool graph_on = false;
@@ -685,7 +689,8 @@ vmap_status vmap_destroy(vmap_ctx* ctx) {
                     ctx->params_d, ctx->wt_d,     ctx->m_d,      ctx->v_d,     ctx->pool_d,   ctx->pick_d,
                     ctx->t_d,      ctx->bobj_d,   ctx->bray_d,   ctx->tiles_d, ctx->flags_d,  ctx->part_d,
                     ctx->items_d,  ctx->counts_d, ctx->given_d,  ctx->loss_d,  ctx->err_d,  ctx->img_off_d,
-                    ctx->img_d,    ctx->act_d,    ctx->act_pp_d, ctx->tile_loss_d, ctx->sig_d,  ctx->done_d};
+                    ctx->img_d,    ctx->act_d,    ctx->act_pp_d, ctx->tile_loss_d, ctx->sig_d,  ctx->done_d,
+                    ctx->scene_d};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& p : ctx->pending) {
@@ -872,6 +877,50 @@ vmap_status vmap_render_depth(vmap_ctx* ctx, int obj, const float* rays, long lo
     const long long blocks = (n + rt - 1) / rt;
     cudaError_t e = launch_tile_c<MODE_EVAL>(c, (int)blocks, ctx->stream, ctx->sp, ta);
     if (e != cudaSuccess) return fail(ctx, VMAP_ERR_CUDA, "eval kernel failed: %s", cudaGetErrorString(e));
+    return VMAP_OK;
+}
+
+vmap_status vmap_render_scene(vmap_ctx* ctx, const float* rays, long long n, const int* objs, int m,
+                              const float* box_half, int n_samples, float* depth, float* rgb, float* occ) {
+    if (!ctx) return VMAP_ERR_ARG;
+    if (!rays || !box_half || !depth) return fail(ctx, VMAP_ERR_ARG, "null argument");
+    if (n < 0 || m < 1) return fail(ctx, VMAP_ERR_ARG, "need n >= 0 rays and m >= 1 objects");
+    for (int j = 0; j < m; ++j) {
+        const int k = objs ? objs[j] : j;
+        if (vmap_status s = check_obj(ctx, k)) return s;
+        const int c = class_of(ctx->objs[k].hidden);
+        if (n_samples < 1 || n_samples > mmax_of(c))
+            return fail(ctx, VMAP_ERR_ARG, "n_samples must be in [1, %d] for hidden %d", mmax_of(c), hidden_of(c));
+    }
+    if (n == 0) return VMAP_OK;
+    const long long need = (long long)m * n * 5;
+    if (need > ctx->scene_cap) {
+        CU(cudaStreamSynchronize(ctx->stream));
+        if (ctx->scene_d) CU(cudaFree(ctx->scene_d));
+        ctx->scene_d = nullptr;
+        ctx->scene_cap = 0;
+        CU(cudaMalloc((void**)&ctx->scene_d, sizeof(float) * need));
+        ctx->scene_cap = need;
+    }
+    for (int j = 0; j < m; ++j) {
+        const int k = objs ? objs[j] : j;
+        const int c = class_of(ctx->objs[k].hidden);
+        TileArgs ta = base_args(ctx);
+        ta.pool = rays;
+        ta.eval_out = nullptr;
+        ta.eval_rec = ctx->scene_d + (long long)j * n * 5;
+        for (int a = 0; a < 3; ++a) ta.eval_half[a] = box_half[3 * j + a];
+        ta.eval_obj = k;
+        ta.eval_n = n;
+        ta.eval_S = n_samples;
+        const int rt = std::min(RTMAX, mmax_of(c) / n_samples);
+        const long long blocks = (n + rt - 1) / rt;
+        cudaError_t e = launch_tile_c<MODE_EVAL>(c, (int)blocks, ctx->stream, ctx->sp, ta);
+        if (e != cudaSuccess) return fail(ctx, VMAP_ERR_CUDA, "eval kernel failed: %s", cudaGetErrorString(e));
+    }
+    const int blocks = (int)std::min<long long>((n + 255) / 256, (long long)ctx->n_sm * 16);
+    k_compose<<<blocks, 256, 0, ctx->stream>>>(ctx->scene_d, m, n, depth, rgb, occ);
+    CHECK_LAUNCH("k_compose");
     return VMAP_OK;
 }
 

@@ -267,7 +267,8 @@ struct TileArgs {
     const float* params;      // canonical parameter arena
     const float* wt;          // transposed-weight arena
     float* part;              // run partial slots
-    float* eval_out;          // MODE_EVAL: rendered depth per ray
+    float* eval_out;          // MODE_EVAL: rendered depth per ray, or NULL
+    float* eval_rec;          // MODE_EVAL: [n][5] (O^, D^, C^) per ray, or NULL
     float eval_half[3];       // MODE_EVAL: box half extents
     int eval_obj;             // MODE_EVAL / MODE_QUERY: the object
     long long eval_n;         // MODE_EVAL: rays; MODE_QUERY: points
@@ -430,7 +431,23 @@ __global__ void __launch_bounds__(NTHREADS, TileCfg<H>::CTAS) k_tile_fp32(StepPa
                     d[12] = tf;
                 }
             }
-            __syncthreads();
+            if (MODE == MODE_EVAL) {
+                // a tile whose rays all miss the box renders zeros without the MLP
+                // (ray r's entry/exit were written by thread r itself)
+                const int r = threadIdx.x;
+                const bool any =
+                    __syncthreads_or(r < nr && rays[r * RAYF + 12] > rays[r * RAYF + 11] && rays[r * RAYF + 12] > 0.f);
+                if (!any) {
+                    for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+                        if (ta.eval_out) ta.eval_out[ray_first + r] = 0.f;
+                        if (ta.eval_rec)
+                            for (int q = 0; q < 5; ++q) ta.eval_rec[(ray_first + r) * 5 + q] = 0.f;
+                    }
+                    continue;
+                }
+            } else {
+                __syncthreads();
+            }
         }
 
         // ---- points x~ = (o + t d - c) / s ----------------------------------
@@ -495,15 +512,30 @@ __global__ void __launch_bounds__(NTHREADS, TileCfg<H>::CTAS) k_tile_fp32(StepPa
             if (threadIdx.x < nr) {
                 const int r = threadIdx.x;
                 const float* d = rays + r * RAYF;
-                float Pr = 1.f, Dh = 0.f;
+                float Pr = 1.f, Dh = 0.f, Oh = 0.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
                 for (int i = 0; i < S; ++i) {
                     const int m = r * S + i;
                     const float o = sigmoidf_(yb[m]);
-                    Dh = fmaf(o * Pr, tsm[m], Dh);
+                    const float T = o * Pr;
+                    Dh = fmaf(T, tsm[m], Dh);
+                    Oh += T;
+                    if (ta.eval_rec) {
+                        C0 = fmaf(T, sigmoidf_(yb[LD + m]), C0);
+                        C1 = fmaf(T, sigmoidf_(yb[2 * LD + m]), C1);
+                        C2 = fmaf(T, sigmoidf_(yb[3 * LD + m]), C2);
+                    }
                     Pr = Pr * (1.f - o);
                 }
                 const bool hit = d[12] > d[11] && d[12] > 0.f;
-                ta.eval_out[ray_first + r] = hit ? Dh : 0.f;
+                if (ta.eval_out) ta.eval_out[ray_first + r] = hit ? Dh : 0.f;
+                if (ta.eval_rec) {
+                    float* e = ta.eval_rec + (ray_first + r) * 5;
+                    e[0] = hit ? Oh : 0.f;
+                    e[1] = hit ? Dh : 0.f;
+                    e[2] = hit ? C0 : 0.f;
+                    e[3] = hit ? C1 : 0.f;
+                    e[4] = hit ? C2 : 0.f;
+                }
             }
             continue;
         }

@@ -82,6 +82,8 @@ SIGNATURES = {
     "vmap_backward": (_I, [_P, _P, _P, _P]),
     "vmap_query_occupancy": (_I, [_P, _I, _P, _LL, _P, _P]),
     "vmap_render_depth": (_I, [_P, _I, _P, _LL, ctypes.POINTER(ctypes.c_float), _I, _P]),
+    "vmap_render_scene": (_I, [_P, _P, _LL, ctypes.POINTER(ctypes.c_int), _I, ctypes.POINTER(ctypes.c_float), _I,
+                               _P, _P, _P]),
     "vmap_get_object_state": (_I, [_P, _I, _P, _P, _P, _IP]),
     "vmap_set_object_state": (_I, [_P, _I, _P, _P, _P, _I]),
     "vmap_get_params": (_I, [_P, _P]),

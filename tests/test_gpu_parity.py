@@ -503,3 +503,43 @@ def test_full_objective_with_off_mask_rays_matches_oracle():
     for k in range(K):
         errs = vh.layer_errors(vm.get_object_state(k)[0].cpu().numpy(), ost[k].params, ost[k].H)
         assert max(errs) <= W_RTOL, f"object {k}: weight errors {errs}"
+
+
+def test_scene_render_composes_objects_by_rendered_depth():
+    """Section 3.4: per-object renders inside each object's box, ranked by
+    rendered depth and composed front to back, against the oracle."""
+    rng = np.random.default_rng(61)
+    objs = []
+    for H in (16, 32, 64, 128):
+        o = scenes.make_object(rng, (1, 2), 0.15, 0.35, 0.2, H=H, per_view=64, room=(0.4, 0.4, 0.2))
+        o["init"] = scenes.init_weights(rng, H)
+        o["n_surface"], o["n_strat"] = 10, 12
+        o["rays"] = 32
+        objs.append(o)
+    sc = dict(objects=objs, B=scenes.make_B(62), seed=61)
+    vm = vh.library_context(sc)
+    eye = np.array([0.3, -4.0, 1.2])
+    Rwc = scenes.look_at(eye, np.array([0.0, 0.0, 1.0]))
+    u, v = np.meshgrid(np.arange(0, 640, 16), np.arange(0, 480, 16))
+    o_, d_ = scenes.camera_rays(Rwc, eye, u.ravel().astype(np.float64), v.ravel().astype(np.float64))
+    rays = np.zeros((o_.shape[0], 12), np.float32)
+    rays[:, 0:3], rays[:, 3:6] = o_, d_
+    n = rays.shape[0]
+    half = [[float(o["scale"])] * 3 for o in objs]
+    depth = torch.empty(n, device="cuda")
+    rgb = torch.empty(n, 3, device="cuda")
+    occ = torch.empty(n, device="cuda")
+    vm.render_scene(torch.from_numpy(rays).cuda(), [0, 1, 2, 3], half, 24, depth, rgb, occ)
+    cfg = vh.oracle_config(sc)
+    recs = [ev.render_object(cfg, o["init"].astype(np.float64), o["H"], o["center"], o["scale"], rays, half[k], 24)
+            for k, o in enumerate(objs)]
+    D, C, O = ev.compose(recs)
+    meets = sum((r[0] > 0).astype(int) for r in recs)
+    assert np.sum(meets >= 2) >= 20 and np.sum(meets == 0) >= 20   # overlaps and misses both occur
+    tol = 1e-4 * float(np.max(D))
+    assert np.max(np.abs(depth.cpu().numpy() - D)) <= tol
+    assert np.max(np.abs(rgb.cpu().numpy() - C)) <= 1e-4
+    assert np.max(np.abs(occ.cpu().numpy() - O)) <= 1e-4
+    # a listed subset composes only those objects
+    vm.render_scene(torch.from_numpy(rays).cuda(), [2], [half[2]], 24, depth)
+    assert np.max(np.abs(depth.cpu().numpy() - recs[2][1])) <= tol

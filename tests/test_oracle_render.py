@@ -171,3 +171,47 @@ def test_eval_ray_box_and_render_closed_forms():
     # a miss renders 0
     rays[1, 0:3] = [5, 5, 5]
     assert ev.render_depth(cfg, p, H, np.zeros(3), 1.0, rays, [1, 1, 1], 10)[1] == 0.0
+
+
+def test_scene_compose_closed_forms():
+    """Scene composition (occlusion by rendered depth): one object is its own
+    render; an opaque nearer object hides the farther; two semi-transparent
+    layers compose as D1 + (1 - O1) D2; listing order does not matter."""
+    from oracle import evaluate as ev
+    rng = np.random.default_rng(0)
+    n = 50
+    def rec(O, z):
+        O = np.asarray(O, np.float64)
+        return O, O * z, O[:, None] * rng.uniform(0, 1, (n, 3))
+    a = rec(rng.uniform(0.1, 0.9, n), 1.0)
+    b = rec(rng.uniform(0.1, 0.9, n), 2.0)
+    D, C, O = ev.compose([a])
+    assert np.allclose(D, a[1]) and np.allclose(C, a[2]) and np.allclose(O, a[0])
+    opaque = rec(np.ones(n), 0.5)
+    D, C, O = ev.compose([b, opaque])
+    assert np.allclose(D, opaque[1]) and np.allclose(C, opaque[2]) and np.allclose(O, 1.0)
+    D, C, O = ev.compose([b, a])
+    assert np.allclose(D, a[1] + (1 - a[0]) * b[1])
+    assert np.allclose(C, a[2] + (1 - a[0])[:, None] * b[2])
+    assert np.allclose(O, 1 - (1 - a[0]) * (1 - b[0]))
+    D2, C2, O2 = ev.compose([a, b])
+    assert np.array_equal(D, D2) and np.array_equal(C, C2)
+    # a ray no object meets renders nothing
+    empty = (np.zeros(n), np.zeros(n), np.zeros((n, 3)))
+    D, C, O = ev.compose([empty, empty])
+    assert not D.any() and not C.any() and not O.any()
+
+
+def test_render_object_matches_depth_render():
+    from oracle import evaluate as ev
+    from oracle import vmap_step as vs
+    from paper_2302_01838_b300 import scenes
+    rng = np.random.default_rng(4)
+    o = scenes.make_object(rng, (1, 2), 0.1, 0.3, 0.2, H=16, per_view=64)
+    cfg = vs.Config(seed=1, B=scenes.make_B(5))
+    p = scenes.init_weights(rng, 16).astype(np.float64)
+    rays = o["pool"][:40].astype(np.float64)
+    half = [0.4, 0.4, 0.4]
+    O, D, C = ev.render_object(cfg, p, 16, o["center"], o["scale"], rays, half, 24)
+    assert np.allclose(D, ev.render_depth(cfg, p, 16, o["center"], o["scale"], rays, half, 24))
+    assert np.all((O >= 0) & (O <= 1)) and np.all(C >= 0) and np.all(C <= O[:, None] + 1e-12)
