@@ -87,6 +87,7 @@ struct vmap_ctx {
     int* pick_d = nullptr;
     float* t_d = nullptr;
     int *bobj_d = nullptr, *bray_d = nullptr;
+    int* ray_bj_d = nullptr;        // batch object of each batch ray (written by the builder)
     TileDev* tiles_d = nullptr;
     int* flags_d = nullptr;
     int tile_cap = 0;
@@ -386,6 +387,7 @@ vmap_status launch_build_sample(vmap_ctx* ctx, int given) {
     a.tile_cap = ctx->tile_cap;
     a.bobj = ctx->bobj_d;
     a.bray = ctx->bray_d;
+    a.ray_bj = ctx->ray_bj_d;
     a.items = ctx->items_d;
     a.counts = ctx->counts_d;
     a.sig = ctx->sig_d;
@@ -396,7 +398,7 @@ vmap_status launch_build_sample(vmap_ctx* ctx, int given) {
     const int blocks = (ctx->cfg.max_rays_total + SAMPLE_RAYS_PER_BLOCK - 1) / SAMPLE_RAYS_PER_BLOCK;
     pi = prof_begin(ctx, PS_SAMPLE);
     k_sample<<<blocks, 32 * SAMPLE_RAYS_PER_BLOCK, 0, ctx->stream>>>(ctx->sp, ctx->objs_d, ctx->ob_d, ctx->bobj_d, ctx->bray_d,
-                                             ctx->counts_d, given ? ctx->given_d : ctx->pool_d, given,
+                                             ctx->ray_bj_d, ctx->counts_d, given ? ctx->given_d : ctx->pool_d, given,
                                              ctx->steps_d, ctx->pick_d, ctx->t_d);
     prof_end(ctx, pi);
     CHECK_LAUNCH("k_sample");
@@ -637,6 +639,7 @@ vmap_status vmap_init_objects(vmap_ctx** out, const vmap_config* cfg, void* cuda
     ALLOC(ctx->t_d, sizeof(float) * (size_t)cfg->max_rays_total * SMAX);
     ALLOC(ctx->bobj_d, sizeof(int) * K);
     ALLOC(ctx->bray_d, sizeof(int) * K);
+    ALLOC(ctx->ray_bj_d, sizeof(int) * (size_t)cfg->max_rays_total);
     ctx->tile_cap = cfg->max_rays_total + 16;
     ALLOC(ctx->tiles_d, sizeof(TileDev) * (size_t)ctx->tile_cap * NCLASS);
     ALLOC(ctx->flags_d, sizeof(int) * (size_t)ctx->tile_cap * NCLASS);
@@ -690,7 +693,7 @@ vmap_status vmap_destroy(vmap_ctx* ctx) {
                     ctx->t_d,      ctx->bobj_d,   ctx->bray_d,   ctx->tiles_d, ctx->flags_d,  ctx->part_d,
                     ctx->items_d,  ctx->counts_d, ctx->given_d,  ctx->loss_d,  ctx->err_d,  ctx->img_off_d,
                     ctx->img_d,    ctx->act_d,    ctx->act_pp_d, ctx->tile_loss_d, ctx->sig_d,  ctx->done_d,
-                    ctx->scene_d};
+                    ctx->scene_d,  ctx->ray_bj_d};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& p : ctx->pending) {

@@ -169,7 +169,7 @@ extern "C" vmap_status vmap_object_grad_static(const vmap_config* cfg, const vma
     a.items = items;
     a.counts = counts;
     k_build<<<1, BUILD_THREADS, 0, st>>>(a);
-    k_sample<<<(NA_MAX_RAYS + SAMPLE_RAYS_PER_BLOCK - 1) / SAMPLE_RAYS_PER_BLOCK, 32 * SAMPLE_RAYS_PER_BLOCK, 0, st>>>(sp, objs, ob, bobj, bray, counts, desc->rays, 1, ints + 3,
+    k_sample<<<(NA_MAX_RAYS + SAMPLE_RAYS_PER_BLOCK - 1) / SAMPLE_RAYS_PER_BLOCK, 32 * SAMPLE_RAYS_PER_BLOCK, 0, st>>>(sp, objs, ob, bobj, bray, nullptr, counts, desc->rays, 1, ints + 3,
                                                        pick, tbuf);
     TileArgs ta{};
     ta.objs = objs;

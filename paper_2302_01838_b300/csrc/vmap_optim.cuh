@@ -32,6 +32,38 @@ __host__ __device__ constexpr long long img_count(int H) { return (long long)H *
 
 
 
+// Weight element p of an object of width H (a power of two) -> (layer l,
+// output row n, input column k), or -1 for a bias. 32-bit arithmetic; the
+// only division is by the constant fan-in of layer 1.
+__device__ __forceinline__ int weight_of(int H, int p, int& n, int& k) {
+    const int lg = __ffs(H) - 1;
+    if (p < DIN * H) {
+        n = p / DIN;
+        k = p - n * DIN;
+        return 0;
+    }
+    int base = DIN * H + H;
+    if (p < base) return -1;
+#pragma unroll
+    for (int l = 1; l < 4; ++l) {
+        if (p < base + H * H) {
+            const int q = p - base;
+            n = q >> lg;
+            k = q & (H - 1);
+            return l;
+        }
+        base += H * H + H;
+        if (p < base) return -1;
+    }
+    if (p < base + NOUT * H) {
+        const int q = p - base;
+        n = q >> lg;
+        k = q & (H - 1);
+        return 4;
+    }
+    return -1;
+}
+
 // index of canonical parameter p in the transposed shadow, or -1 for a bias
 __device__ __forceinline__ long long wt_index(int H, long long p) {
 #pragma unroll 1
@@ -91,7 +123,7 @@ __global__ void __launch_bounds__(REDUCE_CHUNK) k_reduce(StepParams sp, const Ob
                                                          float* __restrict__ dcenter_out,
                                                          __nv_bfloat16* img, const long long* __restrict__ img_off,
                                                          int* done) {
-    __shared__ float sh_loss;
+    __shared__ float sh_loss, sh_bc1, sh_bc2;
     __shared__ int sh_last;
     const int n_items = counts[BC_ITEMS];
 #pragma unroll 1
@@ -109,23 +141,34 @@ __global__ void __launch_bounds__(REDUCE_CHUNK) k_reduce(StepParams sp, const Ob
         // this thread's gradient: slots summed in slot order, loads issued eight
         // at a time (independent of the loss, so it overlaps thread 0's loss sum)
         float g = 0.f;
+        float th0 = 0.f, m0 = 0.f, v0 = 0.f;   // Adam state, loaded with the slots
+        const long long q = ob.param_off + p;
         if (mode != RED_LOSS && p < P) {
+            if (mode == RED_ADAM) {
+                th0 = params[q];
+                m0 = mom[q];
+                v0 = vel[q];
+            }
             const int nr = bt.n_runs;
             const float* src = part + bt.part_off + p;
-            int t = 0;
-            for (; t + 8 <= nr; t += 8) {   // eight loads in flight, added in slot order
+            for (int t = 0; t < nr; t += 8) {   // eight (predicated) loads in flight, added in slot order
                 float v[8];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) v[u] = src[(long long)(t + u) * stride];
+                for (int u = 0; u < 8; ++u) v[u] = t + u < nr ? src[(long long)(t + u) * stride] : 0.f;
 #pragma unroll
-                for (int u = 0; u < 8; ++u) g += v[u];
+                for (int u = 0; u < 8; ++u)
+                    if (t + u < nr) g += v[u];
             }
-            for (; t < nr; ++t) g += src[(long long)t * stride];
         }
         __syncthreads();   // sh_loss of the previous item has been read
         if (threadIdx.x < 32) {
             const float L = object_loss_warp(sp, ob, bt, part);
-            if (threadIdx.x == 0) sh_loss = L;
+            if (threadIdx.x == 0) {
+                sh_loss = L;
+                const int t1 = steps[k] + 1;   // Adam bias corrections with the object's step + 1
+                sh_bc1 = 1.f - powf(sp.beta1, (float)t1);
+                sh_bc2 = 1.f - powf(sp.beta2, (float)t1);
+            }
             if (threadIdx.x == 0 && item.y == 0) {
                 if (loss_out) loss_out[k] = frozen ? __int_as_float(0x7fc00000) : L;
                 if (dcenter_out) {
@@ -154,21 +197,22 @@ __global__ void __launch_bounds__(REDUCE_CHUNK) k_reduce(StepParams sp, const Ob
             atomicOr(status + k, 2);
             continue;
         }
-        const int t1 = steps[k] + 1;
-        const float bc1 = 1.f - powf(sp.beta1, (float)t1);
-        const float bc2 = 1.f - powf(sp.beta2, (float)t1);
-        const long long q = ob.param_off + p;
-        const float m = sp.beta1 * mom[q] + (1.f - sp.beta1) * g;
-        const float v = sp.beta2 * vel[q] + (1.f - sp.beta2) * g * g;
+        const float bc1 = sh_bc1, bc2 = sh_bc2;
+        const float m = sp.beta1 * m0 + (1.f - sp.beta1) * g;
+        const float v = sp.beta2 * v0 + (1.f - sp.beta2) * g * g;
         mom[q] = m;
         vel[q] = v;
-        const float th = params[q] - sp.lr * (m / bc1) / (sqrtf(v / bc2) + sp.eps);
+        const float th = th0 - sp.lr * (m / bc1) / (sqrtf(v / bc2) + sp.eps);
         params[q] = th;
-        const long long w = wt_index(H, p);
-        if (w >= 0) wt[ob.wt_off + w] = th;
-        if (img && img_off[k] >= 0) {          // BF16 tensor-core operand image
-            const long long wi = img_index(H, p);
-            if (wi >= 0) img[img_off[k] + wi] = __float2bfloat16(th);
+        int wn, wk;
+        const int l = weight_of(H, (int)p, wn, wk);
+        if (l >= 0) {
+            const int N = l == 4 ? NOUT : H;
+            wt[ob.wt_off + wt_layer_off(H, l) + (long long)wk * N + wn] = th;   // transposed shadow
+            if (img && img_off[k] >= 0) {                                        // BF16 operand image
+                const long long base = l == 0 ? 0 : (long long)H * DINP + (long long)(l - 1) * H * H;
+                img[img_off[k] + base + cm_off(wn, wk, l == 0 ? DINP : H) / 2] = __float2bfloat16(th);
+            }
         }
     }
     if (mode != RED_ADAM || !done) return;

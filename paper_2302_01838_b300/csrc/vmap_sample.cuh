@@ -34,14 +34,16 @@ constexpr int SAMPLE_RAYS_PER_BLOCK = 8;
 
 __global__ void __launch_bounds__(32 * SAMPLE_RAYS_PER_BLOCK) k_sample(
     StepParams sp, const ObjDev* __restrict__ objs, const ObjBatch* __restrict__ obs, const int* __restrict__ bobj,
-    const int* __restrict__ bray_off, const int* __restrict__ counts, const float* __restrict__ src, int given,
-    const int* __restrict__ steps, int* __restrict__ pick_out, float* __restrict__ t_out) {
+    const int* __restrict__ bray_off, const int* __restrict__ ray_bj, const int* __restrict__ counts,
+    const float* __restrict__ src, int given, const int* __restrict__ steps, int* __restrict__ pick_out,
+    float* __restrict__ t_out) {
     const int i = blockIdx.x * SAMPLE_RAYS_PER_BLOCK + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     const int total_rays = counts[BC_RAYS];
     const int nb = counts[BC_NB];
     if (i >= total_rays) return;
-    const int j = upper_index(bray_off, nb, i);
+    // the ray's batch object: from the builder's per-ray table, or by search
+    const int j = ray_bj ? ray_bj[i] : upper_index(bray_off, nb, i);
     const int k = bobj[j];
     const ObjDev& ob = objs[k];
     const ObjBatch& bt = obs[k];
