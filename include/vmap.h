@@ -200,6 +200,20 @@ vmap_status vmap_render_depth(vmap_ctx* ctx, int obj, const float* rays, long lo
 vmap_status vmap_render_scene(vmap_ctx* ctx, const float* rays, long long n, const int* objs, int m,
                               const float* box_half, int n_samples, float* depth, float* rgb, float* occ);
 
+/* Mesh of one object (section 4 evaluates object meshes obtained by querying
+ * each object inside its 3D bound): occupancy on a (res+1)^3 lattice over
+ * c_k +- box_half, then marching tetrahedra (six Kuhn tetrahedra per cube,
+ * a lattice vertex inside when its occupancy > level; the surface is closed
+ * inside the box and each triangle faces from inside to outside).
+ *   box_half: HOST [3]; 1 <= res <= 512.
+ *   tris: DEVICE [max_tris][3][3] world-space vertices, in a deterministic
+ *   order (cube index with x fastest, then tetrahedron, then triangle), or
+ *   NULL with max_tris = 0 to count only. *n_tris (HOST) receives the total,
+ *   which may exceed max_tris (then only max_tris are written).
+ * Allocates and frees its scratch; synchronises. */
+vmap_status vmap_extract_mesh(vmap_ctx* ctx, int obj, const float* box_half, int res, float level, float* tris,
+                              long long max_tris, long long* n_tris);
+
 /* Object state in canonical layout. Any DEVICE pointer may be NULL.
  * step: HOST, may be NULL (reading it synchronises). */
 vmap_status vmap_get_object_state(vmap_ctx* ctx, int obj, float* params, float* m, float* v,

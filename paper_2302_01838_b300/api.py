@@ -175,6 +175,17 @@ class VMap:
         self._check(self.lib.vmap_query_occupancy(self.h, int(obj), _ptr(pts), pts.shape[0],
                                                   _ptr(occ), _ptr(rgb)))
 
+    def extract_mesh(self, obj, box_half, res, level=0.5):
+        """Triangles [n, 3, 3] (CUDA, world space) of the object's occupancy level set."""
+        hb = np.ascontiguousarray(np.asarray(box_half, np.float32).reshape(3))
+        hp = hb.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        n = ctypes.c_longlong()
+        self._check(self.lib.vmap_extract_mesh(self.h, int(obj), hp, int(res), float(level), None, 0, ctypes.byref(n)))
+        tris = torch.empty(max(n.value, 1), 3, 3, device="cuda")
+        self._check(self.lib.vmap_extract_mesh(self.h, int(obj), hp, int(res), float(level), _ptr(tris), n.value,
+                                               ctypes.byref(n)))
+        return tris[:n.value]
+
     def render_scene(self, rays, objs, box_half, n_samples, depth, rgb=None, occ=None):
         """Occlusion-aware render of the listed objects (vmap_render_scene)."""
         objs = list(objs)

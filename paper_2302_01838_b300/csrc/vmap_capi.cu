@@ -15,6 +15,7 @@
 
 #include "../../include/vmap.h"
 #include "vmap_build.cuh"
+#include "vmap_mesh.cuh"
 #include "vmap_common.cuh"
 #include "vmap_optim.cuh"
 #include "vmap_sample.cuh"
@@ -924,6 +925,62 @@ vmap_status vmap_render_scene(vmap_ctx* ctx, const float* rays, long long n, con
     const int blocks = (int)std::min<long long>((n + 255) / 256, (long long)ctx->n_sm * 16);
     k_compose<<<blocks, 256, 0, ctx->stream>>>(ctx->scene_d, m, n, depth, rgb, occ);
     CHECK_LAUNCH("k_compose");
+    return VMAP_OK;
+}
+
+vmap_status vmap_extract_mesh(vmap_ctx* ctx, int obj, const float* box_half, int res, float level, float* tris,
+                              long long max_tris, long long* n_tris) {
+    if (vmap_status s = check_obj(ctx, obj)) return s;
+    if (!box_half || !n_tris) return fail(ctx, VMAP_ERR_ARG, "null argument");
+    if (res < 1 || res > 512) return fail(ctx, VMAP_ERR_ARG, "res must be in [1, 512]");
+    if (max_tris < 0 || (max_tris > 0 && !tris)) return fail(ctx, VMAP_ERR_ARG, "bad triangle buffer");
+    const ObjDev& ob = ctx->objs[obj];
+    const long long n1 = res + 1, nv = n1 * n1 * n1, nc = (long long)res * res * res;
+    // scratch: lattice points, occupancy, per-cube counts, offsets
+    const size_t b_pts = sizeof(float) * 3 * nv, b_occ = sizeof(float) * nv, b_cnt = sizeof(int) * nc;
+    const size_t o_occ = (b_pts + 255) & ~(size_t)255, o_cnt = (o_occ + b_occ + 255) & ~(size_t)255;
+    const size_t o_off = (o_cnt + b_cnt + 255) & ~(size_t)255, total = o_off + sizeof(long long) * (nc + 1);
+    unsigned char* scratch = nullptr;
+    CU(cudaStreamSynchronize(ctx->stream));
+    CU(cudaMalloc((void**)&scratch, total));
+    float* pts = (float*)scratch;
+    float* occ = (float*)(scratch + o_occ);
+    int* counts = (int*)(scratch + o_cnt);
+    long long* offs = (long long*)(scratch + o_off);
+    MtGrid g{};
+    g.occ = occ;
+    g.res = res;
+    g.level = level;
+    for (int a = 0; a < 3; ++a) {
+        g.o[a] = ob.c[a] - box_half[a];
+        g.s[a] = 2.f * box_half[a] / (float)res;
+    }
+    const int blocks = (int)std::min<long long>((nv + 255) / 256, (long long)ctx->n_sm * 32);
+    k_lattice_points<<<blocks, 256, 0, ctx->stream>>>(pts, res, g.o[0], g.o[1], g.o[2], g.s[0], g.s[1], g.s[2]);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        const int c = class_of(ob.hidden);
+        TileArgs ta = base_args(ctx);
+        ta.eval_obj = obj;
+        ta.eval_n = nv;
+        ta.qpts = pts;
+        ta.qocc = occ;
+        ta.qrgb = nullptr;
+        e = launch_tile_c<MODE_QUERY>(c, (int)((nv + mmax_of(c) - 1) / mmax_of(c)), ctx->stream, ctx->sp, ta);
+    }
+    const int cblocks = (int)std::min<long long>((nc + 255) / 256, (long long)ctx->n_sm * 32);
+    if (e == cudaSuccess) {
+        k_mt_count<<<cblocks, 256, 0, ctx->stream>>>(g, counts);
+        k_scan_counts<<<1, BUILD_THREADS, 0, ctx->stream>>>(counts, nc, offs);
+        if (max_tris > 0) k_mt_emit<<<cblocks, 256, 0, ctx->stream>>>(g, offs, tris, max_tris);
+        e = cudaGetLastError();
+    }
+    long long n = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&n, offs + nc, sizeof n, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(scratch);
+    if (e != cudaSuccess) return fail(ctx, VMAP_ERR_CUDA, "mesh extraction failed: %s", cudaGetErrorString(e));
+    *n_tris = n;
     return VMAP_OK;
 }
 

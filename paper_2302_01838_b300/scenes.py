@@ -87,6 +87,50 @@ def cast(prims, center, o, d):
     return best, rgb
 
 
+def union_sdf(prims, center, x):
+    """Signed distance of points x [n, 3] to a union of primitives (negative
+    inside): spheres |x - c| - r, boxes the exact box distance."""
+    x = np.asarray(x, np.float64)
+    best = np.full(x.shape[0], np.inf)
+    for p in prims:
+        q = x - (np.asarray(center, np.float64) + p["offset"])
+        if p["kind"] == "sphere":
+            d = np.linalg.norm(q, axis=1) - p["size"][0]
+        else:
+            a = np.abs(q) - p["size"]
+            d = np.linalg.norm(np.maximum(a, 0.0), axis=1) + np.minimum(np.max(a, axis=1), 0.0)
+        best = np.minimum(best, d)
+    return best
+
+
+def surface_points(rng, prims, center, n):
+    """About n points on the surface of a union of primitives: points on each
+    primitive's surface (area-proportional) that lie on the union's boundary."""
+    pts, areas = [], []
+    for p in prims:
+        areas.append(4 * np.pi * p["size"][0] ** 2 if p["kind"] == "sphere"
+                     else 8 * (p["size"][0] * p["size"][1] + p["size"][1] * p["size"][2] + p["size"][0] * p["size"][2]))
+    areas = np.array(areas) / np.sum(areas)
+    for p, w in zip(prims, areas):
+        m = max(1, int(round(3 * n * w)))
+        c = np.asarray(center, np.float64) + p["offset"]
+        if p["kind"] == "sphere":
+            v = rng.standard_normal((m, 3))
+            q = c + p["size"][0] * v / np.linalg.norm(v, axis=1, keepdims=True)
+        else:
+            h = p["size"]
+            face_area = np.array([h[1] * h[2], h[1] * h[2], h[0] * h[2], h[0] * h[2], h[0] * h[1], h[0] * h[1]])
+            f = rng.choice(6, m, p=face_area / face_area.sum())
+            u = rng.uniform(-1, 1, (m, 3)) * h
+            ax, sgn = f // 2, np.where(f % 2 == 0, 1.0, -1.0)
+            u[np.arange(m), ax] = sgn * h[ax]
+            q = c + u
+        pts.append(q)
+    q = np.concatenate(pts)
+    q = q[np.abs(union_sdf(prims, center, q)) < 1e-6]
+    return q[rng.permutation(q.shape[0])[:n]]
+
+
 def look_at(eye, target, up=np.array([0.0, 0.0, 1.0])):
     """Camera-to-world rotation for a camera with +z forward, +x right, +y down."""
     f = target - eye
