@@ -172,6 +172,16 @@ vmap_status vmap_forward(vmap_ctx* ctx, float* out_loss);
 vmap_status vmap_backward(vmap_ctx* ctx, const float* grad_loss, float* grad_params,
                           float* grad_center);
 
+/* Per-ray gradients of the current batch, the primitive of camera-pose
+ * refinement (section 4, tracking with the map fixed): for batch ray i of
+ * object k, grad_rays[i] = (dL_k/do_i, dL_k/dd_i) through x = o + t d with
+ * the drawn sample depths held fixed (the encoding backward, summed over the
+ * ray's samples). A camera at (p, R) with d = R d_c gets dL/dp = sum dL/do
+ * and, for a rotation exp([w]x) R, dL/dw = sum d x dL/dd. grad_rays: DEVICE
+ * [n_rays][6], batch order (object-major, as vmap_get_samples). No state
+ * changes. FP32 contexts only. */
+vmap_status vmap_ray_gradients(vmap_ctx* ctx, float* grad_rays);
+
 /* Occupancy (and colour) of n arbitrary world points of one object (section
  * 3.4: an object is queried inside its bound). pts DEVICE [n][3];
  * occ DEVICE [n]; rgb DEVICE [n][3] or NULL. n = 0 is a no-op. */

@@ -305,7 +305,8 @@ def encode_backward(xt, B, dgamma):
 def object_forward_backward(cfg, params, H, rays, t, center, scale, want_center_grad=False):
     """Loss and gradients of one object on one batch of rays with given t.
 
-    Returns dict(loss, Ld, Lc, Lo, grad (flat), dcenter (3,), render)."""
+    Returns dict(loss, Ld, Lc, Lo, grad (flat), render) and, with
+    want_center_grad, dcenter (3,) and the per-ray gradients dray_o, dray_d [R, 3]."""
     Ws, bs = unpack(params, H)
     R, S = t.shape
     xt = points(rays, t, center, scale)
@@ -322,6 +323,11 @@ def object_forward_backward(cfg, params, H, rays, t, center, scale, want_center_
     if want_center_grad:
         dxt = encode_backward(xt.reshape(-1, 3), cfg.B, dgamma)
         out["dcenter"] = -dxt.sum(0) / float(scale)
+        # per ray, through x = o + t d with the sample depths t held fixed:
+        # dL/do = sum_i dL/dx_i, dL/dd = sum_i t_i dL/dx_i, dL/dx = dL/dx~ / s
+        dx = dxt.reshape(R, S, 3) / float(scale)
+        out["dray_o"] = dx.sum(1)
+        out["dray_d"] = (dx * t[:, :, None]).sum(1)
     return out
 
 

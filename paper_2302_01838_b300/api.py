@@ -175,6 +175,10 @@ class VMap:
         self._check(self.lib.vmap_query_occupancy(self.h, int(obj), _ptr(pts), pts.shape[0],
                                                   _ptr(occ), _ptr(rgb)))
 
+    def ray_gradients(self, out):
+        """(dL/do, dL/dd) of every ray of the current batch into out [n_rays, 6] (CUDA)."""
+        self._check(self.lib.vmap_ray_gradients(self.h, _ptr(out)))
+
     def extract_mesh(self, obj, box_half, res, level=0.5):
         """Triangles [n, 3, 3] (CUDA, world space) of the object's occupancy level set."""
         hb = np.ascontiguousarray(np.asarray(box_half, np.float32).reshape(3))

@@ -126,6 +126,7 @@ struct vmap_ctx {
     // scene rendering: per (object, ray) records, grown on demand
     float* scene_d = nullptr;
     long long scene_cap = 0;        // floats
+    float* ray_grad_out = nullptr;  // set only while vmap_ray_gradients launches
 
     // CUDA graphs (captured on a private stream, replayed on the context stream)
     bool graph_on = false;
@@ -266,6 +267,7 @@ TileArgs base_args(vmap_ctx* ctx) {
     ta.params = ctx->params_d;
     ta.wt = ctx->wt_d;
     ta.part = ctx->part_d;
+    ta.ray_grad = ctx->ray_grad_out;
     return ta;
 }
 
@@ -840,6 +842,16 @@ vmap_status vmap_backward(vmap_ctx* ctx, const float* grad_loss, float* grad_par
     vmap_status s = grad_center ? launch_tiles<MODE_GRAD_CENTER>(ctx, mask) : launch_tiles<MODE_TRAIN>(ctx, mask);
     if (s) return s;
     return launch_reduce(ctx, RED_GRAD, grad_loss, grad_params, nullptr, grad_center);
+}
+
+vmap_status vmap_ray_gradients(vmap_ctx* ctx, float* grad_rays) {
+    if (!ctx || !grad_rays) return fail(ctx, VMAP_ERR_ARG, "null argument");
+    if (!ctx->batch_ready) return fail(ctx, VMAP_ERR_STATE, "ray gradients need a drawn batch");
+    if (ctx->bf16) return fail(ctx, VMAP_ERR_ARG, "ray gradients need an FP32 context");
+    ctx->ray_grad_out = grad_rays;
+    vmap_status s = launch_tiles<MODE_GRAD_CENTER>(ctx, class_mask(ctx));
+    ctx->ray_grad_out = nullptr;
+    return s;
 }
 
 vmap_status vmap_query_occupancy(vmap_ctx* ctx, int obj, const float* pts, long long n, float* occ, float* rgb) {

@@ -269,6 +269,7 @@ struct TileArgs {
     float* part;              // run partial slots
     float* eval_out;          // MODE_EVAL: rendered depth per ray, or NULL
     float* eval_rec;          // MODE_EVAL: [n][5] (O^, D^, C^) per ray, or NULL
+    float* ray_grad;          // MODE_GRAD_CENTER: [batch rays][6] dL/do, dL/dd per ray, or NULL
     float eval_half[3];       // MODE_EVAL: box half extents
     int eval_obj;             // MODE_EVAL / MODE_QUERY: the object
     long long eval_n;         // MODE_EVAL: rays; MODE_QUERY: points
@@ -642,6 +643,28 @@ __global__ void __launch_bounds__(NTHREADS, TileCfg<H>::CTAS) k_tile_fp32(StepPa
                 float s = 0.f;
                 for (int m = 0; m < M; ++m) s += acc3[threadIdx.x * LD + m];
                 gp[PC + 3 + threadIdx.x] += -s / sc;
+            }
+            // per ray through x = o + t d (depths fixed): dL/do = sum dL/dx, dL/dd = sum t dL/dx
+            if (ta.ray_grad) {
+                for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+                    float go[3] = {0.f, 0.f, 0.f}, gd[3] = {0.f, 0.f, 0.f};
+                    for (int i = 0; i < S; ++i) {
+                        const int m = r * S + i;
+                        const float t = tsm[m];
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            const float v = acc3[a * LD + m] / sc;
+                            go[a] += v;
+                            gd[a] = fmaf(t, v, gd[a]);
+                        }
+                    }
+                    float* out = ta.ray_grad + (long long)(ray_first + r) * 6;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        out[a] = go[a];
+                        out[3 + a] = gd[a];
+                    }
+                }
             }
         }
         __syncthreads();
