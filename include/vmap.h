@@ -310,6 +310,12 @@ vmap_status vmap_hyper_create(vmap_hyper** out, int n_points, int width, int ran
                               int max_batch, unsigned long long seed, void* cuda_stream);
 vmap_status vmap_hyper_destroy(vmap_hyper* h);
 const char* vmap_hyper_last_error(const vmap_hyper* h);
+/* GEMM precision (default VMAP_FP32). VMAP_BF16 (width 128 only): the GEMMs
+ * of the three 128-wide shared layers (forward, input and weight gradients)
+ * run on the tensor cores with BF16 operands and FP32 accumulation; the
+ * 7-input first layer, the rank-r head, biases, losses and Adam stay FP32.
+ * Synchronises when switching to VMAP_BF16 the first time. */
+vmap_status vmap_hyper_set_precision(vmap_hyper* h, int precision);
 /* HOST outputs: number of hypernetwork parameters, and P (outputs per object). */
 vmap_status vmap_hyper_param_count(vmap_hyper* h, long long* n_params, int* out_params);
 vmap_status vmap_hyper_get_params(vmap_hyper* h, float* flat);

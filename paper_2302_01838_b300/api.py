@@ -312,6 +312,10 @@ class HyperNet:
         if st != 0:
             raise VmapError(st, self.lib.vmap_hyper_last_error(self.h).decode())
 
+    def set_precision(self, precision):
+        """native.VMAP_FP32 or native.VMAP_BF16 (tensor-core GEMMs of the 128-wide layers)."""
+        self._check(self.lib.vmap_hyper_set_precision(self.h, int(precision)))
+
     def close(self):
         if getattr(self, "h", None):
             self.lib.vmap_hyper_destroy(self.h)

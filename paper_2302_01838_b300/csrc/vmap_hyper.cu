@@ -6,9 +6,13 @@
 //   per set    z = channel-wise max of h3 over the points (ties: lowest index)
 //   head       u = Wa z + ba (rank r), theta = Wb u + bb (P outputs)
 //   loss       L = sum (theta - target)^2 / (B P)
-// Every GEMM is a tiled FP32 SIMT kernel (64 x 64 tiles, 4 x 4 per thread,
-// split over K where the reduction is long); column sums and split partials
-// are added in a fixed order, so results are bitwise reproducible.
+// In FP32 mode every GEMM is a tiled FP32 SIMT kernel (64 x 64 tiles, 4 x 4
+// per thread, split over K where the reduction is long). In BF16 mode the six
+// GEMMs of the 128-wide shared layers (two forward layers, their input and
+// weight gradients) run on the tensor cores (vmap_hgemm.cuh: BF16 operands,
+// FP32 accumulation); the 7-input first layer and the rank-16 head stay FP32.
+// Column sums and split partials are added in a fixed order, so results are
+// bitwise reproducible.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -20,6 +24,7 @@
 #include <string>
 
 #include "../../include/vmap.h"
+#include "vmap_hgemm.cuh"
 
 namespace {
 
@@ -208,6 +213,10 @@ struct vmap_hyper {
     float *split = nullptr, *colpart = nullptr, *mse_part = nullptr, *loss_tmp = nullptr;
     long long *seg_bounds = nullptr;
     int* seg_fan = nullptr;
+    int bf16 = 0;                      // tensor-core GEMMs for the 128-wide layers
+    float* tc_part = nullptr;          // [n_sm][128][128] split-K partials of the tensor-core weight gradients
+    int* err_d = nullptr;              // set when a bounded MMA wait gives up
+    int n_sm = 148;
     std::string err;
 };
 
@@ -232,10 +241,61 @@ vmap_status hfail(vmap_hyper* h, vmap_status s, const char* fmt, ...) {
         if (e_ != cudaSuccess) return hfail(h, VMAP_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
 
+template <bool B_MN, int EPI>
+cudaError_t launch_hgemm_rows(vmap_hyper* h, long long M, const float* A, const float* B, const float* bias, float* C) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(vmapk::k_hgemm_rows<B_MN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)vmapk::HgemmSmem::BYTES);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    vmapk::k_hgemm_rows<B_MN, EPI><<<(unsigned)((M + 127) / 128), 128, vmapk::HgemmSmem::BYTES, h->stream>>>(
+        M, A, B, bias, C, h->err_d);
+    return cudaGetLastError();
+}
+
+// tensor-core forms: C[M][128] = A[M][128] W^T (TB) or A W (!TB), and dW[128][128] = A^T B over K rows
+template <bool TA, bool TB>
+bool tc_shape(vmap_hyper* h, int M, int N, int K, int lda, int ldb) {
+    if (!h->bf16) return false;
+    if (!TA) return N == vmapk::HG && K == vmapk::HG && lda == vmapk::HG && ldb == vmapk::HG;
+    return !TB && M == vmapk::HG && N == vmapk::HG && lda == vmapk::HG && ldb == vmapk::HG;
+}
+
+template <bool TA, bool TB>
+vmap_status gemm_tc(vmap_hyper* h, int M, int N, int K, const float* A, const float* B, float* C, const float* bias,
+                    bool relu) {
+    cudaError_t e;
+    if (!TA) {
+        if (TB) e = relu ? launch_hgemm_rows<false, 2>(h, M, A, B, bias, C)
+                        : bias ? launch_hgemm_rows<false, 1>(h, M, A, B, bias, C)
+                               : launch_hgemm_rows<false, 0>(h, M, A, B, nullptr, C);
+        else e = launch_hgemm_rows<true, 0>(h, M, A, B, nullptr, C);
+    } else {
+        static bool attr = false;
+        if (!attr) {
+            e = cudaFuncSetAttribute(vmapk::k_hgemm_tn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)vmapk::HgemmSmem::BYTES);
+            if (e != cudaSuccess) return hfail(h, VMAP_ERR_CUDA, "hgemm attribute: %s", cudaGetErrorString(e));
+            attr = true;
+        }
+        const long long per = ((long long)K + h->n_sm - 1) / h->n_sm;
+        const long long chunk = std::max<long long>(vmapk::HG, (per + vmapk::HG - 1) / vmapk::HG * vmapk::HG);
+        const int splits = (int)((K + chunk - 1) / chunk);
+        vmapk::k_hgemm_tn<<<splits, 128, vmapk::HgemmSmem::BYTES, h->stream>>>(K, chunk, A, B, h->tc_part, h->err_d);
+        k_sum_splits<<<256, 256, 0, h->stream>>>(vmapk::HG, vmapk::HG, splits, h->tc_part, C, bias);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return hfail(h, VMAP_ERR_CUDA, "tensor-core GEMM: %s", cudaGetErrorString(e));
+    return VMAP_OK;
+}
+
 // C = op(A) op(B) (+bias, ReLU); long reductions are split over K and summed in order
 template <bool TA, bool TB>
 vmap_status gemm(vmap_hyper* h, int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C,
                  const float* bias, bool relu) {
+    if (tc_shape<TA, TB>(h, M, N, K, lda, ldb)) return gemm_tc<TA, TB>(h, M, N, K, A, B, C, bias, relu);
     const dim3 blk(256);
     const int gm = (M + BM - 1) / BM, gn = (N + BN - 1) / BN;
     int splits = 1;
@@ -392,7 +452,7 @@ vmap_status vmap_hyper_destroy(vmap_hyper* h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     void* ptrs[] = {h->params, h->grad, h->m, h->v, h->h1, h->h2, h->h3, h->da, h->db, h->arg, h->z, h->u,
                     h->th, h->dth, h->du, h->dz, h->split, h->colpart, h->mse_part, h->loss_tmp, h->seg_bounds,
-                    h->seg_fan};
+                    h->seg_fan, h->tc_part, h->err_d};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete h;
@@ -400,6 +460,25 @@ vmap_status vmap_hyper_destroy(vmap_hyper* h) {
 }
 
 const char* vmap_hyper_last_error(const vmap_hyper* h) { return h ? h->err.c_str() : "null hypernetwork"; }
+
+vmap_status vmap_hyper_set_precision(vmap_hyper* h, int precision) {
+    if (!h) return VMAP_ERR_ARG;
+    if (precision != VMAP_FP32 && precision != VMAP_BF16) return hfail(h, VMAP_ERR_ARG, "unknown precision %d", precision);
+    if (precision == VMAP_BF16) {
+        if (h->W != vmapk::HG) return hfail(h, VMAP_ERR_ARG, "BF16 GEMMs need width %d", vmapk::HG);
+        HCU(cudaStreamSynchronize(h->stream));
+        if (!h->tc_part) {
+            int dev = 0;
+            HCU(cudaGetDevice(&dev));
+            HCU(cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, dev));
+            HCU(cudaMalloc((void**)&h->tc_part, sizeof(float) * (size_t)h->n_sm * vmapk::HG * vmapk::HG));
+            HCU(cudaMalloc((void**)&h->err_d, sizeof(int)));
+            HCU(cudaMemset(h->err_d, 0, sizeof(int)));
+        }
+    }
+    h->bf16 = precision == VMAP_BF16;
+    return VMAP_OK;
+}
 
 vmap_status vmap_hyper_param_count(vmap_hyper* h, long long* n, int* out_params) {
     if (!h) return VMAP_ERR_ARG;

@@ -85,6 +85,7 @@ SIGNATURES = {
     "vmap_extract_mesh": (_I, [_P, _I, ctypes.POINTER(ctypes.c_float), _I, ctypes.c_float, _P, _LL,
                                ctypes.POINTER(ctypes.c_longlong)]),
     "vmap_ray_gradients": (_I, [_P, _P]),
+    "vmap_hyper_set_precision": (_I, [_P, _I]),
     "vmap_render_scene": (_I, [_P, _P, _LL, ctypes.POINTER(ctypes.c_int), _I, ctypes.POINTER(ctypes.c_float), _I,
                                _P, _P, _P]),
     "vmap_get_object_state": (_I, [_P, _I, _P, _P, _P, _IP]),

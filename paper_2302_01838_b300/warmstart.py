@@ -65,8 +65,11 @@ def produce_dataset(n, seed, steps, chunk=1000, log=None):
     return np.concatenate(X), np.concatenate(T)
 
 
-def train_hypernet(X, T, epochs=200, batch=256, lr=1e-3, seed=0, log=None):
+def train_hypernet(X, T, epochs=200, batch=256, lr=1e-3, seed=0, log=None, precision=VMAP_BF16):
+    """The set-encoder hypernetwork trained on (set input, converged weights)
+    pairs; by default its 128-wide layers run on the tensor cores (BF16)."""
     hyp = HyperNet(n_points=X.shape[1], max_batch=batch, seed=seed)
+    hyp.set_precision(precision)
     # start the head bias at the mean target (data-dependent initialisation)
     p = hyp.get_params()
     p[-T.shape[1]:] = torch.from_numpy(T.mean(0)).cuda()

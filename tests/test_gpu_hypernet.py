@@ -67,3 +67,34 @@ def test_hypernet_training_and_warmstart():
     assert float(m.abs().max()) == 0.0 and float(v.abs().max()) == 0.0
     vm.sample_rays([120, 120]); vm.train_step()
     assert vm.get_object_state(1)[3] == 1 and vm.get_object_state(0)[3] == 2
+
+
+def test_bf16_hypernet_gradient_matches_rounding_model():
+    """BF16 mode (tensor-core GEMMs for the 128-wide layers) against the
+    oracle's BF16 rounding model (tight) and the FP64 model (BF16-level)."""
+    from paper_2302_01838_b300.api import HyperNet
+    from paper_2302_01838_b300.native import VMAP_BF16
+    B = 6
+    sc, X = _inputs(B, seed=3)
+    rng = np.random.default_rng(1)
+    hyp = HyperNet(max_batch=8, seed=5)
+    hyp.set_precision(VMAP_BF16)
+    p = rng.standard_normal(hyp.n_params).astype(np.float32) * 0.1
+    T = rng.standard_normal((B, hyp.P)).astype(np.float32) * 0.2
+    hyp.set_params(torch.from_numpy(p).cuda())
+    g, loss = hyp.grad(torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda())
+    g = g.cpu().numpy()
+    for bf16, tol in ((True, 1e-2), (False, 1e-1)):
+        th, cache = hn.forward(p.astype(np.float64), X.astype(np.float64), bf16=bf16)
+        gref = hn.backward(p.astype(np.float64), cache, th, T, bf16=bf16)
+        assert abs(loss.item() - hn.loss(th, T)) <= (1e-4 if bf16 else 1e-2) * hn.loss(th, T)
+        errs = [vh.rel_l2(a, b) for a, b in zip(hn.unpack(g), hn.unpack(gref))]
+        assert max(errs) <= tol, (bf16, errs)
+    # training in BF16 mode lowers the loss
+    Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+    out = torch.empty(1, device="cuda")
+    hyp.train_step(Xd, Td, 1e-3, out)
+    first = out.item()
+    for _ in range(100):
+        hyp.train_step(Xd, Td, 1e-3, out)
+    assert out.item() < 0.7 * first

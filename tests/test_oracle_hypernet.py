@@ -59,3 +59,24 @@ def test_max_pool_picks_the_largest_point_and_lowest_index_on_ties():
     assert list(cache["arg"][0]) == [1, 0]
     assert np.allclose(cache["z"][0], [2.0, 3.0])
     assert np.allclose(th[0], [5.0, 5.0])          # u = 2 + 3, theta = u
+
+
+def test_bf16_hypernet_model_reduces_to_fp64_and_stays_close():
+    """The hypernetwork's BF16 rounding model: bf16=False is the FP64 model
+    bitwise; bf16=True stays within BF16-level relative error of it."""
+    import numpy as np
+    from oracle import hypernet as hn
+    rng = np.random.default_rng(7)
+    B, N, P = 3, 24, 100
+    p = rng.standard_normal(hn.count(P=P)) * 0.1
+    X = rng.standard_normal((B, N, 7))
+    T = rng.standard_normal((B, P)) * 0.1
+    th0, c0 = hn.forward(p, X, P=P)
+    th1, c1 = hn.forward(p, X, P=P, bf16=False)
+    assert np.array_equal(th0, th1)
+    g0 = hn.backward(p, c0, th0, T, P=P)
+    assert np.array_equal(g0, hn.backward(p, c1, th1, T, P=P, bf16=False))
+    thb, cb = hn.forward(p, X, P=P, bf16=True)
+    gb = hn.backward(p, cb, thb, T, P=P, bf16=True)
+    assert 0 < np.linalg.norm(thb - th0) <= 2e-2 * np.linalg.norm(th0)
+    assert 0 < np.linalg.norm(gb - g0) <= 5e-2 * np.linalg.norm(g0)
