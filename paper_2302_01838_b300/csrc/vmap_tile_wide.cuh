@@ -368,16 +368,17 @@ __global__ void __launch_bounds__(WIDE_THREADS, 1) k_wide_fb(StepParams sp, Wide
     if (warp == 0) tmem_dealloc(tmem, C::NCOLS);
 }
 
-// Weight-gradient jobs: operand A (M side, 128 lanes) and B (N side) of job j
-// inside a tile's activation record, their column counts, and N.
+// Weight-gradient jobs: operand A (M side, 128 TMEM lanes = input index) and
+// B (N side = output index) of job j inside a tile's activation record, their
+// column counts, and N. Every job computes a transposed gradient
+// dW_{j+1}^T [in][out] = a_j^T dZ_{j+1} (a_0 = encoding, a_j = h_j, dZ_5 = dY),
+// so a warp's flush writes 32 consecutive inputs of one output row.
 struct WideJob {
     int a_off, a_cc, a_bytes, b_off, b_cc, b_bytes, n;
 };
 __device__ __forceinline__ WideJob wide_job(int j) {
-    // j = 0..3: dW_{j+1} [out][in] = dZ_{j+1}^T a_j   (a_0 = encoding, a_j = h_j)
-    // j = 4:    dW5^T   [in][out] = h4^T dY
-    if (j == 0) return {WideAct::dz(0), WH, TM * WH * 2, WideAct::G0, DINP, TM * DINP * 2, DINP};
-    if (j < 4) return {WideAct::dz(j), WH, TM * WH * 2, WideAct::h(j - 1), WH, TM * WH * 2, WH};
+    if (j == 0) return {WideAct::G0, DINP, TM * DINP * 2, WideAct::dz(0), WH, TM * WH * 2, WH};
+    if (j < 4) return {WideAct::h(j - 1), WH, TM * WH * 2, WideAct::dz(j), WH, TM * WH * 2, WH};
     return {WideAct::h(3), WH, TM * WH * 2, WideAct::DY, 16, TM * 16 * 2, 16};
 }
 
@@ -452,8 +453,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_wide_dw(WideArgs wa) {
     // bias partial sums: thread = (column chunk c8, row r8 within a core matrix, strip parity sp2);
     // a warp reads 512 contiguous bytes of the core-matrix tile (no bank conflicts)
     const int c8 = (tid >> 3) & 15, r8 = tid & 7, sp2 = tid >> 7;
-    const int b_cc = j < 4 ? jb.a_cc : jb.b_cc;
-    const int b_src = j < 4 ? 0 : 32768;   // operand holding dZ (A) or dY (B) in the stage
+    const int b_cc = jb.b_cc;
+    const int b_src = 32768;               // operand B holds dZ (or dY for job 4)
     const bool b_active = c8 * 8 < b_cc;
     float bs[8];
     float lacc[3] = {0.f, 0.f, 0.f};
@@ -535,18 +536,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_wide_dw(WideArgs wa) {
         }
         tc_fence_after();
         if (j < 4) {
+            // lane = input index, column = output index: W_{j+1}[out][in]
             const int fan = j == 0 ? DIN : WH;
-            float* w = gp + w_off(WH, j) + (long long)row * fan;
-            const int half = jb.n / 2;
+            float* w = gp + w_off(WH, j) + row;
 #pragma unroll 1
-            for (int c0 = 0; c0 < half; c0 += 16) {
+            for (int c0 = 0; c0 < WH / 2; c0 += 16) {
                 float v[16];
-                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + hf * half + c0, v);
+                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + hf * (WH / 2) + c0, v);
                 tmem_ld_wait();
+                if (row < fan) {
 #pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    const int in = hf * half + c0 + u;
-                    if (in < fan) w[in] = v[u];
+                    for (int u = 0; u < 16; ++u) w[(long long)(hf * (WH / 2) + c0 + u) * fan] = v[u];
                 }
             }
         } else {
