@@ -127,6 +127,9 @@ struct vmap_ctx {
     float* scene_d = nullptr;
     long long scene_cap = 0;        // floats
     float* ray_grad_out = nullptr;  // set only while vmap_ray_gradients launches
+    // BF16 training does not keep the FP32 transposed shadow current (only the
+    // FP32 eval/query kernels read it there); it is rebuilt before they run
+    bool shadow_stale = false;
 
     // CUDA graphs (captured on a private stream, replayed on the context stream)
     bool graph_on = false;
@@ -438,7 +441,7 @@ vmap_status launch_reduce(vmap_ctx* ctx, int mode, const float* grad_loss, float
                           float* dcenter_out) {
     const int pi = prof_begin(ctx, PS_REDUCE);
     k_reduce<<<ctx->n_sm * 16, REDUCE_CHUNK, 0, ctx->stream>>>(ctx->sp, ctx->objs_d, ctx->ob_d, ctx->bobj_d, ctx->items_d,
-                                                     ctx->counts_d, ctx->part_d, ctx->params_d, ctx->wt_d,
+                                                     ctx->counts_d, ctx->part_d, ctx->params_d, ctx->bf16 ? nullptr : ctx->wt_d,
                                                      ctx->m_d, ctx->v_d, ctx->steps_d, ctx->status_d, mode,
                                                      grad_loss, grad_out, loss_out, dcenter_out,
                                                      ctx->bf16 ? ctx->img_d : nullptr, ctx->img_off_d,
@@ -555,6 +558,15 @@ vmap_status sample_impl(vmap_ctx* ctx, const int* rays_per_object, const float* 
     ctx->total_rays = (int)rays;          // upper bounds until read back (frozen objects drop out)
     ctx->total_samples = samples;
     ctx->batch_ready = true;
+    return VMAP_OK;
+}
+
+// the FP32 kernels (eval, query) read the transposed shadow: refresh it after BF16 training
+vmap_status fresh_shadow(vmap_ctx* ctx) {
+    if (!ctx->shadow_stale || ctx->objs.empty()) return VMAP_OK;
+    k_shadow_all<<<dim3(16, (unsigned)ctx->objs.size()), 256, 0, ctx->stream>>>(ctx->objs_d, ctx->params_d, ctx->wt_d);
+    CHECK_LAUNCH("k_shadow_all");
+    ctx->shadow_stale = false;
     return VMAP_OK;
 }
 
@@ -809,6 +821,8 @@ vmap_status vmap_train_step(vmap_ctx* ctx, float* out_loss) {
     } else {
         if (vmap_status s = launch_train(ctx, mask)) return s;
     }
+    // BF16 steps (eager or replayed) leave the FP32 shadow behind the weights
+    if (ctx->bf16) ctx->shadow_stale = true;
     if (out_loss)
         CU(cudaMemcpyAsync(out_loss, ctx->loss_d, sizeof(float) * ctx->objs.size(), cudaMemcpyDeviceToDevice,
                            ctx->stream));
@@ -856,6 +870,7 @@ vmap_status vmap_ray_gradients(vmap_ctx* ctx, float* grad_rays) {
 
 vmap_status vmap_query_occupancy(vmap_ctx* ctx, int obj, const float* pts, long long n, float* occ, float* rgb) {
     if (vmap_status s = check_obj(ctx, obj)) return s;
+    if (vmap_status s = fresh_shadow(ctx)) return s;
     if (n < 0) return fail(ctx, VMAP_ERR_ARG, "negative point count");
     if (n == 0) return VMAP_OK;
     if (!pts || !occ) return fail(ctx, VMAP_ERR_ARG, "null argument");
@@ -876,6 +891,7 @@ vmap_status vmap_query_occupancy(vmap_ctx* ctx, int obj, const float* pts, long 
 vmap_status vmap_render_depth(vmap_ctx* ctx, int obj, const float* rays, long long n, const float* box_half,
                               int n_samples, float* depth) {
     if (vmap_status s = check_obj(ctx, obj)) return s;
+    if (vmap_status s = fresh_shadow(ctx)) return s;
     if (!rays || !box_half || !depth) return fail(ctx, VMAP_ERR_ARG, "null argument");
     if (n < 0) return fail(ctx, VMAP_ERR_ARG, "negative ray count");
     const int c = class_of(ctx->objs[obj].hidden);
@@ -909,6 +925,7 @@ vmap_status vmap_render_scene(vmap_ctx* ctx, const float* rays, long long n, con
             return fail(ctx, VMAP_ERR_ARG, "n_samples must be in [1, %d] for hidden %d", mmax_of(c), hidden_of(c));
     }
     if (n == 0) return VMAP_OK;
+    if (vmap_status s = fresh_shadow(ctx)) return s;
     const long long need = (long long)m * n * 5;
     if (need > ctx->scene_cap) {
         CU(cudaStreamSynchronize(ctx->stream));
@@ -946,6 +963,7 @@ vmap_status vmap_extract_mesh(vmap_ctx* ctx, int obj, const float* box_half, int
     if (!box_half || !n_tris) return fail(ctx, VMAP_ERR_ARG, "null argument");
     if (res < 1 || res > 512) return fail(ctx, VMAP_ERR_ARG, "res must be in [1, 512]");
     if (max_tris < 0 || (max_tris > 0 && !tris)) return fail(ctx, VMAP_ERR_ARG, "bad triangle buffer");
+    if (vmap_status s = fresh_shadow(ctx)) return s;
     const ObjDev& ob = ctx->objs[obj];
     const long long n1 = res + 1, nv = n1 * n1 * n1, nc = (long long)res * res * res;
     // scratch: lattice points, occupancy, per-cube counts, offsets

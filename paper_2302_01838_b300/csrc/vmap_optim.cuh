@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(REDUCE_CHUNK) k_reduce(StepParams sp, const Ob
         const int l = weight_of(H, (int)p, wn, wk);
         if (l >= 0) {
             const int N = l == 4 ? NOUT : H;
-            wt[ob.wt_off + wt_layer_off(H, l) + (long long)wk * N + wn] = th;   // transposed shadow
+            if (wt) wt[ob.wt_off + wt_layer_off(H, l) + (long long)wk * N + wn] = th;   // transposed shadow
             if (img && img_off[k] >= 0) {                                        // BF16 operand image
                 const long long base = l == 0 ? 0 : (long long)H * DINP + (long long)(l - 1) * H * H;
                 img[img_off[k] + base + cm_off(wn, wk, l == 0 ? DINP : H) / 2] = __float2bfloat16(th);
@@ -251,6 +251,21 @@ __global__ void k_init_params(float* params, int H, unsigned stream, uint32_t ke
             params[p] = (2.f * word_to_unit(ww[l]) - 1.f) / sqrtf((float)fan_in);
         }
     }
+}
+
+// rebuild the transposed shadows of objects 0..n-1 (blockIdx.y = object)
+__global__ void k_shadow_all(const ObjDev* __restrict__ objs, const float* __restrict__ params, float* wt) {
+    const ObjDev& ob = objs[blockIdx.y];
+    const int H = ob.hidden;
+    const long long P = param_count(H);
+    const float* p = params + ob.param_off;
+    float* w = wt + ob.wt_off;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P; i += (long long)gridDim.x * blockDim.x) {
+        int n, k;
+        const int l = weight_of(H, (int)i, n, k);
+        if (l >= 0) w[wt_layer_off(H, l) + (long long)k * (l == 4 ? NOUT : H) + n] = p[i];
+    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 3 * H; i += gridDim.x * blockDim.x) w[DIN * H + i] = 0.f;
 }
 
 // rebuild the transposed shadow of one object from its canonical parameters

@@ -187,3 +187,29 @@ def test_bf16_checkpoint_resume_refreshes_the_operand_images():
         a.sample_rays([64, 64]); a.train_step(la)
         b.sample_rays([64, 64]); b.train_step(lb)
         assert torch.equal(la, lb)
+
+
+def test_bf16_training_then_queries_see_the_current_weights():
+    """BF16 steps update the master weights; the FP32 query and depth-render
+    kernels must evaluate exactly those weights afterwards."""
+    sc = _wide_scene(47, n_small=2, bg_rays=64)
+    cfg = vh.oracle_config(sc)
+    R = [o["rays"] for o in sc["objects"]]
+    vm = vh.library_context(sc, precision=VMAP_BF16)
+    vm.set_graph(True)                       # replayed steps too
+    rng = np.random.default_rng(0)
+    for rep in range(2):
+        for _ in range(5):
+            vm.sample_rays(R)
+            vm.train_step()
+        _check_queries(vm, sc, cfg, rng)
+
+
+def _check_queries(vm, sc, cfg, rng):
+    for k, o in enumerate(sc["objects"]):
+        p = vm.get_object_state(k)[0].cpu().numpy().astype(np.float64)
+        pts = (np.asarray(o["center"], np.float64) + rng.uniform(-0.3, 0.3, (200, 3))).astype(np.float32)
+        occ = torch.empty(200, device="cuda")
+        vm.query_occupancy(k, torch.from_numpy(pts).cuda(), occ)
+        ref, _ = vs.query(cfg, p, o["H"], np.asarray(o["center"], np.float64), float(o["scale"]), pts)
+        assert np.max(np.abs(occ.cpu().numpy() - ref)) <= 1e-5, k
