@@ -142,6 +142,7 @@ __global__ void __launch_bounds__(WIDE_THREADS, 1) k_wide_fb(StepParams sp, Wide
     auto wait_mma = [&]() {
         const bool ok = mbar_wait(mbar, phase, MMA_WAIT_LIMIT);
         phase ^= 1;
+        if (tid == 0) bulk_wait_read();   // operand tiles may be rewritten after the barrier
         if (__syncthreads_or(!ok)) {
             abort = true;
             if (tid == 0) atomicExch(wa.err, 1);
@@ -154,6 +155,13 @@ __global__ void __launch_bounds__(WIDE_THREADS, 1) k_wide_fb(StepParams sp, Wide
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
+    };
+    // the activation record receives an operand tile by one bulk copy (after sync_for_mma)
+    auto record = [&](unsigned char* dst, const unsigned char* tile, int bytes) {
+        if (tid == 0) {
+            bulk_store(dst, tile, (uint32_t)bytes);
+            bulk_commit();
+        }
     };
     // this thread's 32 accumulator columns
     auto load_acc = [&](float (&v)[32]) {
@@ -182,6 +190,7 @@ __global__ void __launch_bounds__(WIDE_THREADS, 1) k_wide_fb(StepParams sp, Wide
         const float* P = ta.params + ob.param_off;
         const float cx = ob.c[0], cy = ob.c[1], cz = ob.c[2], sc = ob.scale;
         unsigned char* at = GRAD ? act + (long long)tl * WideAct::BYTES : nullptr;
+        if (tid == 0) bulk_wait_read();   // the previous tile's last records have left shared memory
 
         if (first && tid == 0) {
             // the weight image arrives by bulk copy while the tile is encoded
@@ -214,9 +223,10 @@ __global__ void __launch_bounds__(WIDE_THREADS, 1) k_wide_fb(StepParams sp, Wide
         // ---- encoding -> G0 (and the activation record); two threads per sample --
         for (int f = tid; f < 2 * TM; f += blockDim.x) {
             const int m = f % TM;
-            encode_row_half(sp, xt[m], xt[TM + m], xt[2 * TM + m], m, f / TM, G0, GRAD ? at + WideAct::G0 : nullptr);
+            encode_row_half(sp, xt[m], xt[TM + m], xt[2 * TM + m], m, f / TM, G0, nullptr);
         }
         sync_for_mma();
+        if (GRAD) record(at + WideAct::G0, G0, TM * DINP * 2);
         if (first) {
             const bool ok = mbar_wait(wbar, wphase, MMA_WAIT_LIMIT);
             if (__syncthreads_or(!ok)) {
@@ -257,12 +267,11 @@ __global__ void __launch_bounds__(WIDE_THREADS, 1) k_wide_fb(StepParams sp, Wide
 #pragma unroll
                 for (int j = 0; j < 8; ++j) u[j] = fmaxf(v[8 * c + j] + bv[8 * c + j], 0.f);
                 bits |= (unsigned)pos_bits(u, 8 * c);
-                const int off = cm_off(row, col0 + 8 * c, WH);
-                st_bf16x8(HA, off, u);
-                if (GRAD) *reinterpret_cast<uint4*>(at + WideAct::h(l) + off) = *reinterpret_cast<const uint4*>(HA + off);
+                st_bf16x8(HA, cm_off(row, col0 + 8 * c, WH), u);
             }
             mask[(l * TM + row) * 4 + qc] = bits;
             sync_for_mma();
+            if (GRAD) record(at + WideAct::h(l), HA, TM * WH * 2);
             if (tid == 0) {
                 if (l < 3) {
 #pragma unroll
@@ -319,11 +328,10 @@ __global__ void __launch_bounds__(WIDE_THREADS, 1) k_wide_fb(StepParams sp, Wide
             float v[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) v[j] = (half == 0 && j < NOUT) ? yb[j * TM + r] : 0.f;
-            const int off = cm_off(r, half * 8, 16);
-            st_bf16x8(DYt, off, v);
-            *reinterpret_cast<uint4*>(at + WideAct::DY + off) = *reinterpret_cast<const uint4*>(DYt + off);
+            st_bf16x8(DYt, cm_off(r, half * 8, 16), v);
         }
         sync_for_mma();
+        record(at + WideAct::DY, DYt, TM * 16 * 2);
 
         // ---- backward: input gradients ------------------------------------------
         if (tid == 0) {
@@ -343,11 +351,10 @@ __global__ void __launch_bounds__(WIDE_THREADS, 1) k_wide_fb(StepParams sp, Wide
                 float u[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) u[j] = (bits >> (8 * c + j)) & 1u ? v[8 * c + j] : 0.f;
-                const int off = cm_off(row, col0 + 8 * c, WH);
-                st_bf16x8(DZ, off, u);
-                *reinterpret_cast<uint4*>(at + WideAct::dz(l) + off) = *reinterpret_cast<const uint4*>(DZ + off);
+                st_bf16x8(DZ, cm_off(row, col0 + 8 * c, WH), u);
             }
             sync_for_mma();
+            record(at + WideAct::dz(l), DZ, TM * WH * 2);
             if (l == 0) break;
             if (tid == 0) {
 #pragma unroll
@@ -363,6 +370,7 @@ __global__ void __launch_bounds__(WIDE_THREADS, 1) k_wide_fb(StepParams sp, Wide
         tc_fence_after();
     }
     if (abort && wpend) mbar_wait(wbar, wphase, MMA_WAIT_LIMIT);
+    if (tid == 0) bulk_wait_all();   // every activation record is written before the CTA exits
     tc_fence_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, C::NCOLS);
