@@ -443,23 +443,29 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
         }
 
         // ---- backward -------------------------------------------------------------
-        // layer 5: dZ4 = (dY W5) * [h4 > 0] ; dW5^T += HA[3]^T dY
-        // The input-gradient MMA is committed alone: the weight-gradient MMAs
-        // issued after it run while the epilogue works, and the next commit
-        // (which tracks every earlier MMA) covers them.
-        if (tid == 0) {
-            mma_bf16(tmem + C::C_DX, desc_kmajor(DYt, 16, 0), desc_mnmajor(W5, H, 0), idesc_bf16(TM, H, 0, 1), false);
+        // The input-gradient chain dZ4 -> dZ3 -> dZ2 -> dZ1 is the critical path:
+        // each round commits its input-gradient MMA alone and then issues the
+        // previous layer's weight-gradient MMAs behind it, so those run during
+        // the next epilogue instead of delaying the next commit. Buffers:
+        // dZ4 -> DZ[0], dZ3 -> DZ[1], dZ2 -> HA[3] (h4 is dead once dW5 has run),
+        // dZ1 -> DZ[0] (dZ4 is dead once dW4 has run); a commit tracks every
+        // earlier MMA, so each rewritten buffer's last reader has finished.
+        auto issue_dx = [&](const unsigned char* z, int zcc, const unsigned char* w) {
+#pragma unroll
+            for (int kc = 0; kc < H / 16; ++kc)
+                mma_bf16(tmem + C::C_DX, desc_kmajor(z, zcc, 16 * kc), desc_mnmajor(w, H, 16 * kc),
+                         idesc_bf16(TM, H, 0, 1), kc > 0);
             mma_commit(mbar);
+        };
+        // dW^T [fan-in lanes][n] += a^T z over the tile's samples
+        auto issue_dw = [&](int col, const unsigned char* a, int acc, const unsigned char* z, int zcc, int n) {
 #pragma unroll
             for (int kc = 0; kc < TM / 16; ++kc)
-                mma_bf16(tmem + C::C_DW5, desc_mnmajor(HA[3], CH, 16 * kc), desc_mnmajor(DYt, 16, 16 * kc),
-                         idesc_bf16(TM, 16, 1, 1), !first || kc > 0);
-        }
-        wait_mma();
-        if (abort) break;
-        int cur = 0;
-        // dX epilogue of layer lp (activation mask from HA[lp - 1]) into DZ[cur]
-        auto dx_epilogue = [&](int src_ha, unsigned char* dst) {
+                mma_bf16(tmem + col, desc_mnmajor(a, acc, 16 * kc), desc_mnmajor(z, zcc, 16 * kc),
+                         idesc_bf16(TM, n, 1, 1), !first || kc > 0);
+        };
+        // dZ_l = acc * [h_l > 0] (h_l in HA[l - 1]) -> dst with zcc columns
+        auto dx_epilogue = [&](int src_ha, unsigned char* dst, int zcc) {
             float v[NC];
             tmem_ld_cols<NC>(tmem + ((uint32_t)(q * 32) << 16) + C::C_DX + hf * NC, v);
 #pragma unroll
@@ -468,39 +474,45 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
                 ld_bf16x8(HA[src_ha], cm_off(row, hf * NC + c0, CH), a);
 #pragma unroll
                 for (int j = 0; j < 8; ++j) u[j] = a[j] > 0.f ? v[c0 + j] : 0.f;
-                st_bf16x8(dst, cm_off(row, hf * NC + c0, H), u);
+                st_bf16x8(dst, cm_off(row, hf * NC + c0, zcc), u);
             }
         };
-        dx_epilogue(3, DZ[cur]);
-        sync_for_mma();
-#pragma unroll 1
-        for (int l = 3; l >= 1; --l) {
-            // dZ_l = (dZ_{l+1} W_{l+1}) * [h_l > 0] ; dW_{l+1}^T += HA[l-1]^T dZ_{l+1}
-            // (DZ[cur] is next written two rounds later, after a commit that covers these MMAs)
-            if (tid == 0) {
-#pragma unroll
-                for (int kc = 0; kc < H / 16; ++kc)
-                    mma_bf16(tmem + C::C_DX, desc_kmajor(DZ[cur], H, 16 * kc), desc_mnmajor(Wh[l - 1], H, 16 * kc),
-                             idesc_bf16(TM, H, 0, 1), kc > 0);
-                mma_commit(mbar);
-#pragma unroll
-                for (int kc = 0; kc < TM / 16; ++kc)
-                    mma_bf16(tmem + C::C_DW1 + l * H, desc_mnmajor(HA[l - 1], CH, 16 * kc),
-                             desc_mnmajor(DZ[cur], H, 16 * kc), idesc_bf16(TM, H, 1, 1), !first || kc > 0);
-            }
-            wait_mma();
-            if (abort) break;
-            dx_epilogue(l - 1, DZ[cur ^ 1]);
-            cur ^= 1;
-            sync_for_mma();
-        }
-        if (abort) break;
-        // layer 1: dW1^T += G0^T dZ1
+        // layer 5: dY W5
         if (tid == 0) {
-#pragma unroll
-            for (int kc = 0; kc < TM / 16; ++kc)
-                mma_bf16(tmem + C::C_DW1, desc_mnmajor(G0, DINP, 16 * kc), desc_mnmajor(DZ[cur], H, 16 * kc),
-                         idesc_bf16(TM, H, 1, 1), !first || kc > 0);
+            mma_bf16(tmem + C::C_DX, desc_kmajor(DYt, 16, 0), desc_mnmajor(W5, H, 0), idesc_bf16(TM, H, 0, 1), false);
+            mma_commit(mbar);
+        }
+        wait_mma();
+        if (abort) break;
+        dx_epilogue(3, DZ[0], H);                                   // dZ4
+        sync_for_mma();
+        if (tid == 0) {
+            issue_dx(DZ[0], H, Wh[2]);                              // dZ4 W4
+            issue_dw(C::C_DW5, HA[3], CH, DYt, 16, 16);             // dW5^T += h4^T dY
+        }
+        wait_mma();
+        if (abort) break;
+        dx_epilogue(2, DZ[1], H);                                   // dZ3
+        sync_for_mma();
+        if (tid == 0) {
+            issue_dx(DZ[1], H, Wh[1]);                              // dZ3 W3
+            issue_dw(C::C_DW1 + 3 * H, HA[2], CH, DZ[0], H, H);     // dW4^T += h3^T dZ4
+        }
+        wait_mma();
+        if (abort) break;
+        dx_epilogue(1, HA[3], CH);                                  // dZ2
+        sync_for_mma();
+        if (tid == 0) {
+            issue_dx(HA[3], CH, Wh[0]);                             // dZ2 W2
+            issue_dw(C::C_DW1 + 2 * H, HA[1], CH, DZ[1], H, H);     // dW3^T += h2^T dZ3
+        }
+        wait_mma();
+        if (abort) break;
+        dx_epilogue(0, DZ[0], H);                                   // dZ1
+        sync_for_mma();
+        if (tid == 0) {
+            issue_dw(C::C_DW1 + H, HA[0], CH, HA[3], CH, H);        // dW2^T += h1^T dZ2
+            issue_dw(C::C_DW1, G0, DINP, DZ[0], H, H);              // dW1^T += enc^T dZ1
             mma_commit(mbar);
         }
         wait_mma();
