@@ -13,7 +13,7 @@ namespace vmapk {
 
 constexpr int NCLASS = 4;                  // hidden widths 16, 32, 64, 128
 constexpr int BUILD_THREADS = 1024;
-constexpr int REDUCE_CHUNK = 256;          // parameters per reduce work item (one per thread)
+constexpr int REDUCE_CHUNK = 256;          // parameters per reduce work item (half an item per warp)
 
 __host__ __device__ inline int class_of(int H) { return H == 16 ? 0 : H == 32 ? 1 : H == 64 ? 2 : 3; }
 __host__ __device__ inline int hidden_of(int c) { return 16 << c; }

@@ -440,7 +440,7 @@ vmap_status launch_tiles(vmap_ctx* ctx, int mask) {
 vmap_status launch_reduce(vmap_ctx* ctx, int mode, const float* grad_loss, float* grad_out, float* loss_out,
                           float* dcenter_out) {
     const int pi = prof_begin(ctx, PS_REDUCE);
-    k_reduce<<<ctx->n_sm * 16, REDUCE_CHUNK, 0, ctx->stream>>>(ctx->sp, ctx->objs_d, ctx->ob_d, ctx->bobj_d, ctx->items_d,
+    k_reduce<<<ctx->n_sm * 3, REDUCE_THREADS, 0, ctx->stream>>>(ctx->sp, ctx->objs_d, ctx->ob_d, ctx->bobj_d, ctx->items_d,
                                                      ctx->counts_d, ctx->part_d, ctx->params_d, ctx->bf16 ? nullptr : ctx->wt_d,
                                                      ctx->m_d, ctx->v_d, ctx->steps_d, ctx->status_d, mode,
                                                      grad_loss, grad_out, loss_out, dcenter_out,

@@ -83,135 +83,148 @@ __device__ __forceinline__ long long wt_index(int H, long long p) {
 // Loss of an object from its run slots' sums (Eq. 4-5 as means). Called by
 // a whole warp: lane l sums slots l, l + 32, ... in order, then a fixed
 // butterfly combines the lanes (deterministic).
-__device__ __forceinline__ float object_loss_warp(const StepParams& sp, const ObjDev& ob, const ObjBatch& bt,
-                                                  const float* __restrict__ part) {
-    const long long P = param_count(ob.hidden);
-    const long long stride = P + NEXTRA;
-    const float* e = part + bt.part_off + P;
-    const int lane = threadIdx.x & 31;
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-    for (int t = lane; t < bt.n_runs; t += 32) {
-        s0 += e[(long long)t * stride]; s1 += e[(long long)t * stride + 1]; s2 += e[(long long)t * stride + 2];
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-    }
-    const float R = (float)bt.R;
-    return s0 / R + sp.lam_c * (s1 / (3.f * R)) + sp.lam_o * (s2 / R);
-}
-
-// Fixed grid; each block takes reduce work items (batch object, chunk of
-// REDUCE_CHUNK parameters, one per thread) from the builder's list. Sums the
-// object's run slots in slot order, then (RED_ADAM) applies Adam with the
+// Fixed grid of REDUCE_THREADS-thread blocks; each warp takes half of a
+// reduce work item (batch object, chunk of REDUCE_CHUNK parameters) from the
+// builder's list: 128 parameters, four consecutive ones per lane, moved as
+// 16-byte vectors (parameter offsets, slot strides and every width's
+// parameter count are multiples of four). It sums the object's run slots in
+// slot order and, in the same warp, the object's loss terms (lane-strided
+// over runs, then a butterfly); then (RED_ADAM) applies Adam with the
 // object's step count + 1, or (RED_GRAD) writes grad_loss[k] * g. With
 // RED_ADAM and a `done` counter, the last block to finish advances the step
 // count of every object that was trained and resets the counter.
-__global__ void __launch_bounds__(REDUCE_CHUNK) k_reduce(StepParams sp, const ObjDev* __restrict__ objs,
-                                                         const ObjBatch* __restrict__ obs,
-                                                         const int* __restrict__ bobj,
-                                                         const int2* __restrict__ items,
-                                                         const int* __restrict__ counts,
-                                                         const float* __restrict__ part, float* params,
-                                                         float* wt, float* mom, float* vel,
-                                                         int* steps, int* status,
-                                                         int mode, const float* __restrict__ grad_loss,
-                                                         float* __restrict__ grad_out,
-                                                         float* __restrict__ loss_out,
-                                                         float* __restrict__ dcenter_out,
-                                                         __nv_bfloat16* img, const long long* __restrict__ img_off,
-                                                         int* done) {
-    __shared__ float sh_loss, sh_bc1, sh_bc2;
+constexpr int REDUCE_THREADS = 256;
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ float& at4(float4& v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
+
+__global__ void __launch_bounds__(REDUCE_THREADS, 3) k_reduce(StepParams sp, const ObjDev* __restrict__ objs,
+                                                           const ObjBatch* __restrict__ obs,
+                                                           const int* __restrict__ bobj,
+                                                           const int2* __restrict__ items,
+                                                           const int* __restrict__ counts,
+                                                           const float* __restrict__ part, float* params,
+                                                           float* wt, float* mom, float* vel,
+                                                           int* steps, int* status,
+                                                           int mode, const float* __restrict__ grad_loss,
+                                                           float* __restrict__ grad_out,
+                                                           float* __restrict__ loss_out,
+                                                           float* __restrict__ dcenter_out,
+                                                           __nv_bfloat16* img, const long long* __restrict__ img_off,
+                                                           int* done) {
     __shared__ int sh_last;
-    const int n_items = counts[BC_ITEMS];
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    const int n_units = 2 * counts[BC_ITEMS];   // (item, half)
 #pragma unroll 1
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-        const int2 item = items[it];
+    for (int u = blockIdx.x * wpb + (threadIdx.x >> 5); u < n_units; u += gridDim.x * wpb) {
+        const int2 item = items[u >> 1];
+        const bool head = item.y == 0 && (u & 1) == 0;   // the warp that reports per-object results
         const int k = bobj[item.x];
         const ObjDev& ob = objs[k];
         const ObjBatch& bt = obs[k];
         const int H = ob.hidden;
-        const long long P = param_count(H);
+        const int P = (int)param_count(H);
         const long long stride = P + NEXTRA;
+        const int nr = bt.n_runs;
+        const float* e = part + bt.part_off + P;   // run t's loss sums at e[t * stride + 0..2]
+        // loss terms of the first 32 runs, in flight with the gradient loads below
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+        if (lane < nr) {
+            const float* el = e + (long long)lane * stride;
+            s0 = el[0]; s1 = el[1]; s2 = el[2];
+        }
+        const int t1 = mode == RED_ADAM ? steps[k] + 1 : 1;
         const bool frozen = status[k] != 0;
-        const float gl = grad_loss ? grad_loss[k] : 1.f;
-        const long long p = (long long)item.y * REDUCE_CHUNK + threadIdx.x;
-        // this thread's gradient: slots summed in slot order, loads issued eight
-        // at a time (independent of the loss, so it overlaps thread 0's loss sum)
-        float g = 0.f;
-        float th0 = 0.f, m0 = 0.f, v0 = 0.f;   // Adam state, loaded with the slots
+        const int p = item.y * REDUCE_CHUNK + (u & 1) * (REDUCE_CHUNK / 2) + 4 * lane;
+        const bool act = mode != RED_LOSS && p < P;
         const long long q = ob.param_off + p;
-        if (mode != RED_LOSS && p < P) {
+        float4 g = make_float4(0.f, 0.f, 0.f, 0.f), th0 = g, m0 = g, v0 = g;
+        if (act) {
             if (mode == RED_ADAM) {
-                th0 = params[q];
-                m0 = mom[q];
-                v0 = vel[q];
+                th0 = ld4(params + q);
+                m0 = ld4(mom + q);
+                v0 = ld4(vel + q);
             }
-            const int nr = bt.n_runs;
             const float* src = part + bt.part_off + p;
-            for (int t = 0; t < nr; t += 8) {   // eight (predicated) loads in flight, added in slot order
-                float v[8];
+            for (int t = 0; t < nr; t += 4) {   // four (predicated) slot loads in flight, added in slot order
+                float4 v[4];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) v[u] = t + u < nr ? src[(long long)(t + u) * stride] : 0.f;
+                for (int w = 0; w < 4; ++w) v[w] = t + w < nr ? ld4(src + (long long)(t + w) * stride) : g;
 #pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    if (t + u < nr) g += v[u];
-            }
-        }
-        __syncthreads();   // sh_loss of the previous item has been read
-        if (threadIdx.x < 32) {
-            const float L = object_loss_warp(sp, ob, bt, part);
-            if (threadIdx.x == 0) {
-                sh_loss = L;
-                const int t1 = steps[k] + 1;   // Adam bias corrections with the object's step + 1
-                sh_bc1 = 1.f - powf(sp.beta1, (float)t1);
-                sh_bc2 = 1.f - powf(sp.beta2, (float)t1);
-            }
-            if (threadIdx.x == 0 && item.y == 0) {
-                if (loss_out) loss_out[k] = frozen ? __int_as_float(0x7fc00000) : L;
-                if (dcenter_out) {
-                    float d[3] = {0.f, 0.f, 0.f};
-                    for (int t = 0; t < bt.n_runs; ++t) {
-                        const float* e = part + bt.part_off + (long long)t * stride + P;
-                        d[0] += e[3]; d[1] += e[4]; d[2] += e[5];
+                for (int w = 0; w < 4; ++w)
+                    if (t + w < nr) {
+                        g.x += v[w].x; g.y += v[w].y; g.z += v[w].z; g.w += v[w].w;
                     }
-                    for (int a = 0; a < 3; ++a) dcenter_out[3 * k + a] = gl * d[a];
-                }
             }
         }
-        __syncthreads();
-        const float L = sh_loss;
+        for (int t = 32 + lane; t < nr; t += 32) {
+            const float* el = e + (long long)t * stride;
+            s0 += el[0]; s1 += el[1]; s2 += el[2];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        }
+        const float R = (float)bt.R;
+        const float L = s0 / R + sp.lam_c * (s1 / (3.f * R)) + sp.lam_o * (s2 / R);
+        const float gl = grad_loss ? grad_loss[k] : 1.f;
+        if (head && lane == 0) {
+            if (loss_out) loss_out[k] = frozen ? __int_as_float(0x7fc00000) : L;
+            if (dcenter_out) {
+                float d[3] = {0.f, 0.f, 0.f};
+                for (int t = 0; t < nr; ++t) {
+                    const float* x = e + (long long)t * stride;
+                    d[0] += x[3]; d[1] += x[4]; d[2] += x[5];
+                }
+                for (int c = 0; c < 3; ++c) dcenter_out[3 * k + c] = gl * d[c];
+            }
+        }
         if (mode == RED_LOSS) continue;
         if (mode == RED_ADAM && (frozen || !isfinite(L))) {
-            if (!frozen && item.y == 0 && threadIdx.x == 0) status[k] = 1;
+            if (!frozen && head && lane == 0) status[k] = 1;
             continue;
         }
-        if (p >= P) continue;
+        if (!act) continue;
         if (mode == RED_GRAD) {
-            grad_out[ob.param_off + p] = gl * g;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) grad_out[q + i] = gl * at4(g, i);
             continue;
         }
-        if (!isfinite(g)) {            // leave the element, flag the object
-            atomicOr(status + k, 2);
-            continue;
+        const float bc1 = 1.f - powf(sp.beta1, (float)t1);   // Adam bias corrections
+        const float bc2 = 1.f - powf(sp.beta2, (float)t1);
+        float4 m = m0, v = v0, th = th0;
+        bool bad = false;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float gi = at4(g, i);
+            if (!isfinite(gi)) {       // leave the element, flag the object
+                bad = true;
+                continue;
+            }
+            const float mi = sp.beta1 * at4(m0, i) + (1.f - sp.beta1) * gi;
+            const float vi = sp.beta2 * at4(v0, i) + (1.f - sp.beta2) * gi * gi;
+            at4(m, i) = mi;
+            at4(v, i) = vi;
+            at4(th, i) = at4(th0, i) - sp.lr * (mi / bc1) / (sqrtf(vi / bc2) + sp.eps);
         }
-        const float bc1 = sh_bc1, bc2 = sh_bc2;
-        const float m = sp.beta1 * m0 + (1.f - sp.beta1) * g;
-        const float v = sp.beta2 * v0 + (1.f - sp.beta2) * g * g;
-        mom[q] = m;
-        vel[q] = v;
-        const float th = th0 - sp.lr * (m / bc1) / (sqrtf(v / bc2) + sp.eps);
-        params[q] = th;
-        int wn, wk;
-        const int l = weight_of(H, (int)p, wn, wk);
-        if (l >= 0) {
+        if (bad) atomicOr(status + k, 2);
+        st4(mom + q, m);
+        st4(vel + q, v);
+        st4(params + q, th);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            int wn, wk;
+            const int l = weight_of(H, p + i, wn, wk);
+            if (l < 0) continue;
+            const float x = at4(th, i);
             const int N = l == 4 ? NOUT : H;
-            if (wt) wt[ob.wt_off + wt_layer_off(H, l) + (long long)wk * N + wn] = th;   // transposed shadow
-            if (img && img_off[k] >= 0) {                                        // BF16 operand image
+            if (wt) wt[ob.wt_off + wt_layer_off(H, l) + (long long)wk * N + wn] = x;   // transposed shadow
+            if (img && img_off[k] >= 0) {                                       // BF16 operand image
                 const long long base = l == 0 ? 0 : (long long)H * DINP + (long long)(l - 1) * H * H;
-                img[img_off[k] + base + cm_off(wn, wk, l == 0 ? DINP : H) / 2] = __float2bfloat16(th);
+                img[img_off[k] + base + cm_off(wn, wk, l == 0 ? DINP : H) / 2] = __float2bfloat16(x);
             }
         }
     }

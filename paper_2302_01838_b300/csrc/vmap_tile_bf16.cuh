@@ -137,12 +137,12 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
     const TileArgs& ta = ba.t;
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char* G0 = sm + C::G0;
-    unsigned char* HA[4] = {sm + C::HA, sm + C::HA + C::HA_BYTES, sm + C::HA + 2 * C::HA_BYTES,
-                            sm + C::HA + 3 * C::HA_BYTES};
-    unsigned char* DZ[2] = {sm + C::DZ, sm + C::DZ + C::DZ_BYTES};
+    // tiles by index, computed (a pointer array indexed in a loop would live in local memory)
+    auto HAp = [&](int l) { return sm + C::HA + l * C::HA_BYTES; };
+    auto DZp = [&](int i) { return sm + C::DZ + i * C::DZ_BYTES; };
     unsigned char* DYt = sm + C::DY;
     unsigned char* W1 = sm + C::WIMG;
-    unsigned char* Wh[3] = {W1 + C::W1B, W1 + C::W1B + C::WHB, W1 + C::W1B + 2 * C::WHB};
+    auto Whp = [&](int l) { return W1 + C::W1B + l * C::WHB; };
     unsigned char* W5 = W1 + C::W1B + 3 * C::WHB;
     float* xt = reinterpret_cast<float*>(sm + C::XT);
     float* tsm = reinterpret_cast<float*>(sm + C::TSO);
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
     for (int i = tid; i < 4 * TM; i += blockDim.x) {
         const int l = i / TM, r = i % TM;
         float v[8] = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        st_bf16x8(HA[l], cm_off(r, H, CH), v);   // column H = 1 (bias gradient lane)
+        st_bf16x8(HAp(l), cm_off(r, H, CH), v);   // column H = 1 (bias gradient lane)
     }
     tc_fence_before();
     __syncthreads();
@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
                     float u[8];
 #pragma unroll
                     for (int j = 0; j < 8; ++j) u[j] = fmaxf(v[c0 + j] + bv[c0 + j], 0.f);
-                    st_bf16x8(HA[l], cm_off(row, hf * NC + c0, CH), u);
+                    st_bf16x8(HAp(l), cm_off(row, hf * NC + c0, CH), u);
                 }
             }
             sync_for_mma();
@@ -366,12 +366,12 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
                 if (l < 3) {
 #pragma unroll
                     for (int kc = 0; kc < H / 16; ++kc)
-                        mma_bf16(tmem + C::C_FWD, desc_kmajor(HA[l], CH, 16 * kc), desc_kmajor(Wh[l], H, 16 * kc),
+                        mma_bf16(tmem + C::C_FWD, desc_kmajor(HAp(l), CH, 16 * kc), desc_kmajor(Whp(l), H, 16 * kc),
                                  idesc_bf16(TM, H, 0, 0), kc > 0);
                 } else {
 #pragma unroll
                     for (int kc = 0; kc < H / 16; ++kc)
-                        mma_bf16(tmem + C::C_FWD, desc_kmajor(HA[3], CH, 16 * kc), desc_kmajor(W5, H, 16 * kc),
+                        mma_bf16(tmem + C::C_FWD, desc_kmajor(HAp(3), CH, 16 * kc), desc_kmajor(W5, H, 16 * kc),
                                  idesc_bf16(TM, 16, 0, 0), kc > 0);
                 }
                 mma_commit(mbar);
@@ -471,7 +471,7 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
 #pragma unroll
             for (int c0 = 0; c0 < NC; c0 += 8) {
                 float a[8], u[8];
-                ld_bf16x8(HA[src_ha], cm_off(row, hf * NC + c0, CH), a);
+                ld_bf16x8(HAp(src_ha), cm_off(row, hf * NC + c0, CH), a);
 #pragma unroll
                 for (int j = 0; j < 8; ++j) u[j] = a[j] > 0.f ? v[c0 + j] : 0.f;
                 st_bf16x8(dst, cm_off(row, hf * NC + c0, zcc), u);
@@ -484,35 +484,35 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
         }
         wait_mma();
         if (abort) break;
-        dx_epilogue(3, DZ[0], H);                                   // dZ4
+        dx_epilogue(3, DZp(0), H);                                   // dZ4
         sync_for_mma();
         if (tid == 0) {
-            issue_dx(DZ[0], H, Wh[2]);                              // dZ4 W4
-            issue_dw(C::C_DW5, HA[3], CH, DYt, 16, 16);             // dW5^T += h4^T dY
+            issue_dx(DZp(0), H, Whp(2));                              // dZ4 W4
+            issue_dw(C::C_DW5, HAp(3), CH, DYt, 16, 16);             // dW5^T += h4^T dY
         }
         wait_mma();
         if (abort) break;
-        dx_epilogue(2, DZ[1], H);                                   // dZ3
+        dx_epilogue(2, DZp(1), H);                                   // dZ3
         sync_for_mma();
         if (tid == 0) {
-            issue_dx(DZ[1], H, Wh[1]);                              // dZ3 W3
-            issue_dw(C::C_DW1 + 3 * H, HA[2], CH, DZ[0], H, H);     // dW4^T += h3^T dZ4
+            issue_dx(DZp(1), H, Whp(1));                              // dZ3 W3
+            issue_dw(C::C_DW1 + 3 * H, HAp(2), CH, DZp(0), H, H);     // dW4^T += h3^T dZ4
         }
         wait_mma();
         if (abort) break;
-        dx_epilogue(1, HA[3], CH);                                  // dZ2
+        dx_epilogue(1, HAp(3), CH);                                  // dZ2
         sync_for_mma();
         if (tid == 0) {
-            issue_dx(HA[3], CH, Wh[0]);                             // dZ2 W2
-            issue_dw(C::C_DW1 + 2 * H, HA[1], CH, DZ[1], H, H);     // dW3^T += h2^T dZ3
+            issue_dx(HAp(3), CH, Whp(0));                             // dZ2 W2
+            issue_dw(C::C_DW1 + 2 * H, HAp(1), CH, DZp(1), H, H);     // dW3^T += h2^T dZ3
         }
         wait_mma();
         if (abort) break;
-        dx_epilogue(0, DZ[0], H);                                   // dZ1
+        dx_epilogue(0, DZp(0), H);                                   // dZ1
         sync_for_mma();
         if (tid == 0) {
-            issue_dw(C::C_DW1 + H, HA[0], CH, HA[3], CH, H);        // dW2^T += h1^T dZ2
-            issue_dw(C::C_DW1, G0, DINP, DZ[0], H, H);              // dW1^T += enc^T dZ1
+            issue_dw(C::C_DW1 + H, HAp(0), CH, HAp(3), CH, H);        // dW2^T += h1^T dZ2
+            issue_dw(C::C_DW1, G0, DINP, DZp(0), H, H);              // dW1^T += enc^T dZ1
             mma_commit(mbar);
         }
         wait_mma();

@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(WIDE_THREADS, 1) k_wide_fb(StepParams sp, Wide
     const TileArgs& ta = wa.t;
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char* W1 = sm + C::WIMG;
-    unsigned char* Wh[3] = {W1 + C::W1B, W1 + C::W1B + C::WHB, W1 + C::W1B + 2 * C::WHB};
+    auto Whp = [&](int l) { return W1 + C::W1B + l * C::WHB; };   // computed, not a local-memory array
     unsigned char* W5 = W1 + C::W1B + 3 * C::WHB;
     unsigned char* G0 = sm + C::G0;
     unsigned char* DYt = sm + C::G0;
@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(WIDE_THREADS, 1) k_wide_fb(StepParams sp, Wide
                 if (l < 3) {
 #pragma unroll
                     for (int kc = 0; kc < WH / 16; ++kc)
-                        mma_bf16(tmem, desc_kmajor(HA, WH, 16 * kc), desc_kmajor(Wh[l], WH, 16 * kc),
+                        mma_bf16(tmem, desc_kmajor(HA, WH, 16 * kc), desc_kmajor(Whp(l), WH, 16 * kc),
                                  idesc_bf16(TM, WH, 0, 0), kc > 0);
                 } else {
 #pragma unroll
@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(WIDE_THREADS, 1) k_wide_fb(StepParams sp, Wide
             if (tid == 0) {
 #pragma unroll
                 for (int kc = 0; kc < WH / 16; ++kc)
-                    mma_bf16(tmem, desc_kmajor(DZ, WH, 16 * kc), desc_mnmajor(Wh[l - 1], WH, 16 * kc),
+                    mma_bf16(tmem, desc_kmajor(DZ, WH, 16 * kc), desc_mnmajor(Whp(l - 1), WH, 16 * kc),
                              idesc_bf16(TM, WH, 0, 1), kc > 0);
                 mma_commit(mbar);
             }
