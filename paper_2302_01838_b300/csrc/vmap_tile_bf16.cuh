@@ -55,7 +55,8 @@ template <int H> struct Bf16Cfg {
     static constexpr int YB = TSO + TM * 4;                       // [4][128]
     static constexpr int RAYS = YB + 4 * TM * 4;                  // [32][16]
     static constexpr int LOSS = RAYS + RTMAX * RAYF * 4;          // [4]
-    static constexpr int MBAR = LOSS + 16;
+    static constexpr int BIAS = LOSS + 16;                        // [4][H] + [NOUT] f32 biases of the run's object
+    static constexpr int MBAR = BIAS + (4 * H + 16) * 4;
     static constexpr int WBAR = MBAR + 8;                         // weight image loaded
     static constexpr int TSLOT = WBAR + 8;
     static constexpr int BYTES = TSLOT + 8;
@@ -149,6 +150,7 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
     float* yb = reinterpret_cast<float*>(sm + C::YB);
     float* rays = reinterpret_cast<float*>(sm + C::RAYS);
     float* lossacc = reinterpret_cast<float*>(sm + C::LOSS);
+    float* bsm = reinterpret_cast<float*>(sm + C::BIAS);
     uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + C::MBAR);
     uint64_t* wbar = reinterpret_cast<uint64_t*>(sm + C::WBAR);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + C::TSLOT);
@@ -285,6 +287,8 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
                 wpend = true;
             }
             if (tid < 4) lossacc[tid] = 0.f;
+            // the object's biases, read by the epilogues from shared memory
+            for (int i = tid; i < 4 * H + NOUT; i += blockDim.x) bsm[i] = P[b_off(H, i / H) + i % H];
         }
         __syncthreads();
         for (int m = tid; m < TM; m += blockDim.x) {
@@ -329,15 +333,7 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
                          idesc_bf16(TM, H, 0, 0), kc > 0);
             mma_commit(mbar);
         }
-        // this thread's H/2 bias values of layer l, loaded while the MMA runs
         constexpr int NC = H / 2;
-        float bv[NC];
-        auto load_bias = [&](int l) {
-            const float* b = P + b_off(H, l) + hf * NC;
-#pragma unroll
-            for (int i = 0; i < NC; ++i) bv[i] = __ldg(b + i);
-        };
-        load_bias(0);
         // the next tile of this range: its picks now, its rays and depths during the backward
         const bool has_next = GRAD && tl + 1 < t1;
         TileDev tdn{};
@@ -357,7 +353,7 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
                 for (int c0 = 0; c0 < NC; c0 += 8) {
                     float u[8];
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) u[j] = fmaxf(v[c0 + j] + bv[c0 + j], 0.f);
+                    for (int j = 0; j < 8; ++j) u[j] = fmaxf(v[c0 + j] + bsm[l * H + hf * NC + c0 + j], 0.f);
                     st_bf16x8(HAp(l), cm_off(row, hf * NC + c0, CH), u);
                 }
             }
@@ -376,7 +372,6 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
                 }
                 mma_commit(mbar);
             }
-            if (l < 3) load_bias(l + 1);
             wait_mma();
             if (abort) break;
         }
@@ -387,7 +382,7 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
             tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + C::C_FWD + hf * 8, v);
             tmem_ld_wait();
             if (hf == 0) {
-                const float* b5 = P + b_off(H, 4);
+                const float* b5 = bsm + 4 * H;
 #pragma unroll
                 for (int j = 0; j < NOUT; ++j) yb[j * TM + row] = v[j] + b5[j];
             }
