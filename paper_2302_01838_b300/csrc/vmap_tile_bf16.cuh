@@ -82,45 +82,65 @@ __device__ __forceinline__ void ld_bf16x8(const unsigned char* tile, int off, fl
 
 // sin / cos after reduction to [-pi, pi] (the hardware approximations are
 // accurate there; the result is rounded to BF16 anyway)
-__device__ __forceinline__ float red2pi(float p) { return fmaf(-6.28318530717958647692f, rintf(p * 0.15915494309189533577f), p); }
+__device__ __forceinline__ float red2pi(float p) {
+    // nearest integer of t by adding and removing 1.5 * 2^23 (exact for |t| < 2^22,
+    // ties to even like rintf), kept on the FMA pipe
+    const float t = __fmul_rn(p, 0.15915494309189533577f);
+    const float k = __fsub_rn(__fadd_rn(t, 12582912.f), 12582912.f);
+    return fmaf(-6.28318530717958647692f, k, p);
+}
 
-// Encoding of one sample into row m of a [128][96] BF16 core-matrix tile.
-// Half 0 writes columns 0..47 (x~, sin(B x~)), half 1 columns 48..95
-// (cos(B x~), the ones column 93, zero padding); every feature index is a
-// compile-time constant, so B is read as immediate constant-bank operands.
-// gcopy (may be NULL) receives the same bytes at the same offsets.
+// Encoding of one sample into row m of a [128][96] BF16 core-matrix tile:
+// columns 0..2 x~, 3..47 sin(B x~), 48..92 cos(B x~), 93 one, 94..95 zero.
+// The two threads of a sample split the 45 projections so that each owns
+// whole 8-column core-matrix rows: half 0 takes angles 0..23 and writes
+// columns 0..23 (x~, sin 0..20) and 48..71 (cos 0..23); half 1 takes angles
+// 21..44 and writes columns 24..47 (sin 21..44) and 72..95 (cos 24..44, the
+// one, padding). Each thread computes 24 projections and 45 sines/cosines;
+// every feature index is a compile-time constant, so B is read as immediate
+// constant-bank operands. gcopy (may be NULL) receives the same bytes.
 __device__ __forceinline__ float enc_proj(const StepParams& sp, int j, float x0, float x1, float x2) {
     return red2pi(fmaf(sp.B[3 * j + 2], x2, fmaf(sp.B[3 * j + 1], x1, sp.B[3 * j] * x0)));
 }
+__device__ __forceinline__ void enc_store(unsigned char* tile, unsigned char* gcopy, int m, int ch, const float (&v)[8]) {
+    const int off = cm_off(m, ch * 8, DINP);
+    st_bf16x8(tile, off, v);
+    if (gcopy) *reinterpret_cast<uint4*>(gcopy + off) = *reinterpret_cast<const uint4*>(tile + off);
+}
+// one half of a sample's row: angles J0 .. J0 + 23, sine columns of groups
+// SG .. SG + 2 and cosine columns of groups CG .. CG + 2
+template <int J0, int SG, int CG>
+__device__ __forceinline__ void encode_half(const StepParams& sp, float x0, float x1, float x2, int m,
+                                            unsigned char* tile, unsigned char* gcopy) {
+    float pr[24];
+#pragma unroll
+    for (int j = 0; j < 24; ++j) pr[j] = enc_proj(sp, J0 + j, x0, x1, x2);
+#pragma unroll
+    for (int ch = SG; ch < SG + 3; ++ch) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int c = ch * 8 + u;   // column c < 3: x~; else the sine of angle c - 3
+            v[u] = c == 0 ? x0 : c == 1 ? x1 : c == 2 ? x2 : __sinf(pr[c - 3 - J0]);
+        }
+        enc_store(tile, gcopy, m, ch, v);
+    }
+#pragma unroll
+    for (int ch = CG; ch < CG + 3; ++ch) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int c = ch * 8 + u;   // cosine of angle c - 3 - NF, then the one and padding
+            v[u] = c < DIN ? __cosf(pr[c - 3 - NF - J0]) : (c == DIN ? 1.f : 0.f);
+        }
+        enc_store(tile, gcopy, m, ch, v);
+    }
+}
 __device__ __forceinline__ void encode_row_half(const StepParams& sp, float x0, float x1, float x2, int m, int half,
                                                 unsigned char* tile, unsigned char* gcopy) {
-    if (half == 0) {
-#pragma unroll
-        for (int ch = 0; ch < 6; ++ch) {
-            float v[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int c = ch * 8 + u;
-                v[u] = c == 0 ? x0 : c == 1 ? x1 : c == 2 ? x2 : __sinf(enc_proj(sp, c - 3, x0, x1, x2));
-            }
-            const int off = cm_off(m, ch * 8, DINP);
-            st_bf16x8(tile, off, v);
-            if (gcopy) *reinterpret_cast<uint4*>(gcopy + off) = *reinterpret_cast<const uint4*>(tile + off);
-        }
-    } else {
-#pragma unroll
-        for (int ch = 6; ch < 12; ++ch) {
-            float v[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int c = ch * 8 + u;
-                v[u] = c < DIN ? __cosf(enc_proj(sp, c - 3 - NF, x0, x1, x2)) : (c == DIN ? 1.f : 0.f);
-            }
-            const int off = cm_off(m, ch * 8, DINP);
-            st_bf16x8(tile, off, v);
-            if (gcopy) *reinterpret_cast<uint4*>(gcopy + off) = *reinterpret_cast<const uint4*>(tile + off);
-        }
-    }
+    static_assert(NF == 45 && DIN == 93 && DINP == 96, "feature split below assumes 45 Gaussian features");
+    if (half == 0) encode_half<0, 0, 6>(sp, x0, x1, x2, m, tile, gcopy);
+    else encode_half<21, 3, 9>(sp, x0, x1, x2, m, tile, gcopy);
 }
 
 struct Bf16Args {
