@@ -50,15 +50,15 @@ template <int H> struct Bf16Cfg {
     static constexpr int WIMG_BYTES = W1B + 3 * WHB + W5B;
     static constexpr int GUARD = WIMG + WIMG_BYTES;               // tail room for MN-major over-reads
     static constexpr int F32 = GUARD + 4096;
-    static constexpr int XT = F32;                                // [3][128] f32
-    static constexpr int TSO = XT + 3 * TM * 4;                   // [128]
+    static constexpr int TSO = F32;                               // [128] sample depths
     static constexpr int YB = TSO + TM * 4;                       // [4][128]
     static constexpr int RAYS = YB + 4 * TM * 4;                  // [32][16]
-    static constexpr int LOSS = RAYS + RTMAX * RAYF * 4;          // [4]
-    static constexpr int BIAS = LOSS + 16;                        // [4][H] + [NOUT] f32 biases of the run's object
+    static constexpr int LOSS = RAYS + RTMAX * RAYF * 4;          // [RTMAX][3] run loss sums per ray slot
+    static constexpr int BIAS = LOSS + RTMAX * 3 * 4;             // [4][H] + [NOUT] f32 biases of the run's object
     static constexpr int MBAR = BIAS + (4 * H + 16) * 4;
     static constexpr int WBAR = MBAR + 8;                         // weight image loaded
-    static constexpr int TSLOT = WBAR + 8;
+    static constexpr int MBAR2 = WBAR + 8;                        // MMAs issued by thread 128 done
+    static constexpr int TSLOT = MBAR2 + 8;
     static constexpr int BYTES = TSLOT + 8;
     static_assert(WIMG_BYTES % 16 == 0, "bulk copy size");
 };
@@ -165,7 +165,6 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
     unsigned char* W1 = sm + C::WIMG;
     auto Whp = [&](int l) { return W1 + C::W1B + l * C::WHB; };
     unsigned char* W5 = W1 + C::W1B + 3 * C::WHB;
-    float* xt = reinterpret_cast<float*>(sm + C::XT);
     float* tsm = reinterpret_cast<float*>(sm + C::TSO);
     float* yb = reinterpret_cast<float*>(sm + C::YB);
     float* rays = reinterpret_cast<float*>(sm + C::RAYS);
@@ -173,6 +172,7 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
     float* bsm = reinterpret_cast<float*>(sm + C::BIAS);
     uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + C::MBAR);
     uint64_t* wbar = reinterpret_cast<uint64_t*>(sm + C::WBAR);
+    uint64_t* mbar2 = reinterpret_cast<uint64_t*>(sm + C::MBAR2);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + C::TSLOT);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int q = warp & 3, hf = warp >> 2;   // TMEM lane quadrant, column half
@@ -182,6 +182,7 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
     if (tid == 0) {
         mbar_init(mbar, 1);
         mbar_init(wbar, 1);
+        mbar_init(mbar2, 1);
     }
     if (warp == 0) tmem_alloc(tslot, C::NCOLS);
     for (int i = tid; i < 4 * TM; i += blockDim.x) {
@@ -193,25 +194,31 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-    uint32_t phase = 0, wphase = 0;
+    uint32_t phase = 0, wphase = 0, phase2 = 0;
     bool abort = false, wpend = false;   // wpend: a weight copy was issued and not yet seen complete
     bool pre = false;                    // this tile's rays and depths were prefetched
     int npick = 0;                       // pick of the next tile's ray `tid`
 
+    // Every thread waits for an MMA commit by itself (no CTA barrier, so a
+    // thread that has no epilogue share in a round is not waited for); a
+    // wait that gave up is agreed on at the next CTA barrier.
+    bool wfail = false;
     auto wait_mma = [&]() {
-        const bool ok = mbar_wait(mbar, phase, MMA_WAIT_LIMIT);
+        wfail |= !mbar_wait(mbar, phase, MMA_WAIT_LIMIT);
         phase ^= 1;
-        if (__syncthreads_or(!ok)) {
+        tc_fence_after();
+    };
+    auto agree = [&]() {   // CTA barrier; every thread learns whether any wait gave up
+        if (__syncthreads_or(wfail)) {
             abort = true;
             if (tid == 0) atomicExch(ba.err, 1);
         }
-        tc_fence_after();
     };
     auto sync_for_mma = [&]() {   // smem operand writes and TMEM reads done -> MMA may start
         tmem_ld_wait();
         fence_async_smem();
         tc_fence_before();
-        __syncthreads();
+        agree();
         tc_fence_after();
     };
 
@@ -265,9 +272,13 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
             }
         }
         if (tid == 0) {
-            gp[PC + 0] = lossacc[0];
-            gp[PC + 1] = lossacc[1];
-            gp[PC + 2] = lossacc[2];
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f;   // ray slots in order
+            for (int r = 0; r < RTMAX; ++r) {
+                s0 += lossacc[3 * r]; s1 += lossacc[3 * r + 1]; s2 += lossacc[3 * r + 2];
+            }
+            gp[PC + 0] = s0;
+            gp[PC + 1] = s1;
+            gp[PC + 2] = s2;
             gp[PC + 3] = 0.f;
             gp[PC + 4] = 0.f;
             gp[PC + 5] = 0.f;
@@ -306,33 +317,28 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
                 bulk_load(W1, ba.img + ba.img_off[k], (uint32_t)C::WIMG_BYTES, wbar);
                 wpend = true;
             }
-            if (tid < 4) lossacc[tid] = 0.f;
+            for (int i = tid; i < 3 * RTMAX; i += blockDim.x) lossacc[i] = 0.f;
             // the object's biases, read by the epilogues from shared memory
             for (int i = tid; i < 4 * H + NOUT; i += blockDim.x) bsm[i] = P[b_off(H, i / H) + i % H];
         }
         __syncthreads();
-        for (int m = tid; m < TM; m += blockDim.x) {
-            float x0 = 0.f, x1 = 0.f, x2 = 0.f, t = 0.f;
+        // ---- points and encoding -> G0 (BF16; two threads per sample, each
+        // forms the sample's normalised point itself) ------------------------------
+        for (int f = tid; f < 2 * TM; f += blockDim.x) {
+            const int m = f % TM, half = f / TM;
+            float x0 = 0.f, x1 = 0.f, x2 = 0.f;
             if (m < M) {
-                const int r = m / S;
-                const float* d = rays + r * RAYF;
-                t = pre ? tsm[m] : ta.tbuf[sbase + m];
+                const float* d = rays + (m / S) * RAYF;
+                const float t = pre ? tsm[m] : ta.tbuf[sbase + m];
+                if (!pre && half == 0) tsm[m] = t;
                 x0 = (fmaf(t, d[3], d[0]) - cx) / sc;
                 x1 = (fmaf(t, d[4], d[1]) - cy) / sc;
                 x2 = (fmaf(t, d[5], d[2]) - cz) / sc;
             }
-            tsm[m] = t;
-            xt[m] = x0;
-            xt[TM + m] = x1;
-            xt[2 * TM + m] = x2;
-        }
-        __syncthreads();
-        // ---- encoding -> G0 (BF16; two threads per sample) ----------------------
-        for (int f = tid; f < 2 * TM; f += blockDim.x) {
-            const int m = f % TM;
-            encode_row_half(sp, xt[m], xt[TM + m], xt[2 * TM + m], m, f / TM, G0, nullptr);
+            encode_row_half(sp, x0, x1, x2, m, half, G0, nullptr);
         }
         sync_for_mma();
+        if (abort) break;
 
         // ---- forward ------------------------------------------------------------
         if (first) {
@@ -378,6 +384,7 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
                 }
             }
             sync_for_mma();
+            if (abort) break;
             if (tid == 0) {
                 if (l < 3) {
 #pragma unroll
@@ -404,26 +411,26 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
             if (hf == 0) {
                 const float* b5 = bsm + 4 * H;
 #pragma unroll
-                for (int j = 0; j < NOUT; ++j) yb[j * TM + row] = v[j] + b5[j];
+                for (int j = 0; j < NOUT; ++j) yb[j * TM + row] = sigmoidf_(v[j] + b5[j]);   // o, c (Eq. 1 heads)
             }
         }
-        __syncthreads();
+        agree();
+        if (abort) break;
 
         // ---- rendering, loss, dL/dy (FP32) ----------------------------------------
         const float invR = 1.f / (float)ta.obs[k].R;
-        for (int r = warp; r < nr; r += NTHREADS / 32)
-            render_ray_warp<GRAD, TM>(sp, yb, tsm, rays + r * RAYF, r, S, invR);
+        for (int r = warp; r < nr; r += NTHREADS / 32) {
+            float* d = rays + r * RAYF;
+            render_ray_warp<GRAD, TM, true>(sp, yb, tsm, d, r, S, invR);
+            // the ray's loss terms join its slot's run sums (lane 0 wrote them)
+            if (lane == 0) {
+                lossacc[3 * r] += d[13]; lossacc[3 * r + 1] += d[14]; lossacc[3 * r + 2] += d[15];
+            }
+        }
         for (int m = M + tid; m < TM; m += blockDim.x) {
             yb[m] = 0.f; yb[TM + m] = 0.f; yb[2 * TM + m] = 0.f; yb[3 * TM + m] = 0.f;
         }
         __syncthreads();
-        if (tid == 0) {
-            float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-            for (int r = 0; r < nr; ++r) {
-                s0 += rays[r * RAYF + 13]; s1 += rays[r * RAYF + 14]; s2 += rays[r * RAYF + 15];
-            }
-            lossacc[0] += s0; lossacc[1] += s1; lossacc[2] += s2;
-        }
         if (!GRAD) {
             __syncthreads();
             if (last) flush_run(td.part);
@@ -439,6 +446,7 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
             st_bf16x8(DYt, cm_off(r, half * 8, 16), v);
         }
         sync_for_mma();
+        if (abort) break;
         // rays, depths and the loss terms of this tile are consumed: prefetch the next tile's
         pre = false;
         if (has_next) {
@@ -461,10 +469,15 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
         // The input-gradient chain dZ4 -> dZ3 -> dZ2 -> dZ1 is the critical path:
         // each round commits its input-gradient MMA alone and then issues the
         // previous layer's weight-gradient MMAs behind it, so those run during
-        // the next epilogue instead of delaying the next commit. Buffers:
-        // dZ4 -> DZ[0], dZ3 -> DZ[1], dZ2 -> HA[3] (h4 is dead once dW5 has run),
-        // dZ1 -> DZ[0] (dZ4 is dead once dW4 has run); a commit tracks every
-        // earlier MMA, so each rewritten buffer's last reader has finished.
+        // the next epilogue instead of delaying the next commit. Issuing eight
+        // MMAs holds thread 0 for hundreds of cycles, so in those rounds warp 0
+        // has no epilogue share: warp 4 (the same TMEM lane quadrant) takes both
+        // column halves. In the last round thread 0 feeds dW2 and thread 128
+        // feeds dW1 (each accumulator always from the same thread, in order).
+        // Buffers: dZ4 -> DZ[0], dZ3 -> DZ[1], dZ2 -> HA[3] (h4 is dead once dW5
+        // has run), dZ1 -> DZ[0] (dZ4 is dead once dW4 has run); a commit tracks
+        // every earlier MMA of its thread, so each rewritten buffer's last reader
+        // has finished.
         auto issue_dx = [&](const unsigned char* z, int zcc, const unsigned char* w) {
 #pragma unroll
             for (int kc = 0; kc < H / 16; ++kc)
@@ -479,17 +492,24 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
                 mma_bf16(tmem + col, desc_mnmajor(a, acc, 16 * kc), desc_mnmajor(z, zcc, 16 * kc),
                          idesc_bf16(TM, n, 1, 1), !first || kc > 0);
         };
-        // dZ_l = acc * [h_l > 0] (h_l in HA[l - 1]) -> dst with zcc columns
-        auto dx_epilogue = [&](int src_ha, unsigned char* dst, int zcc) {
-            float v[NC];
-            tmem_ld_cols<NC>(tmem + ((uint32_t)(q * 32) << 16) + C::C_DX + hf * NC, v);
+        // dZ_l = acc * [h_l > 0] (h_l in HA[l - 1]) -> dst with zcc columns; with
+        // `shift`, warp 0's column half goes to warp 4
+        auto dx_epilogue = [&](int src_ha, unsigned char* dst, int zcc, bool shift) {
+            if (shift && warp == 0) return;
+            const int nh = shift && warp == 4 ? 2 : 1;
+#pragma unroll 1
+            for (int hh = 0; hh < nh; ++hh) {
+                const int h2 = nh == 2 ? hh : hf;
+                float v[NC];
+                tmem_ld_cols<NC>(tmem + ((uint32_t)(q * 32) << 16) + C::C_DX + h2 * NC, v);
 #pragma unroll
-            for (int c0 = 0; c0 < NC; c0 += 8) {
-                float a[8], u[8];
-                ld_bf16x8(HAp(src_ha), cm_off(row, hf * NC + c0, CH), a);
+                for (int c0 = 0; c0 < NC; c0 += 8) {
+                    float a[8], u[8];
+                    ld_bf16x8(HAp(src_ha), cm_off(row, h2 * NC + c0, CH), a);
 #pragma unroll
-                for (int j = 0; j < 8; ++j) u[j] = a[j] > 0.f ? v[c0 + j] : 0.f;
-                st_bf16x8(dst, cm_off(row, hf * NC + c0, zcc), u);
+                    for (int j = 0; j < 8; ++j) u[j] = a[j] > 0.f ? v[c0 + j] : 0.f;
+                    st_bf16x8(dst, cm_off(row, h2 * NC + c0, zcc), u);
+                }
             }
         };
         // layer 5: dY W5
@@ -498,39 +518,45 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
             mma_commit(mbar);
         }
         wait_mma();
-        if (abort) break;
-        dx_epilogue(3, DZp(0), H);                                   // dZ4
+        dx_epilogue(3, DZp(0), H, false);                            // dZ4
         sync_for_mma();
+        if (abort) break;
         if (tid == 0) {
             issue_dx(DZp(0), H, Whp(2));                              // dZ4 W4
             issue_dw(C::C_DW5, HAp(3), CH, DYt, 16, 16);             // dW5^T += h4^T dY
         }
         wait_mma();
-        if (abort) break;
-        dx_epilogue(2, DZp(1), H);                                   // dZ3
+        dx_epilogue(2, DZp(1), H, true);                             // dZ3
         sync_for_mma();
+        if (abort) break;
         if (tid == 0) {
             issue_dx(DZp(1), H, Whp(1));                              // dZ3 W3
             issue_dw(C::C_DW1 + 3 * H, HAp(2), CH, DZp(0), H, H);     // dW4^T += h3^T dZ4
         }
         wait_mma();
-        if (abort) break;
-        dx_epilogue(1, HAp(3), CH);                                  // dZ2
+        dx_epilogue(1, HAp(3), CH, true);                            // dZ2
         sync_for_mma();
+        if (abort) break;
         if (tid == 0) {
             issue_dx(HAp(3), CH, Whp(0));                             // dZ2 W2
             issue_dw(C::C_DW1 + 2 * H, HAp(1), CH, DZp(1), H, H);     // dW3^T += h2^T dZ3
         }
         wait_mma();
-        if (abort) break;
-        dx_epilogue(0, DZp(0), H);                                   // dZ1
+        dx_epilogue(0, DZp(0), H, true);                             // dZ1
         sync_for_mma();
+        if (abort) break;
         if (tid == 0) {
             issue_dw(C::C_DW1 + H, HAp(0), CH, HAp(3), CH, H);        // dW2^T += h1^T dZ2
-            issue_dw(C::C_DW1, G0, DINP, DZp(0), H, H);              // dW1^T += enc^T dZ1
             mma_commit(mbar);
+        } else if (tid == 128) {
+            issue_dw(C::C_DW1, G0, DINP, DZp(0), H, H);              // dW1^T += enc^T dZ1
+            mma_commit(mbar2);
         }
         wait_mma();
+        wfail |= !mbar_wait(mbar2, phase2, MMA_WAIT_LIMIT);
+        phase2 ^= 1;
+        tc_fence_after();
+        agree();
         if (abort) break;
         if (last) flush_run(td.part);
         tc_fence_before();

@@ -289,8 +289,9 @@ __device__ __forceinline__ float warp_sum(float v) {
 // ray's loss terms, and (GRAD) dL/dy for its samples. The exclusive product
 // P_i = prod_{j<i}(1 - o_j) is a multiplicative scan; the reverse recursion
 // S_i = o_i g_i + (1 - o_i) S_{i+1} is a suffix scan of affine maps
-// x -> (1 - o_i) x + o_i g_i (no division by 1 - o_i anywhere).
-template <bool GRAD, int LD>
+// x -> (1 - o_i) x + o_i g_i (no division by 1 - o_i anywhere). With ACT the
+// four outputs in yb already went through the sigmoid.
+template <bool GRAD, int LD, bool ACT = false>
 __device__ __forceinline__ void render_ray_warp(const StepParams& sp, float* yb, const float* tsm,
                                                 float* d, int r, int S, float invR) {
     const int i = threadIdx.x & 31;
@@ -298,10 +299,16 @@ __device__ __forceinline__ void render_ray_warp(const StepParams& sp, float* yb,
     const int m = r * S + i;
     float o = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, t = 0.f;
     if (v) {
-        o = sigmoidf_(yb[m]);
-        c0 = sigmoidf_(yb[LD + m]);
-        c1 = sigmoidf_(yb[2 * LD + m]);
-        c2 = sigmoidf_(yb[3 * LD + m]);
+        o = yb[m];
+        c0 = yb[LD + m];
+        c1 = yb[2 * LD + m];
+        c2 = yb[3 * LD + m];
+        if (!ACT) {
+            o = sigmoidf_(o);
+            c0 = sigmoidf_(c0);
+            c1 = sigmoidf_(c1);
+            c2 = sigmoidf_(c2);
+        }
         t = tsm[m];
     }
     float incl = v ? 1.f - o : 1.f;
