@@ -54,12 +54,11 @@ struct WideFbCfg {
     static constexpr int HA = G0 + TM * DINP * 2;                 // current h [128][128]
     static constexpr int DZ = HA + TM * WH * 2;                   // current dZ [128][128]
     static constexpr int MASK = DZ + TM * WH * 2;                 // [4][128][4] u32: bits of h_l > 0 (word = 32 columns)
-    static constexpr int XT = MASK + 4 * TM * 16;                 // [3][128] f32
-    static constexpr int TSO = XT + 3 * TM * 4;                   // [128]
+    static constexpr int TSO = MASK + 4 * TM * 16;               // [128] sample depths
     static constexpr int YB = TSO + TM * 4;                       // [4][128]
     static constexpr int RAYS = YB + 4 * TM * 4;                  // [RTMAX][RAYF]
-    static constexpr int LOSS = RAYS + RTMAX * RAYF * 4;          // [4]
-    static constexpr int MBAR = LOSS + 16;
+    static constexpr int BIAS = RAYS + RTMAX * RAYF * 4;          // [4][128] + [16] f32 biases of the run's object
+    static constexpr int MBAR = BIAS + (4 * WH + 16) * 4;
     static constexpr int WBAR = MBAR + 8;                         // weight image loaded
     static constexpr int TSLOT = WBAR + 8;
     static constexpr int BYTES = TSLOT + 8;
@@ -111,7 +110,7 @@ __global__ void __launch_bounds__(WIDE_THREADS, 1) k_wide_fb(StepParams sp, Wide
     unsigned char* HA = sm + C::HA;
     unsigned char* DZ = sm + C::DZ;
     uint32_t* mask = reinterpret_cast<uint32_t*>(sm + C::MASK);
-    float* xt = reinterpret_cast<float*>(sm + C::XT);
+    float* bsm = reinterpret_cast<float*>(sm + C::BIAS);
     float* tsm = reinterpret_cast<float*>(sm + C::TSO);
     float* yb = reinterpret_cast<float*>(sm + C::YB);
     float* rays = reinterpret_cast<float*>(sm + C::RAYS);
@@ -138,6 +137,8 @@ __global__ void __launch_bounds__(WIDE_THREADS, 1) k_wide_fb(StepParams sp, Wide
     const uint32_t tl_lane = tmem + ((uint32_t)(q * 32) << 16);
     uint32_t phase = 0, wphase = 0;
     bool abort = false, wpend = false;
+    bool pre = false;                    // this tile's rays and depths were prefetched
+    int npick = 0;                       // pick of the next tile's ray `tid`
 
     auto wait_mma = [&]() {
         const bool ok = mbar_wait(mbar, phase, MMA_WAIT_LIMIT);
@@ -198,32 +199,35 @@ __global__ void __launch_bounds__(WIDE_THREADS, 1) k_wide_fb(StepParams sp, Wide
             bulk_load(W1, wa.img + wa.img_off[k], (uint32_t)C::WIMG_BYTES, wbar);
             wpend = true;
         }
-        for (int r = tid; r < nr; r += blockDim.x) {
-            const float* rec = ta.pool + (ta.obs[k].src_off + ta.pick[td.ray0 + r]) * REC;
-            float* d = rays + r * RAYF;
+        // (after the first tile of a training range, the previous tile's backward
+        // already brought this tile's rays and depths in by cp.async)
+        if (!pre) {
+            for (int r = tid; r < nr; r += blockDim.x) {
+                const float* rec = ta.pool + (ta.obs[k].src_off + ta.pick[td.ray0 + r]) * REC;
+                float* d = rays + r * RAYF;
 #pragma unroll
-            for (int u = 0; u < 11; ++u) d[u] = rec[u];
+                for (int u = 0; u < 11; ++u) d[u] = rec[u];
+            }
+        } else {
+            cp_async_wait_all();
         }
+        if (first)   // the object's biases, read by the epilogues from shared memory
+            for (int i = tid; i < 4 * WH + NOUT; i += blockDim.x) bsm[i] = P[b_off(WH, i / WH) + i % WH];
         __syncthreads();
-        for (int m = tid; m < TM; m += blockDim.x) {
-            float x0 = 0.f, x1 = 0.f, x2 = 0.f, t = 0.f;
+        // ---- points and encoding -> G0 (and the activation record); two threads
+        // per sample, each forming the sample's normalised point itself ------------
+        for (int f = tid; f < 2 * TM; f += blockDim.x) {
+            const int m = f % TM, half = f / TM;
+            float x0 = 0.f, x1 = 0.f, x2 = 0.f;
             if (m < M) {
                 const float* d = rays + (m / S) * RAYF;
-                t = ta.tbuf[sbase + m];
+                const float t = pre ? tsm[m] : ta.tbuf[sbase + m];
+                if (!pre && half == 0) tsm[m] = t;
                 x0 = (fmaf(t, d[3], d[0]) - cx) / sc;
                 x1 = (fmaf(t, d[4], d[1]) - cy) / sc;
                 x2 = (fmaf(t, d[5], d[2]) - cz) / sc;
             }
-            tsm[m] = t;
-            xt[m] = x0;
-            xt[TM + m] = x1;
-            xt[2 * TM + m] = x2;
-        }
-        __syncthreads();
-        // ---- encoding -> G0 (and the activation record); two threads per sample --
-        for (int f = tid; f < 2 * TM; f += blockDim.x) {
-            const int m = f % TM;
-            encode_row_half(sp, xt[m], xt[TM + m], xt[2 * TM + m], m, f / TM, G0, nullptr);
+            encode_row_half(sp, x0, x1, x2, m, half, G0, nullptr);
         }
         sync_for_mma();
         if (GRAD) record(at + WideAct::G0, G0, TM * DINP * 2);
@@ -246,14 +250,13 @@ __global__ void __launch_bounds__(WIDE_THREADS, 1) k_wide_fb(StepParams sp, Wide
                          idesc_bf16(TM, WH, 0, 0), kc > 0);
             mma_commit(mbar);
         }
-        // this thread's 32 bias values of layer l, loaded while the MMA runs
-        float bv[32];
-        auto load_bias = [&](int l) {
-            const float* b = P + b_off(WH, l) + col0;
-#pragma unroll
-            for (int i = 0; i < 32; ++i) bv[i] = __ldg(b + i);
-        };
-        load_bias(0);
+        // the next tile of this range: its picks now, its rays and depths during the backward
+        const bool has_next = GRAD && tl + 1 < t1;
+        TileDev tdn{};
+        if (has_next) {
+            tdn = ta.tiles[tl + 1];
+            if (tid < tdn.nr) npick = ta.pick[tdn.ray0 + tid];
+        }
         wait_mma();
         if (abort) break;
 #pragma unroll 1
@@ -265,7 +268,7 @@ __global__ void __launch_bounds__(WIDE_THREADS, 1) k_wide_fb(StepParams sp, Wide
             for (int c = 0; c < 4; ++c) {
                 float u[8];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) u[j] = fmaxf(v[8 * c + j] + bv[8 * c + j], 0.f);
+                for (int j = 0; j < 8; ++j) u[j] = fmaxf(v[8 * c + j] + bsm[l * WH + col0 + 8 * c + j], 0.f);
                 bits |= (unsigned)pos_bits(u, 8 * c);
                 st_bf16x8(HA, cm_off(row, col0 + 8 * c, WH), u);
             }
@@ -286,7 +289,6 @@ __global__ void __launch_bounds__(WIDE_THREADS, 1) k_wide_fb(StepParams sp, Wide
                 }
                 mma_commit(mbar);
             }
-            if (l < 3) load_bias(l + 1);
             wait_mma();
             if (abort) break;
         }
@@ -296,9 +298,9 @@ __global__ void __launch_bounds__(WIDE_THREADS, 1) k_wide_fb(StepParams sp, Wide
             tmem_ld8(tl_lane, v);
             tmem_ld_wait();
             if (qc == 0) {
-                const float* b5 = P + b_off(WH, 4);
+                const float* b5 = bsm + 4 * WH;
 #pragma unroll
-                for (int j = 0; j < NOUT; ++j) yb[j * TM + row] = v[j] + b5[j];
+                for (int j = 0; j < NOUT; ++j) yb[j * TM + row] = sigmoidf_(v[j] + b5[j]);   // o, c (Eq. 1 heads)
             }
         }
         __syncthreads();
@@ -306,17 +308,24 @@ __global__ void __launch_bounds__(WIDE_THREADS, 1) k_wide_fb(StepParams sp, Wide
         // ---- rendering, loss, dL/dy (FP32) ---------------------------------------
         const float invR = 1.f / (float)ta.obs[k].R;
         for (int r = warp; r < nr; r += blockDim.x / 32)
-            render_ray_warp<GRAD, TM>(sp, yb, tsm, rays + r * RAYF, r, S, invR);
+            render_ray_warp<GRAD, TM, true>(sp, yb, tsm, rays + r * RAYF, r, S, invR);
         for (int m = M + tid; m < TM; m += blockDim.x) {
             yb[m] = 0.f; yb[TM + m] = 0.f; yb[2 * TM + m] = 0.f; yb[3 * TM + m] = 0.f;
         }
         __syncthreads();
-        if (tid == 0) {
+        if (warp == 0) {   // the tile's loss sums, rays in order (lane r holds ray r's terms)
+            const int ln = tid & 31;
+            float e0 = 0.f, e1 = 0.f, e2 = 0.f;
+            if (ln < nr) {
+                e0 = rays[ln * RAYF + 13]; e1 = rays[ln * RAYF + 14]; e2 = rays[ln * RAYF + 15];
+            }
             float s0 = 0.f, s1 = 0.f, s2 = 0.f;
             for (int r = 0; r < nr; ++r) {
-                s0 += rays[r * RAYF + 13]; s1 += rays[r * RAYF + 14]; s2 += rays[r * RAYF + 15];
+                s0 += __shfl_sync(0xffffffffu, e0, r);
+                s1 += __shfl_sync(0xffffffffu, e1, r);
+                s2 += __shfl_sync(0xffffffffu, e2, r);
             }
-            *reinterpret_cast<float4*>(wa.tile_loss + 4 * tl) = make_float4(s0, s1, s2, 0.f);
+            if (ln == 0) *reinterpret_cast<float4*>(wa.tile_loss + 4 * tl) = make_float4(s0, s1, s2, 0.f);
         }
         if (!GRAD) {
             __syncthreads();
@@ -332,6 +341,23 @@ __global__ void __launch_bounds__(WIDE_THREADS, 1) k_wide_fb(StepParams sp, Wide
         }
         sync_for_mma();
         record(at + WideAct::DY, DYt, TM * 16 * 2);
+        // rays, depths and the loss terms of this tile are consumed: prefetch the next tile's
+        pre = false;
+        if (has_next) {
+            const ObjBatch& obn = ta.obs[tdn.obj];
+            const int Sn = ta.objs[tdn.obj].S;
+            if (tid < tdn.nr) {
+                const float* rec = ta.pool + (obn.src_off + npick) * REC;
+                float* d = rays + tid * RAYF;
+                cp_async16(d, rec);
+                cp_async16(d + 4, rec + 4);
+                cp_async16(d + 8, rec + 8);
+            }
+            const long long sb = obn.sample_off + (long long)(tdn.ray0 - obn.ray_off) * Sn;
+            for (int i = tid; i < tdn.nr * Sn; i += blockDim.x) cp_async4(tsm + i, ta.tbuf + sb + i);
+            cp_async_commit();
+            pre = true;
+        }
 
         // ---- backward: input gradients ------------------------------------------
         if (tid == 0) {
@@ -370,6 +396,7 @@ __global__ void __launch_bounds__(WIDE_THREADS, 1) k_wide_fb(StepParams sp, Wide
         tc_fence_after();
     }
     if (abort && wpend) mbar_wait(wbar, wphase, MMA_WAIT_LIMIT);
+    cp_async_wait_all();   // prefetches issued before an abort land before the CTA exits
     if (tid == 0) bulk_wait_all();   // every activation record is written before the CTA exits
     tc_fence_before();
     __syncthreads();
