@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_build(BuildArgs a) {
     }
     __syncthreads();
 
-    // ---- reduce work items: (batch index, chunk of REDUCE_CHUNK parameters) --
+    // ---- reduce work items: (object, chunk of REDUCE_CHUNK parameters) -------
     const int nb = a.counts[BC_NB];
     long long icarry = 0;
     for (int base = 0; base < nb; base += BUILD_THREADS) {
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_build(BuildArgs a) {
         if (j < nb) nch = (int)((param_count(a.objs[a.bobj[j]].hidden) + REDUCE_CHUNK - 1) / REDUCE_CHUNK);
         long long tot;
         const long long i0 = icarry + block_scan(nch, &tot, sh);
-        for (int c = 0; c < nch; ++c) a.items[i0 + c] = make_int2(j, c);
+        for (int c = 0; c < nch; ++c) a.items[i0 + c] = make_int2(a.bobj[j], c);   // (object, chunk)
         icarry += tot;
     }
     if (threadIdx.x == 0) a.counts[BC_ITEMS] = (int)icarry;

@@ -97,7 +97,7 @@ struct vmap_ctx {
     int2* items_d = nullptr;
     int* counts_d = nullptr;
     int* sig_d = nullptr;           // inputs of the last batch build ([0] = -1: rebuild)
-    int* done_d = nullptr;          // blocks of the reduce that have finished (reset by the last)
+    int* done_d = nullptr;          // per object: reduce warps that have finished (reset by the last)
     long long build_key = -1;       // launch shape the last build ran with
     float* given_d = nullptr;
     float* loss_d = nullptr;
@@ -440,7 +440,7 @@ vmap_status launch_tiles(vmap_ctx* ctx, int mask) {
 vmap_status launch_reduce(vmap_ctx* ctx, int mode, const float* grad_loss, float* grad_out, float* loss_out,
                           float* dcenter_out) {
     const int pi = prof_begin(ctx, PS_REDUCE);
-    k_reduce<<<ctx->n_sm * 3, REDUCE_THREADS, 0, ctx->stream>>>(ctx->sp, ctx->objs_d, ctx->ob_d, ctx->bobj_d, ctx->items_d,
+    k_reduce<<<ctx->n_sm * 3, REDUCE_THREADS, 0, ctx->stream>>>(ctx->sp, ctx->objs_d, ctx->ob_d, ctx->items_d,
                                                      ctx->counts_d, ctx->part_d, ctx->params_d, ctx->bf16 ? nullptr : ctx->wt_d,
                                                      ctx->m_d, ctx->v_d, ctx->steps_d, ctx->status_d, mode,
                                                      grad_loss, grad_out, loss_out, dcenter_out,
@@ -669,7 +669,7 @@ vmap_status vmap_init_objects(vmap_ctx** out, const vmap_config* cfg, void* cuda
     ALLOC(ctx->items_d, sizeof(int2) * (size_t)K * ((param_count(128) + REDUCE_CHUNK - 1) / REDUCE_CHUNK));
     ALLOC(ctx->counts_d, sizeof(int) * BC_N);
     ALLOC(ctx->sig_d, sizeof(int) * (2 + (size_t)K));
-    ALLOC(ctx->done_d, sizeof(int));
+    ALLOC(ctx->done_d, sizeof(int) * K);
     ALLOC(ctx->given_d, sizeof(float) * REC * (size_t)cfg->max_rays_total);
     ALLOC(ctx->loss_d, sizeof(float) * K);
     ALLOC(ctx->err_d, sizeof(int));
@@ -688,7 +688,7 @@ vmap_status vmap_init_objects(vmap_ctx** out, const vmap_config* cfg, void* cuda
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->n_obj_d, 0, sizeof(int), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->counts_d, 0, sizeof(int) * BC_N, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->sig_d, 0xFF, sizeof(int) * (2 + (size_t)K), ctx->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->done_d, 0, sizeof(int), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->done_d, 0, sizeof(int) * K, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->err_d, 0, sizeof(int), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->img_off_d, 0xFF, sizeof(long long) * K, ctx->stream);
     if (e == cudaSuccess && ctx->act_pp_d) e = cudaMemsetAsync(ctx->act_pp_d, 0, sizeof(unsigned char*), ctx->stream);

@@ -84,15 +84,16 @@ __device__ __forceinline__ long long wt_index(int H, long long p) {
 // a whole warp: lane l sums slots l, l + 32, ... in order, then a fixed
 // butterfly combines the lanes (deterministic).
 // Fixed grid of REDUCE_THREADS-thread blocks; each warp takes half of a
-// reduce work item (batch object, chunk of REDUCE_CHUNK parameters) from the
+// reduce work item (object, chunk of REDUCE_CHUNK parameters) from the
 // builder's list: 128 parameters, four consecutive ones per lane, moved as
 // 16-byte vectors (parameter offsets, slot strides and every width's
 // parameter count are multiples of four). It sums the object's run slots in
 // slot order and, in the same warp, the object's loss terms (lane-strided
 // over runs, then a butterfly); then (RED_ADAM) applies Adam with the
 // object's step count + 1, or (RED_GRAD) writes grad_loss[k] * g. With
-// RED_ADAM and a `done` counter, the last block to finish advances the step
-// count of every object that was trained and resets the counter.
+// RED_ADAM and per-object counters `done` (zero between launches), the last
+// warp of an object to finish (every other one has read the step count)
+// advances the object's step count unless it is frozen, and resets its counter.
 constexpr int REDUCE_THREADS = 256;
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
@@ -100,7 +101,6 @@ __device__ __forceinline__ float& at4(float4& v, int i) { return i == 0 ? v.x : 
 
 __global__ void __launch_bounds__(REDUCE_THREADS, 3) k_reduce(StepParams sp, const ObjDev* __restrict__ objs,
                                                            const ObjBatch* __restrict__ obs,
-                                                           const int* __restrict__ bobj,
                                                            const int2* __restrict__ items,
                                                            const int* __restrict__ counts,
                                                            const float* __restrict__ part, float* params,
@@ -112,15 +112,12 @@ __global__ void __launch_bounds__(REDUCE_THREADS, 3) k_reduce(StepParams sp, con
                                                            float* __restrict__ dcenter_out,
                                                            __nv_bfloat16* img, const long long* __restrict__ img_off,
                                                            int* done) {
-    __shared__ int sh_last;
     const int lane = threadIdx.x & 31;
     const int wpb = blockDim.x >> 5;
     const int n_units = 2 * counts[BC_ITEMS];   // (item, half)
-#pragma unroll 1
-    for (int u = blockIdx.x * wpb + (threadIdx.x >> 5); u < n_units; u += gridDim.x * wpb) {
-        const int2 item = items[u >> 1];
-        const bool head = item.y == 0 && (u & 1) == 0;   // the warp that reports per-object results
-        const int k = bobj[item.x];
+    // one unit: half `half` of chunk `chunk` of object k
+    auto reduce_unit = [&](const int k, const int chunk, const int half) {
+        const bool head = chunk == 0 && half == 0;   // the warp that reports per-object results
         const ObjDev& ob = objs[k];
         const ObjBatch& bt = obs[k];
         const int H = ob.hidden;
@@ -136,7 +133,7 @@ __global__ void __launch_bounds__(REDUCE_THREADS, 3) k_reduce(StepParams sp, con
         }
         const int t1 = mode == RED_ADAM ? steps[k] + 1 : 1;
         const bool frozen = status[k] != 0;
-        const int p = item.y * REDUCE_CHUNK + (u & 1) * (REDUCE_CHUNK / 2) + 4 * lane;
+        const int p = chunk * REDUCE_CHUNK + half * (REDUCE_CHUNK / 2) + 4 * lane;
         const bool act = mode != RED_LOSS && p < P;
         const long long q = ob.param_off + p;
         float4 g = make_float4(0.f, 0.f, 0.f, 0.f), th0 = g, m0 = g, v0 = g;
@@ -182,16 +179,16 @@ __global__ void __launch_bounds__(REDUCE_THREADS, 3) k_reduce(StepParams sp, con
                 for (int c = 0; c < 3; ++c) dcenter_out[3 * k + c] = gl * d[c];
             }
         }
-        if (mode == RED_LOSS) continue;
+        if (mode == RED_LOSS) return;
         if (mode == RED_ADAM && (frozen || !isfinite(L))) {
             if (!frozen && head && lane == 0) status[k] = 1;
-            continue;
+            return;
         }
-        if (!act) continue;
+        if (!act) return;
         if (mode == RED_GRAD) {
 #pragma unroll
             for (int i = 0; i < 4; ++i) grad_out[q + i] = gl * at4(g, i);
-            continue;
+            return;
         }
         const float bc1 = 1.f - powf(sp.beta1, (float)t1);   // Adam bias corrections
         const float bc2 = 1.f - powf(sp.beta2, (float)t1);
@@ -227,24 +224,24 @@ __global__ void __launch_bounds__(REDUCE_THREADS, 3) k_reduce(StepParams sp, con
                 img[img_off[k] + base + cm_off(wn, wk, l == 0 ? DINP : H) / 2] = __float2bfloat16(x);
             }
         }
+    };
+#pragma unroll 1
+    for (int u = blockIdx.x * wpb + (threadIdx.x >> 5); u < n_units; u += gridDim.x * wpb) {
+        const int2 item = items[u >> 1];
+        const int k = item.x;
+        reduce_unit(k, item.y, u & 1);
+        if (mode == RED_ADAM && done) {
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence();
+                const int units = 2 * (int)((param_count(objs[k].hidden) + REDUCE_CHUNK - 1) / REDUCE_CHUNK);
+                if (atomicAdd(done + k, 1) == units - 1) {
+                    done[k] = 0;
+                    if (atomicAdd(status + k, 0) == 0) steps[k] += 1;
+                }
+            }
+        }
     }
-    if (mode != RED_ADAM || !done) return;
-    // the last block to finish (every block has read the step counts it needs)
-    // advances the step count of each trained, unfrozen object
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        sh_last = atomicAdd(done, 1) == (int)gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!sh_last) return;
-    __threadfence();
-    const int nb = counts[BC_NB];
-    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
-        const int k = bobj[j];
-        if (atomicAdd(status + k, 0) == 0) steps[k] += 1;
-    }
-    if (threadIdx.x == 0) *done = 0;
 }
 
 // seeded default init: parameter p draws word p % 4 of Philox block p / 4 with
