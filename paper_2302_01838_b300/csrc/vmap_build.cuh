@@ -39,7 +39,7 @@ struct BuildArgs {
     long long part_base[NCLASS];
     int* bobj;                 // [max_objects] batch object ids
     int* bray;                 // [max_objects] their first batch ray
-    int* ray_bj;               // [max_rays_total] batch index of each batch ray, or NULL
+    int* ray_bj;               // [max_rays_total] object of each batch ray, or NULL
     int2* items;               // reduce work (batch index, chunk)
     int* counts;               // [BC_N]
     int* sig;                  // [2 + max_objects] inputs of the last build (n_obj, given, rays
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_build(BuildArgs a) {
                 a.bobj[j0] = k;
                 a.bray[j0] = (int)ray0;
                 if (a.ray_bj)
-                    for (int i = 0; i < R; ++i) a.ray_bj[ray0 + i] = (int)j0;
+                    for (int i = 0; i < R; ++i) a.ray_bj[ray0 + i] = k;
                 const int rt = rays_per_tile(a, c, S);
                 TileDev* tl = a.tiles + (long long)c * a.tile_cap + tb[c];
                 for (int i = 0; i < nt; ++i) {

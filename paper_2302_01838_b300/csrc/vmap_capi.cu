@@ -88,7 +88,7 @@ struct vmap_ctx {
     int* pick_d = nullptr;
     float* t_d = nullptr;
     int *bobj_d = nullptr, *bray_d = nullptr;
-    int* ray_bj_d = nullptr;        // batch object of each batch ray (written by the builder)
+    int* ray_bj_d = nullptr;        // object of each batch ray (written by the builder)
     TileDev* tiles_d = nullptr;
     int* flags_d = nullptr;
     int tile_cap = 0;

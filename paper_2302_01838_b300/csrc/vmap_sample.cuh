@@ -34,17 +34,15 @@ constexpr int SAMPLE_RAYS_PER_BLOCK = 8;
 
 __global__ void __launch_bounds__(32 * SAMPLE_RAYS_PER_BLOCK) k_sample(
     StepParams sp, const ObjDev* __restrict__ objs, const ObjBatch* __restrict__ obs, const int* __restrict__ bobj,
-    const int* __restrict__ bray_off, const int* __restrict__ ray_bj, const int* __restrict__ counts,
+    const int* __restrict__ bray_off, const int* __restrict__ ray_obj, const int* __restrict__ counts,
     const float* __restrict__ src, int given, const int* __restrict__ steps, int* __restrict__ pick_out,
     float* __restrict__ t_out) {
     const int i = blockIdx.x * SAMPLE_RAYS_PER_BLOCK + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     const int total_rays = counts[BC_RAYS];
-    const int nb = counts[BC_NB];
     if (i >= total_rays) return;
-    // the ray's batch object: from the builder's per-ray table, or by search
-    const int j = ray_bj ? ray_bj[i] : upper_index(bray_off, nb, i);
-    const int k = bobj[j];
+    // the ray's object: from the builder's per-ray table, or by search
+    const int k = ray_obj ? ray_obj[i] : bobj[upper_index(bray_off, counts[BC_NB], i)];
     const ObjDev& ob = objs[k];
     const ObjBatch& bt = obs[k];
     const uint32_t r = (uint32_t)(i - bt.ray_off), step = (uint32_t)steps[k], stream = ob.stream;
@@ -55,9 +53,9 @@ __global__ void __launch_bounds__(32 * SAMPLE_RAYS_PER_BLOCK) k_sample(
     uint4 blk = make_uint4(0u, 0u, 0u, 0u);
     if (lane < nblk) blk = philox4x32_10(make_uint4(r, (uint32_t)lane, step, stream), sp.key0, sp.key1);
     auto word = [&](int w) {   // warp-collective: every lane asks for its own word w
-        const int src = w >> 2, c = w & 3;
-        const uint32_t x = __shfl_sync(0xffffffffu, blk.x, src), y = __shfl_sync(0xffffffffu, blk.y, src);
-        const uint32_t z = __shfl_sync(0xffffffffu, blk.z, src), ww = __shfl_sync(0xffffffffu, blk.w, src);
+        const int sl = w >> 2, c = w & 3;
+        const uint32_t x = __shfl_sync(0xffffffffu, blk.x, sl), y = __shfl_sync(0xffffffffu, blk.y, sl);
+        const uint32_t z = __shfl_sync(0xffffffffu, blk.z, sl), ww = __shfl_sync(0xffffffffu, blk.w, sl);
         return c == 0 ? x : c == 1 ? y : c == 2 ? z : ww;
     };
     // word 0 picks the ray; with caller-given rays it is drawn and dropped so
