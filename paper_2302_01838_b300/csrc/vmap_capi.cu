@@ -319,8 +319,13 @@ WideArgs wide_args(vmap_ctx* ctx) {
     return WideArgs{ta, ctx->img_d, ctx->img_off_d, ctx->err_d, ctx->act_pp_d, ctx->tile_loss_d, 0};
 }
 
+// overlap: with `after_tile` (the previous kernel in the stream is a BF16 tile
+// kernel, which signals its dependents once all its CTAs are resident), the
+// width-128 kernel is launched with programmatic stream serialization, so its
+// CTAs start on SMs as the tile kernel's CTAs finish; it waits for the tile
+// kernel's completion before it exits (the two touch disjoint objects)
 template <int MODE>
-cudaError_t launch_wide_fb(vmap_ctx* ctx) {
+cudaError_t launch_wide_fb(vmap_ctx* ctx, bool after_tile = false) {
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_wide_fb<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -328,8 +333,17 @@ cudaError_t launch_wide_fb(vmap_ctx* ctx) {
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    k_wide_fb<MODE><<<ctx->n_sm * ctx->gmult[3], WIDE_THREADS, WideFbCfg::BYTES, ctx->stream>>>(ctx->sp, wide_args(ctx));
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(ctx->n_sm * ctx->gmult[3]));
+    cfg.blockDim = dim3(WIDE_THREADS);
+    cfg.dynamicSmemBytes = WideFbCfg::BYTES;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = after_tile ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k_wide_fb<MODE>, ctx->sp, wide_args(ctx));
 }
 
 cudaError_t launch_wide_dw(vmap_ctx* ctx, int loss_only) {
@@ -413,13 +427,14 @@ vmap_status launch_build_sample(vmap_ctx* ctx, int given) {
 
 template <int MODE>
 vmap_status launch_tiles(vmap_ctx* ctx, int mask) {
+    bool after_tile = false;   // the last launch in the stream is a BF16 tile kernel
     for (int c = 0; c < NCLASS; ++c) {
         if (!(mask & (1 << c))) continue;
         cudaError_t e;
         if (uses_wide(ctx, c)) {
             constexpr int BM = MODE == MODE_FORWARD ? MODE_FORWARD : MODE_TRAIN;
             int pi = MODE == MODE_TRAIN ? prof_begin(ctx, PS_TILE + c) : -1;
-            e = launch_wide_fb<BM>(ctx);
+            e = launch_wide_fb<BM>(ctx, after_tile && pi < 0);
             prof_end(ctx, pi);
             if (e == cudaSuccess) {
                 pi = MODE == MODE_TRAIN ? prof_begin(ctx, PS_WIDE_DW) : -1;
@@ -430,6 +445,7 @@ vmap_status launch_tiles(vmap_ctx* ctx, int mask) {
             const int pi = MODE == MODE_TRAIN ? prof_begin(ctx, PS_TILE + c) : -1;
             e = launch_class<MODE>(ctx, c);
             prof_end(ctx, pi);
+            after_tile = uses_tc(ctx, c) && pi < 0;
         }
         if (e != cudaSuccess)
             return fail(ctx, VMAP_ERR_CUDA, "tile kernel (H=%d) failed: %s", hidden_of(c), cudaGetErrorString(e));

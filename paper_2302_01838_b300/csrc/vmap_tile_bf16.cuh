@@ -178,6 +178,9 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
     const int q = warp & 3, hf = warp >> 2;   // TMEM lane quadrant, column half
     const int row = q * 32 + lane;            // the sample (or fan-in lane) this thread reads
 
+    // every CTA of this grid is resident once each has passed this point: a
+    // width-128 kernel launched behind it may then take the SMs it frees
+    pdl_launch_dependents();
     // ---- set-up: barrier, tensor memory, constant columns ---------------------
     if (tid == 0) {
         mbar_init(mbar, 1);

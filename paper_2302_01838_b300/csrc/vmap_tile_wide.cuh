@@ -176,9 +176,13 @@ __global__ void __launch_bounds__(WIDE_THREADS, 1) k_wide_fb(StepParams sp, Wide
         tmem_ld_wait();
     };
 
+    // Tile ranges front-loaded: the first n % G CTAs take one tile more. CTAs
+    // start in block order, so when this kernel starts on the SMs that a
+    // preceding tile kernel frees, the CTAs that start last have the least to do.
     const long long n_tiles = *ta.n_tiles;
-    const long long t0 = (long long)blockIdx.x * n_tiles / gridDim.x;
-    const long long t1 = (long long)(blockIdx.x + 1) * n_tiles / gridDim.x;
+    const long long nG = gridDim.x, per = n_tiles / nG, rem = n_tiles % nG, cb = blockIdx.x;
+    const long long t0 = cb < rem ? cb * (per + 1) : rem * (per + 1) + (cb - rem) * per;
+    const long long t1 = t0 + (cb < rem ? per + 1 : per);
 
 #pragma unroll 1
     for (long long tl = t0; tl < t1 && !abort; ++tl) {
@@ -398,6 +402,10 @@ __global__ void __launch_bounds__(WIDE_THREADS, 1) k_wide_fb(StepParams sp, Wide
     if (abort && wpend) mbar_wait(wbar, wphase, MMA_WAIT_LIMIT);
     cp_async_wait_all();   // prefetches issued before an abort land before the CTA exits
     if (tid == 0) bulk_wait_all();   // every activation record is written before the CTA exits
+    // when launched behind a tile kernel (programmatic stream serialization),
+    // this grid completes only after that kernel has: what follows in the
+    // stream sees both
+    pdl_wait();
     tc_fence_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, C::NCOLS);
