@@ -140,23 +140,32 @@ __global__ void __launch_bounds__(WIDE_THREADS, 1) k_wide_fb(StepParams sp, Wide
     bool pre = false;                    // this tile's rays and depths were prefetched
     int npick = 0;                       // pick of the next tile's ray `tid`
 
+    // Every thread waits for an MMA commit by itself (no CTA barrier); a wait
+    // that gave up is agreed on at the next CTA barrier.
+    bool wfail = false;
     auto wait_mma = [&]() {
-        const bool ok = mbar_wait(mbar, phase, MMA_WAIT_LIMIT);
+        wfail |= !mbar_wait(mbar, phase, MMA_WAIT_LIMIT);
         phase ^= 1;
-        if (tid == 0) bulk_wait_read();   // operand tiles may be rewritten after the barrier
-        if (__syncthreads_or(!ok)) {
+        tc_fence_after();
+    };
+    // operand writes and TMEM reads done -> MMA may start. The record copy of the
+    // previous round (the other of the two ping-pong tiles) has finished reading
+    // before the barrier, so that tile may be rewritten in the next round.
+    auto sync_for_mma = [&]() {
+        tmem_ld_wait();
+        fence_async_smem();
+        tc_fence_before();
+        if (tid == 0) bulk_wait_read();
+        if (__syncthreads_or(wfail)) {
             abort = true;
             if (tid == 0) atomicExch(wa.err, 1);
         }
         tc_fence_after();
     };
-    auto sync_for_mma = [&]() {
-        tmem_ld_wait();
-        fence_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-    };
+    // h_{l+1} (forward round l) and dZ_{l+1} (backward round l) alternate between
+    // the two 32 KB tiles: h1, h3, dZ4, dZ2 -> HA; h2, h4, dZ3, dZ1 -> DZ
+    auto hbuf = [&](int l) { return (l & 1) ? DZ : HA; };
+    auto zbuf = [&](int l) { return (l & 1) ? HA : DZ; };
     // the activation record receives an operand tile by one bulk copy (after sync_for_mma)
     auto record = [&](unsigned char* dst, const unsigned char* tile, int bytes) {
         if (tid == 0) {
@@ -234,6 +243,7 @@ __global__ void __launch_bounds__(WIDE_THREADS, 1) k_wide_fb(StepParams sp, Wide
             encode_row_half(sp, x0, x1, x2, m, half, G0, nullptr);
         }
         sync_for_mma();
+        if (abort) break;
         if (GRAD) record(at + WideAct::G0, G0, TM * DINP * 2);
         if (first) {
             const bool ok = mbar_wait(wbar, wphase, MMA_WAIT_LIMIT);
@@ -265,36 +275,46 @@ __global__ void __launch_bounds__(WIDE_THREADS, 1) k_wide_fb(StepParams sp, Wide
         if (abort) break;
 #pragma unroll 1
         for (int l = 0; l < 4; ++l) {
+            unsigned char* hb = hbuf(l);
             float v[32];
             load_acc(v);
-            unsigned bits = 0;
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 float u[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) u[j] = fmaxf(v[8 * c + j] + bsm[l * WH + col0 + 8 * c + j], 0.f);
-                bits |= (unsigned)pos_bits(u, 8 * c);
-                st_bf16x8(HA, cm_off(row, col0 + 8 * c, WH), u);
+                st_bf16x8(hb, cm_off(row, col0 + 8 * c, WH), u);
             }
-            mask[(l * TM + row) * 4 + qc] = bits;
             sync_for_mma();
-            if (GRAD) record(at + WideAct::h(l), HA, TM * WH * 2);
+            if (abort) break;
+            if (GRAD) record(at + WideAct::h(l), hb, TM * WH * 2);
             if (tid == 0) {
                 if (l < 3) {
 #pragma unroll
                     for (int kc = 0; kc < WH / 16; ++kc)
-                        mma_bf16(tmem, desc_kmajor(HA, WH, 16 * kc), desc_kmajor(Whp(l), WH, 16 * kc),
+                        mma_bf16(tmem, desc_kmajor(hb, WH, 16 * kc), desc_kmajor(Whp(l), WH, 16 * kc),
                                  idesc_bf16(TM, WH, 0, 0), kc > 0);
                 } else {
 #pragma unroll
                     for (int kc = 0; kc < WH / 16; ++kc)
-                        mma_bf16(tmem, desc_kmajor(HA, WH, 16 * kc), desc_kmajor(W5, WH, 16 * kc),
+                        mma_bf16(tmem, desc_kmajor(hb, WH, 16 * kc), desc_kmajor(W5, WH, 16 * kc),
                                  idesc_bf16(TM, 16, 0, 0), kc > 0);
                 }
                 mma_commit(mbar);
             }
+            if (GRAD) {
+                // the ReLU mask of h_{l+1} (needed by the backward), from the BF16
+                // tile the MMA is reading, while the MMA runs
+                unsigned bits = 0;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    float a[8];
+                    ld_bf16x8(hb, cm_off(row, col0 + 8 * c, WH), a);
+                    bits |= (unsigned)pos_bits(a, 8 * c);
+                }
+                mask[(l * TM + row) * 4 + qc] = bits;
+            }
             wait_mma();
-            if (abort) break;
         }
         if (abort) break;
         {
@@ -307,7 +327,11 @@ __global__ void __launch_bounds__(WIDE_THREADS, 1) k_wide_fb(StepParams sp, Wide
                 for (int j = 0; j < NOUT; ++j) yb[j * TM + row] = sigmoidf_(v[j] + b5[j]);   // o, c (Eq. 1 heads)
             }
         }
-        __syncthreads();
+        if (__syncthreads_or(wfail)) {
+            abort = true;
+            if (tid == 0) atomicExch(wa.err, 1);
+        }
+        if (abort) break;
 
         // ---- rendering, loss, dL/dy (FP32) ---------------------------------------
         const float invR = 1.f / (float)ta.obs[k].R;
@@ -344,6 +368,7 @@ __global__ void __launch_bounds__(WIDE_THREADS, 1) k_wide_fb(StepParams sp, Wide
             st_bf16x8(DYt, cm_off(r, half * 8, 16), v);
         }
         sync_for_mma();
+        if (abort) break;
         record(at + WideAct::DY, DYt, TM * 16 * 2);
         // rays, depths and the loss terms of this tile are consumed: prefetch the next tile's
         pre = false;
@@ -371,8 +396,8 @@ __global__ void __launch_bounds__(WIDE_THREADS, 1) k_wide_fb(StepParams sp, Wide
 #pragma unroll 1
         for (int l = 3; l >= 0; --l) {
             // accumulator = dZ_{l+2} W_{l+2} (dY W5 for l = 3); dZ_{l+1} = acc * [h_{l+1} > 0]
+            unsigned char* zb = zbuf(l);
             wait_mma();
-            if (abort) break;
             float v[32];
             load_acc(v);
             const unsigned bits = mask[(l * TM + row) * 4 + qc];
@@ -381,15 +406,16 @@ __global__ void __launch_bounds__(WIDE_THREADS, 1) k_wide_fb(StepParams sp, Wide
                 float u[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) u[j] = (bits >> (8 * c + j)) & 1u ? v[8 * c + j] : 0.f;
-                st_bf16x8(DZ, cm_off(row, col0 + 8 * c, WH), u);
+                st_bf16x8(zb, cm_off(row, col0 + 8 * c, WH), u);
             }
             sync_for_mma();
-            record(at + WideAct::dz(l), DZ, TM * WH * 2);
+            if (abort) break;
+            record(at + WideAct::dz(l), zb, TM * WH * 2);
             if (l == 0) break;
             if (tid == 0) {
 #pragma unroll
                 for (int kc = 0; kc < WH / 16; ++kc)
-                    mma_bf16(tmem, desc_kmajor(DZ, WH, 16 * kc), desc_mnmajor(Whp(l - 1), WH, 16 * kc),
+                    mma_bf16(tmem, desc_kmajor(zb, WH, 16 * kc), desc_mnmajor(Whp(l - 1), WH, 16 * kc),
                              idesc_bf16(TM, WH, 0, 1), kc > 0);
                 mma_commit(mbar);
             }
