@@ -346,7 +346,11 @@ cudaError_t launch_wide_fb(vmap_ctx* ctx, bool after_tile = false) {
     return cudaLaunchKernelEx(&cfg, k_wide_fb<MODE>, ctx->sp, wide_args(ctx));
 }
 
-cudaError_t launch_wide_dw(vmap_ctx* ctx, int loss_only) {
+// with `after_fb` (the previous kernel in the stream is k_wide_fb, which
+// signals its dependents once all its CTAs are resident) the weight-gradient
+// kernel is launched with programmatic stream serialization: its set-up runs on
+// SMs k_wide_fb frees, and it waits for k_wide_fb before reading the records
+cudaError_t launch_wide_dw(vmap_ctx* ctx, int loss_only, bool after_fb = false) {
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_wide_dw, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -356,8 +360,17 @@ cudaError_t launch_wide_dw(vmap_ctx* ctx, int loss_only) {
     }
     WideArgs wa = wide_args(ctx);
     wa.loss_only = loss_only;
-    k_wide_dw<<<WJOBS * wide_ranges(ctx), NTHREADS, WideDwCfg::BYTES, ctx->stream>>>(wa);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(WJOBS * wide_ranges(ctx)));
+    cfg.blockDim = dim3(NTHREADS);
+    cfg.dynamicSmemBytes = WideDwCfg::BYTES;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = after_fb ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k_wide_dw, wa);
 }
 
 // one width class of the step's tile kernel (FP32 SIMT, or BF16 tensor cores)
@@ -437,8 +450,9 @@ vmap_status launch_tiles(vmap_ctx* ctx, int mask) {
             e = launch_wide_fb<BM>(ctx, after_tile && pi < 0);
             prof_end(ctx, pi);
             if (e == cudaSuccess) {
+                const bool fb_plain = pi < 0;   // no profiling event between the two launches
                 pi = MODE == MODE_TRAIN ? prof_begin(ctx, PS_WIDE_DW) : -1;
-                e = launch_wide_dw(ctx, BM == MODE_FORWARD);
+                e = launch_wide_dw(ctx, BM == MODE_FORWARD, fb_plain && pi < 0);
                 prof_end(ctx, pi);
             }
         } else {

@@ -124,6 +124,9 @@ __global__ void __launch_bounds__(WIDE_THREADS, 1) k_wide_fb(StepParams sp, Wide
     const int row = q * 32 + (tid & 31);
     const int col0 = qc * 32;
     unsigned char* act = GRAD ? *wa.act : nullptr;
+    // every CTA of this grid is resident once each has passed this point: the
+    // weight-gradient kernel launched behind it may then take freed SMs
+    pdl_launch_dependents();
 
     if (tid == 0) {
         mbar_init(mbar, 1);
@@ -473,6 +476,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_wide_dw(WideArgs wa) {
     const int n = (int)(t1 - t0);
 
     if (wa.loss_only) {
+        pdl_wait();   // the tile losses come from k_wide_fb
         // fold the tile losses of every run into its slot, in tile order
         if (tid == 0) {
             float l0 = 0.f, l1 = 0.f, l2 = 0.f;
@@ -502,6 +506,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_wide_dw(WideArgs wa) {
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    // launched behind k_wide_fb (programmatic stream serialization): the set-up
+    // above overlapped its end; the operand records and tile losses are its
+    pdl_wait();
     const uint32_t tmem = *tslot;
     bool abort = false;
     // thread 0 fills stage i % NST with tile t0 + i
