@@ -99,6 +99,14 @@ struct vmap_ctx {
     int* sig_d = nullptr;           // inputs of the last batch build ([0] = -1: rebuild)
     int* done_d = nullptr;          // per object: reduce warps that have finished (reset by the last)
     long long build_key = -1;       // launch shape the last build ran with
+    // host-side inputs of the last batch build: when none changed, the builder
+    // is not launched (objects frozen on the device since then stay in the
+    // layout; the reduce already leaves them untouched)
+    long long layout_gen = 0;       // bumped by every change of an object's layout fields or status
+    bool built = false;
+    int built_K = -1, built_given = -1;
+    long long built_gen = -1, built_key = -1;
+    std::vector<int> built_req;
     float* given_d = nullptr;
     float* loss_d = nullptr;
     bool batch_ready = false;
@@ -134,7 +142,8 @@ struct vmap_ctx {
     // CUDA graphs (captured on a private stream, replayed on the context stream)
     bool graph_on = false;
     cudaStream_t cap_stream = nullptr;
-    cudaGraphExec_t g_sample[2] = {nullptr, nullptr};   // [given]
+    cudaGraphExec_t g_sample[2] = {nullptr, nullptr};   // [given]: builder + sampler
+    cudaGraphExec_t g_sample_only[2] = {nullptr, nullptr};   // [given]: sampler alone
     cudaGraphExec_t g_train = nullptr;
     int g_classes = -1;                 // class mask the train graph was captured for
 
@@ -218,6 +227,11 @@ void prof_flush(vmap_ctx* ctx) {
 
 void drop_graphs(vmap_ctx* ctx) {
     prof_flush(ctx);
+    for (auto& g : ctx->g_sample_only)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
     for (auto& g : ctx->g_sample)
         if (g) {
             cudaGraphExecDestroy(g);
@@ -237,7 +251,8 @@ vmap_status check_obj(vmap_ctx* ctx, int obj) {
     return VMAP_OK;
 }
 
-vmap_status upload_obj(vmap_ctx* ctx, int k) {
+vmap_status upload_obj(vmap_ctx* ctx, int k, bool layout = true) {
+    if (layout) ++ctx->layout_gen;
     // pageable source: the bytes are staged before the call returns
     CU(cudaMemcpyAsync(ctx->objs_d + k, &ctx->objs[k], sizeof(ObjDev), cudaMemcpyHostToDevice, ctx->stream));
     return VMAP_OK;
@@ -400,7 +415,7 @@ cudaError_t launch_class(vmap_ctx* ctx, int c) {
 int class_mmax(vmap_ctx* ctx, int c) { return uses_tc(ctx, c) || uses_wide(ctx, c) ? TM : mmax_of(c); }
 
 // ---- the step's launches ------------------------------------------------------
-vmap_status launch_build_sample(vmap_ctx* ctx, int given) {
+vmap_status launch_build_sample(vmap_ctx* ctx, int given, bool build = true) {
     BuildArgs a{};
     a.objs = ctx->objs_d;
     a.ob = ctx->ob_d;
@@ -424,10 +439,13 @@ vmap_status launch_build_sample(vmap_ctx* ctx, int given) {
     a.items = ctx->items_d;
     a.counts = ctx->counts_d;
     a.sig = ctx->sig_d;
-    int pi = prof_begin(ctx, PS_BUILD);
-    k_build<<<1, BUILD_THREADS, 0, ctx->stream>>>(a);
-    prof_end(ctx, pi);
-    CHECK_LAUNCH("k_build");
+    int pi = -1;
+    if (build) {
+        pi = prof_begin(ctx, PS_BUILD);
+        k_build<<<1, BUILD_THREADS, 0, ctx->stream>>>(a);
+        prof_end(ctx, pi);
+        CHECK_LAUNCH("k_build");
+    }
     const int blocks = (ctx->cfg.max_rays_total + SAMPLE_RAYS_PER_BLOCK - 1) / SAMPLE_RAYS_PER_BLOCK;
     pi = prof_begin(ctx, PS_SAMPLE);
     k_sample<<<blocks, 32 * SAMPLE_RAYS_PER_BLOCK, 0, ctx->stream>>>(ctx->sp, ctx->objs_d, ctx->ob_d, ctx->bobj_d, ctx->bray_d,
@@ -571,20 +589,35 @@ vmap_status sample_impl(vmap_ctx* ctx, const int* rays_per_object, const float* 
         CU(cudaMemsetAsync(ctx->sig_d, 0xFF, sizeof(int), ctx->stream));
         ctx->build_key = key;
     }
-    ctx->req_h.assign(rays_per_object, rays_per_object + K);
-    if (K) CU(cudaMemcpyAsync(ctx->req_d, ctx->req_h.data(), sizeof(int) * K, cudaMemcpyHostToDevice, ctx->stream));
+    const int gi = given ? 1 : 0;
+    // the layout depends on (objects, their layout fields and status, rays per
+    // object, given or pool rays, launch shape): skip the builder when the host
+    // changed none of them since the last build
+    const bool same = ctx->built && ctx->built_K == K && ctx->built_given == gi && ctx->built_gen == ctx->layout_gen &&
+                      ctx->built_key == key && std::equal(rays_per_object, rays_per_object + K, ctx->built_req.begin());
+    if (!same) {
+        ctx->req_h.assign(rays_per_object, rays_per_object + K);
+        if (K) CU(cudaMemcpyAsync(ctx->req_d, ctx->req_h.data(), sizeof(int) * K, cudaMemcpyHostToDevice, ctx->stream));
+    }
     ctx->batch_given = given != nullptr;
     if (given && rays) CU(cudaMemcpyAsync(ctx->given_d, given, sizeof(float) * REC * rays, kind, ctx->stream));
-    const int gi = given ? 1 : 0;
+    const bool build = !same;
     if (ctx->graph_on) {
-        if (!ctx->g_sample[gi]) {
-            vmap_status s = capture(ctx, &ctx->g_sample[gi], [&] { return launch_build_sample(ctx, gi); });
+        cudaGraphExec_t* g = build ? &ctx->g_sample[gi] : &ctx->g_sample_only[gi];
+        if (!*g) {
+            vmap_status s = capture(ctx, g, [&] { return launch_build_sample(ctx, gi, build); });
             if (s) return s;
         }
-        if (vmap_status s = replay(ctx, ctx->g_sample[gi], PS_GRAPH_SAMPLE)) return s;
+        if (vmap_status s = replay(ctx, *g, PS_GRAPH_SAMPLE)) return s;
     } else {
-        if (vmap_status s = launch_build_sample(ctx, gi)) return s;
+        if (vmap_status s = launch_build_sample(ctx, gi, build)) return s;
     }
+    ctx->built = true;
+    ctx->built_K = K;
+    ctx->built_given = gi;
+    ctx->built_gen = ctx->layout_gen;
+    ctx->built_key = key;
+    ctx->built_req.assign(rays_per_object, rays_per_object + K);
     ctx->total_rays = (int)rays;          // upper bounds until read back (frozen objects drop out)
     ctx->total_samples = samples;
     ctx->batch_ready = true;
@@ -811,6 +844,7 @@ vmap_status vmap_add_object(vmap_ctx* ctx, const vmap_object_desc* d, const floa
     CU(cudaMemsetAsync(ctx->v_d + poff, 0, sizeof(float) * P, ctx->stream));
     CU(cudaMemsetAsync(ctx->steps_d + id, 0, sizeof(int), ctx->stream));
     CU(cudaMemsetAsync(ctx->status_d + id, 0, sizeof(int), ctx->stream));
+    ++ctx->layout_gen;
     CU(cudaMemsetAsync(ctx->req_d + id, 0, sizeof(int), ctx->stream));
     ctx->param_used = poff + P;
     ctx->wt_used = woff + wt_count(d->hidden);
@@ -1125,7 +1159,7 @@ vmap_status vmap_set_object_center(vmap_ctx* ctx, int obj, const float* center) 
     if (vmap_status s = check_obj(ctx, obj)) return s;
     if (!center) return fail(ctx, VMAP_ERR_ARG, "null center");
     for (int a = 0; a < 3; ++a) ctx->objs[obj].c[a] = center[a];
-    return upload_obj(ctx, obj);
+    return upload_obj(ctx, obj, false);   // the centre is not a layout input
 }
 
 vmap_status vmap_object_info(vmap_ctx* ctx, int obj, int* hidden, int* param_count_out, long long* param_offset,
