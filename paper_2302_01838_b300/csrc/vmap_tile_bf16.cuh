@@ -200,6 +200,7 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
     uint32_t phase = 0, wphase = 0, phase2 = 0;
     bool abort = false, wpend = false;   // wpend: a weight copy was issued and not yet seen complete
     bool pre = false;                    // this tile's rays and depths were prefetched
+    bool dwpend = false;                 // the last tile's dW1/dW2 MMAs were issued and not yet waited for
     int npick = 0;                       // pick of the next tile's ray `tid`
 
     // Every thread waits for an MMA commit by itself (no CTA barrier, so a
@@ -325,6 +326,16 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
             for (int i = tid; i < 4 * H + NOUT; i += blockDim.x) bsm[i] = P[b_off(H, i / H) + i % H];
         }
         __syncthreads();
+        // the previous tile's last weight-gradient MMAs read G0: they ran during
+        // this tile's set-up above and must be done before G0 is rewritten
+        auto wait_dw12 = [&]() {
+            wait_mma();
+            wfail |= !mbar_wait(mbar2, phase2, MMA_WAIT_LIMIT);
+            phase2 ^= 1;
+            tc_fence_after();
+            dwpend = false;
+        };
+        if (dwpend) wait_dw12();
         // ---- points and encoding -> G0 (BF16; two threads per sample, each
         // forms the sample's normalised point itself) ------------------------------
         for (int f = tid; f < 2 * TM; f += blockDim.x) {
@@ -555,16 +566,21 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
             issue_dw(C::C_DW1, G0, DINP, DZp(0), H, H);              // dW1^T += enc^T dZ1
             mma_commit(mbar2);
         }
-        wait_mma();
-        wfail |= !mbar_wait(mbar2, phase2, MMA_WAIT_LIMIT);
-        phase2 ^= 1;
-        tc_fence_after();
-        agree();
-        if (abort) break;
-        if (last) flush_run(td.part);
+        dwpend = true;
+        if (last) {   // the run's gradient leaves TMEM: wait for its last MMAs now
+            wait_dw12();
+            agree();
+            if (abort) break;
+            flush_run(td.part);
+        }
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
+    }
+    // the range's last tile ends a run, so nothing is pending unless a wait gave up
+    if (dwpend) {
+        mbar_wait(mbar, phase, MMA_WAIT_LIMIT);
+        mbar_wait(mbar2, phase2, MMA_WAIT_LIMIT);
     }
     // a weight copy whose wait gave up may still be in flight: give it one more bounded wait
     if (abort && wpend) mbar_wait(wbar, wphase, MMA_WAIT_LIMIT);
