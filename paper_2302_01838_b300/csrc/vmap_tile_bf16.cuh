@@ -50,10 +50,10 @@ template <int H> struct Bf16Cfg {
     static constexpr int WIMG_BYTES = W1B + 3 * WHB + W5B;
     static constexpr int GUARD = WIMG + WIMG_BYTES;               // tail room for MN-major over-reads
     static constexpr int F32 = GUARD + 4096;
-    static constexpr int TSO = F32;                               // [128] sample depths
-    static constexpr int YB = TSO + TM * 4;                       // [4][128]
-    static constexpr int RAYS = YB + 4 * TM * 4;                  // [32][16]
-    static constexpr int LOSS = RAYS + RTMAX * RAYF * 4;          // [RTMAX][3] run loss sums per ray slot
+    static constexpr int TSO = F32;                               // [2][128] sample depths (this tile, next tile)
+    static constexpr int YB = TSO + 2 * TM * 4;                   // [4][128]
+    static constexpr int RAYS = YB + 4 * TM * 4;                  // [2][32][16] ray records (this tile, next tile)
+    static constexpr int LOSS = RAYS + 2 * RTMAX * RAYF * 4;      // [RTMAX][3] run loss sums per ray slot
     static constexpr int BIAS = LOSS + RTMAX * 3 * 4;             // [4][H] + [NOUT] f32 biases of the run's object
     static constexpr int MBAR = BIAS + (4 * H + 16) * 4;
     static constexpr int WBAR = MBAR + 8;                         // weight image loaded
@@ -165,9 +165,7 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
     unsigned char* W1 = sm + C::WIMG;
     auto Whp = [&](int l) { return W1 + C::W1B + l * C::WHB; };
     unsigned char* W5 = W1 + C::W1B + 3 * C::WHB;
-    float* tsm = reinterpret_cast<float*>(sm + C::TSO);
     float* yb = reinterpret_cast<float*>(sm + C::YB);
-    float* rays = reinterpret_cast<float*>(sm + C::RAYS);
     float* lossacc = reinterpret_cast<float*>(sm + C::LOSS);
     float* bsm = reinterpret_cast<float*>(sm + C::BIAS);
     uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + C::MBAR);
@@ -199,7 +197,10 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
     const uint32_t tmem = *tslot;
     uint32_t phase = 0, wphase = 0, phase2 = 0;
     bool abort = false, wpend = false;   // wpend: a weight copy was issued and not yet seen complete
-    bool pre = false;                    // this tile's rays and depths were prefetched
+    // the ray records and depths of consecutive tiles alternate between two
+    // buffers, so the next tile's are prefetched (cp.async) during this tile's forward
+    bool pre_next = false;               // the next tile's rays and depths were prefetched
+    int bufi = 1;
     bool dwpend = false;                 // the last tile's dW1/dW2 MMAs were issued and not yet waited for
     int npick = 0;                       // pick of the next tile's ray `tid`
 
@@ -291,6 +292,11 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
 
 #pragma unroll 1
     for (long long tl = t0; tl < t1 && !abort; ++tl) {
+        bufi ^= 1;
+        const bool pre = pre_next;   // this tile's rays and depths were prefetched
+        pre_next = false;
+        float* tsm = reinterpret_cast<float*>(sm + C::TSO) + bufi * TM;
+        float* rays = reinterpret_cast<float*>(sm + C::RAYS) + bufi * (RTMAX * RAYF);
         const TileDev td = ta.tiles[tl];
         const int k = td.obj, nr = td.nr;
         const bool first = tl == t0 || ta.tiles[tl - 1].obj != k;
@@ -303,7 +309,7 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
 
         // ---- rays, depths, points; weights at the start of a run ---------------
         // (after the first tile of a training range, the previous tile's
-        // backward already brought this tile's rays and depths in by cp.async)
+        // forward already started this tile's rays and depths by cp.async)
         if (!pre) {
             for (int r = tid; r < nr; r += blockDim.x) {
                 const float* rec = ta.pool + (ta.obs[k].src_off + ta.pick[td.ray0 + r]) * REC;
@@ -374,7 +380,8 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
             mma_commit(mbar);
         }
         constexpr int NC = H / 2;
-        // the next tile of this range: its picks now, its rays and depths during the backward
+        // the next tile of this range: its picks now, its rays and depths (into the
+        // other buffers) once the picks have arrived
         const bool has_next = GRAD && tl + 1 < t1;
         TileDev tdn{};
         if (has_next) {
@@ -383,6 +390,23 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
         }
         wait_mma();
         if (abort) break;
+        if (has_next) {
+            const ObjBatch& obn = ta.obs[tdn.obj];
+            const int Sn = ta.objs[tdn.obj].S;
+            float* rays_n = reinterpret_cast<float*>(sm + C::RAYS) + (bufi ^ 1) * (RTMAX * RAYF);
+            float* tsm_n = reinterpret_cast<float*>(sm + C::TSO) + (bufi ^ 1) * TM;
+            if (tid < tdn.nr) {
+                const float* rec = ta.pool + (obn.src_off + npick) * REC;
+                float* d = rays_n + tid * RAYF;
+                cp_async16(d, rec);
+                cp_async16(d + 4, rec + 4);
+                cp_async16(d + 8, rec + 8);
+            }
+            const long long sb = obn.sample_off + (long long)(tdn.ray0 - obn.ray_off) * Sn;
+            if (tid < tdn.nr * Sn) cp_async4(tsm_n + tid, ta.tbuf + sb + tid);
+            cp_async_commit();
+            pre_next = true;
+        }
 #pragma unroll 1
         for (int l = 0; l < 4; ++l) {
             // epilogue of layer l + 1: bias, ReLU, BF16 -> HA[l]
@@ -461,23 +485,6 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
         }
         sync_for_mma();
         if (abort) break;
-        // rays, depths and the loss terms of this tile are consumed: prefetch the next tile's
-        pre = false;
-        if (has_next) {
-            const ObjBatch& obn = ta.obs[tdn.obj];
-            const int Sn = ta.objs[tdn.obj].S;
-            if (tid < tdn.nr) {
-                const float* rec = ta.pool + (obn.src_off + npick) * REC;
-                float* d = rays + tid * RAYF;
-                cp_async16(d, rec);
-                cp_async16(d + 4, rec + 4);
-                cp_async16(d + 8, rec + 8);
-            }
-            const long long sb = obn.sample_off + (long long)(tdn.ray0 - obn.ray_off) * Sn;
-            if (tid < tdn.nr * Sn) cp_async4(tsm + tid, ta.tbuf + sb + tid);
-            cp_async_commit();
-            pre = true;
-        }
 
         // ---- backward -------------------------------------------------------------
         // The input-gradient chain dZ4 -> dZ3 -> dZ2 -> dZ1 is the critical path:
