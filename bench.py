@@ -277,8 +277,7 @@ def timed_steps(vm, R, steps, flush, loss):
     for i in range(steps):
         flush.fill_(float(i))
         ev[i][0].record()
-        vm.sample_rays(R)
-        vm.train_step(loss)
+        vm.step(R, loss)   # sample_rays + train_step as one launch sequence
         ev[i][1].record()
     torch.cuda.synchronize()
     return sum(a.elapsed_time(b) for a, b in ev)
@@ -328,8 +327,7 @@ def run_ours(args):
 
     # ---- profiled kernel-by-kernel pass: per-kernel device time ----------------
     for _ in range(3):
-        vm.sample_rays(R)
-        vm.train_step(loss)
+        vm.step(R, loss)
     vm.profile_reset()
     vm.profile_enable(True)
     timed_steps(vm, R, args.prof_steps, flush, loss)
@@ -341,8 +339,7 @@ def run_ours(args):
     if not args.no_graph:
         vm.set_graph(True)
     for _ in range(max(args.warmup, 3)):
-        vm.sample_rays(R)
-        vm.train_step(loss)
+        vm.step(R, loss)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -384,8 +381,7 @@ def run_ours(args):
         if not args.no_graph:
             v32.set_graph(True)
         for _ in range(3):
-            v32.sample_rays(R)
-            v32.train_step(loss)
+            v32.step(R, loss)
         ms32 = sharding.max_over_ranks(timed_steps(v32, R, args.fp32_steps, flush, loss))
         v32.close()
         fp32 = {"value": world * sps * args.fp32_steps / (ms32 * 1e-3), "unit": UNIT,

@@ -159,6 +159,13 @@ vmap_status vmap_train_step_host(vmap_ctx* ctx, const float* rays, const int* ra
  * vmap_sync_status); the others are unaffected. */
 vmap_status vmap_train_step(vmap_ctx* ctx, float* out_loss);
 
+/* vmap_sample_rays(ctx, rays_per_object) followed by vmap_train_step(ctx,
+ * out_loss), with the same results, issued as one launch sequence (in graph
+ * mode one replay): the step's first tile kernel is launched behind the
+ * sampler (programmatic dependent launch) and waits for it before reading
+ * the batch. Arguments, ownership and errors as for the two calls. */
+vmap_status vmap_step(vmap_ctx* ctx, const int* rays_per_object, float* out_loss);
+
 /* Loss of the current batch without changing any state.
  * out_loss: DEVICE [n_objects] (NaN for objects not in the batch). */
 vmap_status vmap_forward(vmap_ctx* ctx, float* out_loss);

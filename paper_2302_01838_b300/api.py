@@ -163,6 +163,12 @@ class VMap:
         self._check(self.lib.vmap_train_step(self.h, _ptr(out_loss)))
         return out_loss
 
+    def step(self, rays_per_object, out_loss=None):
+        """sample_rays(rays_per_object) then train_step(out_loss), as one launch sequence."""
+        arr = (ctypes.c_int * len(rays_per_object))(*[int(r) for r in rays_per_object])
+        self._check(self.lib.vmap_step(self.h, arr, _ptr(out_loss)))
+        return out_loss
+
     def forward(self, out_loss):
         self._check(self.lib.vmap_forward(self.h, _ptr(out_loss)))
         return out_loss

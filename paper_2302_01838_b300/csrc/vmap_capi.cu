@@ -125,6 +125,10 @@ struct vmap_ctx {
     long long img_used = 0, img_cap = 0;
     std::vector<long long> img_off;
     int* err_d = nullptr;   // set by a kernel whose bounded wait gave up
+    // the training step's second loss destination (the caller's out_loss): its
+    // address lives on the device, so a captured step writes wherever it points
+    float** loss_pp_d = nullptr;
+    float* loss_user_h = nullptr;   // the address loss_pp_d holds
     // width-128 tensor-core path: per-tile activation records, grown on demand;
     // kernels read the buffer's address from act_pp_d, so captured graphs survive a regrowth
     unsigned char* act_d = nullptr;
@@ -145,6 +149,8 @@ struct vmap_ctx {
     cudaGraphExec_t g_sample[2] = {nullptr, nullptr};   // [given]: builder + sampler
     cudaGraphExec_t g_sample_only[2] = {nullptr, nullptr};   // [given]: sampler alone
     cudaGraphExec_t g_train = nullptr;
+    cudaGraphExec_t g_step[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [given][build]: sampler + step
+    int g_step_classes[2][2] = {{-1, -1}, {-1, -1}};
     int g_classes = -1;                 // class mask the train graph was captured for
 
     // profiling
@@ -152,6 +158,9 @@ struct vmap_ctx {
     std::vector<cudaEvent_t> ev_free;
     std::vector<ProfPair> pending;
     bool capturing = false;
+    // the sampler was the stream's last launch (one step's sequence, no profiling
+    // event between): the step's first BF16 tile kernel starts behind it
+    bool after_sample = false;
     double prof_ms[PS_N] = {0};
     long long prof_n[PS_N] = {0};
 };
@@ -242,6 +251,12 @@ void drop_graphs(vmap_ctx* ctx) {
         ctx->g_train = nullptr;
     }
     ctx->g_classes = -1;
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+            if (ctx->g_step[i][j]) cudaGraphExecDestroy(ctx->g_step[i][j]);
+            ctx->g_step[i][j] = nullptr;
+            ctx->g_step_classes[i][j] = -1;
+        }
 }
 
 vmap_status check_obj(vmap_ctx* ctx, int obj) {
@@ -313,8 +328,14 @@ cudaError_t launch_tile_c(int c, int grid, cudaStream_t st, const StepParams& sp
     }
 }
 
+// with `after_sample` (the previous kernel in the stream is the sampler, which
+// signals its dependents at its start) the tile kernel is launched with
+// programmatic stream serialization: its set-up and first tile records run on
+// SMs the sampler's last blocks free, and it waits for the sampler before
+// reading the picks and depths
 template <int H, int MODE>
-cudaError_t launch_tile_bf16(int grid, cudaStream_t st, const StepParams& sp, const Bf16Args& ba) {
+cudaError_t launch_tile_bf16(int grid, cudaStream_t st, const StepParams& sp, const Bf16Args& ba,
+                             bool after_sample = false) {
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_tile_bf16<H, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -323,8 +344,17 @@ cudaError_t launch_tile_bf16(int grid, cudaStream_t st, const StepParams& sp, co
         attr_set = true;
     }
     if (grid <= 0) return cudaSuccess;
-    k_tile_bf16<H, MODE><<<grid, NTHREADS, Bf16Cfg<H>::BYTES, st>>>(sp, ba);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(NTHREADS);
+    cfg.dynamicSmemBytes = Bf16Cfg<H>::BYTES;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = after_sample ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k_tile_bf16<H, MODE>, sp, ba);
 }
 
 WideArgs wide_args(vmap_ctx* ctx) {
@@ -390,7 +420,7 @@ cudaError_t launch_wide_dw(vmap_ctx* ctx, int loss_only, bool after_fb = false) 
 
 // one width class of the step's tile kernel (FP32 SIMT, or BF16 tensor cores)
 template <int MODE>
-cudaError_t launch_class(vmap_ctx* ctx, int c) {
+cudaError_t launch_class(vmap_ctx* ctx, int c, bool after_sample = false) {
     TileArgs ta = base_args(ctx);
     ta.tiles = ctx->tiles_d + (long long)c * ctx->tile_cap;
     ta.n_tiles = ctx->counts_d + BC_TILES + c;
@@ -404,9 +434,9 @@ cudaError_t launch_class(vmap_ctx* ctx, int c) {
         constexpr int BM = MODE == MODE_FORWARD ? MODE_FORWARD : MODE_TRAIN;
         Bf16Args ba{ta, ctx->img_d, ctx->img_off_d, ctx->err_d};
         switch (c) {
-            case 0: return launch_tile_bf16<16, BM>(grid, ctx->stream, ctx->sp, ba);
-            case 1: return launch_tile_bf16<32, BM>(grid, ctx->stream, ctx->sp, ba);
-            default: return launch_tile_bf16<64, BM>(grid, ctx->stream, ctx->sp, ba);
+            case 0: return launch_tile_bf16<16, BM>(grid, ctx->stream, ctx->sp, ba, after_sample);
+            case 1: return launch_tile_bf16<32, BM>(grid, ctx->stream, ctx->sp, ba, after_sample);
+            default: return launch_tile_bf16<64, BM>(grid, ctx->stream, ctx->sp, ba, after_sample);
         }
     }
     return launch_tile_c<MODE>(c, grid, ctx->stream, ctx->sp, ta);
@@ -459,9 +489,13 @@ vmap_status launch_build_sample(vmap_ctx* ctx, int given, bool build = true) {
 template <int MODE>
 vmap_status launch_tiles(vmap_ctx* ctx, int mask) {
     bool after_tile = false;   // the last launch in the stream is a BF16 tile kernel
+    bool after_sample = ctx->after_sample;   // ... the sampler
+    ctx->after_sample = false;
     for (int c = 0; c < NCLASS; ++c) {
         if (!(mask & (1 << c))) continue;
         cudaError_t e;
+        const bool after_sample_c = after_sample;   // only the first launch follows the sampler
+        after_sample = false;
         if (uses_wide(ctx, c)) {
             constexpr int BM = MODE == MODE_FORWARD ? MODE_FORWARD : MODE_TRAIN;
             int pi = MODE == MODE_TRAIN ? prof_begin(ctx, PS_TILE + c) : -1;
@@ -475,7 +509,7 @@ vmap_status launch_tiles(vmap_ctx* ctx, int mask) {
             }
         } else {
             const int pi = MODE == MODE_TRAIN ? prof_begin(ctx, PS_TILE + c) : -1;
-            e = launch_class<MODE>(ctx, c);
+            e = launch_class<MODE>(ctx, c, after_sample_c && uses_tc(ctx, c) && pi < 0);
             prof_end(ctx, pi);
             after_tile = uses_tc(ctx, c) && pi < 0;
         }
@@ -486,24 +520,36 @@ vmap_status launch_tiles(vmap_ctx* ctx, int mask) {
 }
 
 vmap_status launch_reduce(vmap_ctx* ctx, int mode, const float* grad_loss, float* grad_out, float* loss_out,
-                          float* dcenter_out) {
+                          float* dcenter_out, bool train = false) {
     const int pi = prof_begin(ctx, PS_REDUCE);
     k_reduce<<<ctx->n_sm * 3, REDUCE_THREADS, 0, ctx->stream>>>(ctx->sp, ctx->objs_d, ctx->ob_d, ctx->items_d,
                                                      ctx->counts_d, ctx->part_d, ctx->params_d, ctx->bf16 ? nullptr : ctx->wt_d,
                                                      ctx->m_d, ctx->v_d, ctx->steps_d, ctx->status_d, mode,
                                                      grad_loss, grad_out, loss_out, dcenter_out,
                                                      ctx->bf16 ? ctx->img_d : nullptr, ctx->img_off_d,
-                                                     ctx->done_d);
+                                                     ctx->done_d, train ? ctx->n_obj_d : nullptr,
+                                                     train ? ctx->loss_pp_d : nullptr);
     prof_end(ctx, pi);
     CHECK_LAUNCH("k_reduce");
     return VMAP_OK;
 }
 
+// point the training step's second loss destination at `out` (NULL: none)
+vmap_status set_loss_dest(vmap_ctx* ctx, float* out) {
+    if (out != ctx->loss_user_h) {   // pageable source: staged before the call returns
+        ctx->loss_user_h = out;
+        CU(cudaMemcpyAsync(ctx->loss_pp_d, &ctx->loss_user_h, sizeof(float*), cudaMemcpyHostToDevice, ctx->stream));
+    }
+    return VMAP_OK;
+}
+
+// The reduce writes every object's loss (NaN outside the batch) to loss_d and
+// to the caller's buffer whose address loss_pp_d holds: no fill before the
+// step and no copy after it.
 vmap_status launch_train(vmap_ctx* ctx, int mask) {
-    CU(cudaMemsetAsync(ctx->loss_d, 0xFF, sizeof(float) * ctx->cfg.max_objects, ctx->stream));
     if (vmap_status s = launch_tiles<MODE_TRAIN>(ctx, mask)) return s;
-    // the reduce's last block advances the step counts
-    return launch_reduce(ctx, RED_ADAM, nullptr, nullptr, ctx->loss_d, nullptr);
+    // the last warp of each object advances its step count
+    return launch_reduce(ctx, RED_ADAM, nullptr, nullptr, ctx->loss_d, nullptr, true);
 }
 
 // capture fn() into an executable graph on the context stream
@@ -560,7 +606,15 @@ vmap_status grow_act(vmap_ctx* ctx, long long need) {
     return VMAP_OK;
 }
 
-vmap_status sample_impl(vmap_ctx* ctx, const int* rays_per_object, const float* given, cudaMemcpyKind kind) {
+// what sample_plan settles on the host before a batch's launches
+struct SamplePlan {
+    int K = 0, gi = 0;
+    bool build = false;
+    long long key = 0, rays = 0, samples = 0;
+};
+
+vmap_status sample_plan(vmap_ctx* ctx, const int* rays_per_object, const float* given, cudaMemcpyKind kind,
+                        SamplePlan& sp) {
     if (!ctx || !rays_per_object) return fail(ctx, VMAP_ERR_ARG, "null argument");
     const int K = (int)ctx->objs.size();
     long long rays = 0, samples = 0;
@@ -601,26 +655,42 @@ vmap_status sample_impl(vmap_ctx* ctx, const int* rays_per_object, const float* 
     }
     ctx->batch_given = given != nullptr;
     if (given && rays) CU(cudaMemcpyAsync(ctx->given_d, given, sizeof(float) * REC * rays, kind, ctx->stream));
-    const bool build = !same;
+    sp.K = K;
+    sp.gi = gi;
+    sp.build = !same;
+    sp.key = key;
+    sp.rays = rays;
+    sp.samples = samples;
+    return VMAP_OK;
+}
+
+// the host's record of the batch whose launches were just issued
+void sample_done(vmap_ctx* ctx, const int* rays_per_object, const SamplePlan& sp) {
+    ctx->built = true;
+    ctx->built_K = sp.K;
+    ctx->built_given = sp.gi;
+    ctx->built_gen = ctx->layout_gen;
+    ctx->built_key = sp.key;
+    ctx->built_req.assign(rays_per_object, rays_per_object + sp.K);
+    ctx->total_rays = (int)sp.rays;          // upper bounds until read back (frozen objects drop out)
+    ctx->total_samples = sp.samples;
+    ctx->batch_ready = true;
+}
+
+vmap_status sample_impl(vmap_ctx* ctx, const int* rays_per_object, const float* given, cudaMemcpyKind kind) {
+    SamplePlan sp;
+    if (vmap_status s = sample_plan(ctx, rays_per_object, given, kind, sp)) return s;
     if (ctx->graph_on) {
-        cudaGraphExec_t* g = build ? &ctx->g_sample[gi] : &ctx->g_sample_only[gi];
+        cudaGraphExec_t* g = sp.build ? &ctx->g_sample[sp.gi] : &ctx->g_sample_only[sp.gi];
         if (!*g) {
-            vmap_status s = capture(ctx, g, [&] { return launch_build_sample(ctx, gi, build); });
+            vmap_status s = capture(ctx, g, [&] { return launch_build_sample(ctx, sp.gi, sp.build); });
             if (s) return s;
         }
         if (vmap_status s = replay(ctx, *g, PS_GRAPH_SAMPLE)) return s;
     } else {
-        if (vmap_status s = launch_build_sample(ctx, gi, build)) return s;
+        if (vmap_status s = launch_build_sample(ctx, sp.gi, sp.build)) return s;
     }
-    ctx->built = true;
-    ctx->built_K = K;
-    ctx->built_given = gi;
-    ctx->built_gen = ctx->layout_gen;
-    ctx->built_key = key;
-    ctx->built_req.assign(rays_per_object, rays_per_object + K);
-    ctx->total_rays = (int)rays;          // upper bounds until read back (frozen objects drop out)
-    ctx->total_samples = samples;
-    ctx->batch_ready = true;
+    sample_done(ctx, rays_per_object, sp);
     return VMAP_OK;
 }
 
@@ -692,6 +762,13 @@ vmap_status vmap_init_objects(vmap_ctx** out, const vmap_config* cfg, void* cuda
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->device);
     if (e != cudaSuccess) return bail(VMAP_ERR_CUDA);
+    // the step's small kernels run between kernels that take most of an SM's
+    // shared memory: with the same carveout no SM reconfigures its L1/shared
+    // split (an idle gap of microseconds) at each of their boundaries
+    for (const void* f : {(const void*)k_sample, (const void*)k_reduce, (const void*)k_build}) {
+        e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return bail(VMAP_ERR_CUDA);
+    }
 #define ALLOC(ptr, bytes)                                                                      \
     do {                                                                                       \
         e = cudaMalloc((void**)&(ptr), (bytes));                                               \
@@ -735,6 +812,7 @@ vmap_status vmap_init_objects(vmap_ctx** out, const vmap_config* cfg, void* cuda
     ALLOC(ctx->done_d, sizeof(int) * K);
     ALLOC(ctx->given_d, sizeof(float) * REC * (size_t)cfg->max_rays_total);
     ALLOC(ctx->loss_d, sizeof(float) * K);
+    ALLOC(ctx->loss_pp_d, sizeof(float*));
     ALLOC(ctx->err_d, sizeof(int));
     ALLOC(ctx->img_off_d, sizeof(long long) * K);
     if (ctx->bf16) {
@@ -755,6 +833,7 @@ vmap_status vmap_init_objects(vmap_ctx** out, const vmap_config* cfg, void* cuda
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->err_d, 0, sizeof(int), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->img_off_d, 0xFF, sizeof(long long) * K, ctx->stream);
     if (e == cudaSuccess && ctx->act_pp_d) e = cudaMemsetAsync(ctx->act_pp_d, 0, sizeof(unsigned char*), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->loss_pp_d, 0, sizeof(float*), ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return bail(VMAP_ERR_CUDA);
     *out = ctx;
@@ -771,7 +850,7 @@ vmap_status vmap_destroy(vmap_ctx* ctx) {
                     ctx->t_d,      ctx->bobj_d,   ctx->bray_d,   ctx->tiles_d, ctx->flags_d,  ctx->part_d,
                     ctx->items_d,  ctx->counts_d, ctx->given_d,  ctx->loss_d,  ctx->err_d,  ctx->img_off_d,
                     ctx->img_d,    ctx->act_d,    ctx->act_pp_d, ctx->tile_loss_d, ctx->sig_d,  ctx->done_d,
-                    ctx->scene_d,  ctx->ray_bj_d};
+                    ctx->scene_d,  ctx->ray_bj_d, ctx->loss_pp_d};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& p : ctx->pending) {
@@ -867,10 +946,56 @@ vmap_status vmap_sample_rays_given(vmap_ctx* ctx, const float* rays, const int* 
     return sample_impl(ctx, rays_per_object, rays, cudaMemcpyDeviceToDevice);
 }
 
+}  // extern "C"
+
+namespace {
+// a batch and its training step as one launch sequence (one graph replay)
+vmap_status step_impl(vmap_ctx* ctx, const int* rays_per_object, const float* given, cudaMemcpyKind kind,
+                      float* out_loss) {
+    SamplePlan sp;
+    if (vmap_status s = sample_plan(ctx, rays_per_object, given, kind, sp)) return s;
+    const int mask = class_mask(ctx);
+    if (vmap_status s = set_loss_dest(ctx, out_loss)) return s;
+    auto seq = [&]() -> vmap_status {
+        if (vmap_status s = launch_build_sample(ctx, sp.gi, sp.build)) return s;
+        ctx->after_sample = !ctx->prof_on || ctx->capturing;   // no profiling event after the sampler
+        vmap_status s = launch_train(ctx, mask);
+        ctx->after_sample = false;
+        return s;
+    };
+    if (ctx->graph_on) {
+        cudaGraphExec_t& g = ctx->g_step[sp.gi][sp.build ? 1 : 0];
+        int& gc = ctx->g_step_classes[sp.gi][sp.build ? 1 : 0];
+        if (g && gc != mask) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+        if (!g) {
+            if (vmap_status s = capture(ctx, &g, seq)) return s;
+            gc = mask;
+        }
+        if (vmap_status s = replay(ctx, g, PS_GRAPH_TRAIN)) return s;
+    } else {
+        if (vmap_status s = seq()) return s;
+    }
+    sample_done(ctx, rays_per_object, sp);
+    if (ctx->bf16) ctx->shadow_stale = true;
+    ctx->batch_ready = false;
+    return VMAP_OK;
+}
+}  // namespace
+
+extern "C" {
+
+vmap_status vmap_step(vmap_ctx* ctx, const int* rays_per_object, float* out_loss) {
+    return step_impl(ctx, rays_per_object, nullptr, cudaMemcpyDeviceToDevice, out_loss);
+}
+
 vmap_status vmap_train_step(vmap_ctx* ctx, float* out_loss) {
     if (!ctx) return VMAP_ERR_ARG;
     if (!ctx->batch_ready) return fail(ctx, VMAP_ERR_STATE, "train_step needs a fresh vmap_sample_rays");
     const int mask = class_mask(ctx);
+    if (vmap_status s = set_loss_dest(ctx, out_loss)) return s;
     if (ctx->graph_on) {
         if (ctx->g_train && ctx->g_classes != mask) {
             cudaGraphExecDestroy(ctx->g_train);
@@ -887,17 +1012,13 @@ vmap_status vmap_train_step(vmap_ctx* ctx, float* out_loss) {
     }
     // BF16 steps (eager or replayed) leave the FP32 shadow behind the weights
     if (ctx->bf16) ctx->shadow_stale = true;
-    if (out_loss)
-        CU(cudaMemcpyAsync(out_loss, ctx->loss_d, sizeof(float) * ctx->objs.size(), cudaMemcpyDeviceToDevice,
-                           ctx->stream));
     ctx->batch_ready = false;
     return VMAP_OK;
 }
 
 vmap_status vmap_train_step_host(vmap_ctx* ctx, const float* rays, const int* rays_per_object, float* loss) {
     if (!ctx || !rays || !loss) return fail(ctx, VMAP_ERR_ARG, "null argument");
-    if (vmap_status s = sample_impl(ctx, rays_per_object, rays, cudaMemcpyHostToDevice)) return s;
-    if (vmap_status s = vmap_train_step(ctx, nullptr)) return s;
+    if (vmap_status s = step_impl(ctx, rays_per_object, rays, cudaMemcpyHostToDevice, nullptr)) return s;
     CU(cudaMemcpyAsync(loss, ctx->loss_d, sizeof(float) * ctx->objs.size(), cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
     return VMAP_OK;

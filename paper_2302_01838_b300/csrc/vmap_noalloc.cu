@@ -190,6 +190,6 @@ extern "C" vmap_status vmap_object_grad_static(const vmap_config* cfg, const vma
     // the step slot holds `step`, the status slot 0: the reduce writes the gradient and the loss
     k_reduce<<<8, REDUCE_THREADS, 0, st>>>(sp, objs, ob, items, counts, part, nullptr, nullptr, nullptr, nullptr,
                                 ints + 3, ints + 2, RED_GRAD, nullptr, grad, loss, nullptr, nullptr, nullptr,
-                                nullptr);
+                                nullptr, nullptr, nullptr);
     return cudaGetLastError() == cudaSuccess ? VMAP_OK : VMAP_ERR_CUDA;
 }

@@ -111,10 +111,22 @@ __global__ void __launch_bounds__(REDUCE_THREADS, 3) k_reduce(StepParams sp, con
                                                            float* __restrict__ loss_out,
                                                            float* __restrict__ dcenter_out,
                                                            __nv_bfloat16* img, const long long* __restrict__ img_off,
-                                                           int* done) {
+                                                           int* done, const int* __restrict__ n_obj,
+                                                           float* const* __restrict__ loss_user_pp) {
     const int lane = threadIdx.x & 31;
     const int wpb = blockDim.x >> 5;
     const int n_units = 2 * counts[BC_ITEMS];   // (item, half)
+    // a second copy of the losses, to the caller's buffer (address read at run time)
+    float* const loss_user = loss_user_pp ? *loss_user_pp : nullptr;
+    // with n_obj: objects outside the batch report NaN (the batch's heads write the rest)
+    if (n_obj) {
+        const int K = *n_obj;
+        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x)
+            if (obs[k].R == 0) {
+                if (loss_out) loss_out[k] = __int_as_float(0x7fc00000);
+                if (loss_user) loss_user[k] = __int_as_float(0x7fc00000);
+            }
+    }
     // one unit: half `half` of chunk `chunk` of object k
     auto reduce_unit = [&](const int k, const int chunk, const int half) {
         const bool head = chunk == 0 && half == 0;   // the warp that reports per-object results
@@ -169,7 +181,9 @@ __global__ void __launch_bounds__(REDUCE_THREADS, 3) k_reduce(StepParams sp, con
         const float L = s0 / R + sp.lam_c * (s1 / (3.f * R)) + sp.lam_o * (s2 / R);
         const float gl = grad_loss ? grad_loss[k] : 1.f;
         if (head && lane == 0) {
-            if (loss_out) loss_out[k] = frozen ? __int_as_float(0x7fc00000) : L;
+            const float lv = frozen ? __int_as_float(0x7fc00000) : L;
+            if (loss_out) loss_out[k] = lv;
+            if (loss_user) loss_user[k] = lv;
             if (dcenter_out) {
                 float d[3] = {0.f, 0.f, 0.f};
                 for (int t = 0; t < nr; ++t) {

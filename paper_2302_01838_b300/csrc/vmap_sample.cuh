@@ -2,6 +2,7 @@
 #pragma once
 #include "vmap_build.cuh"
 #include "vmap_common.cuh"
+#include "vmap_tc.cuh"
 
 namespace vmapk {
 
@@ -37,6 +38,9 @@ __global__ void __launch_bounds__(32 * SAMPLE_RAYS_PER_BLOCK) k_sample(
     const int* __restrict__ bray_off, const int* __restrict__ ray_obj, const int* __restrict__ counts,
     const float* __restrict__ src, int given, const int* __restrict__ steps, int* __restrict__ pick_out,
     float* __restrict__ t_out) {
+    // a tile kernel launched behind the sampler may take SMs its last blocks
+    // free; it waits for the sampler's completion before reading picks and depths
+    pdl_launch_dependents();
     const int i = blockIdx.x * SAMPLE_RAYS_PER_BLOCK + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     const int total_rays = counts[BC_RAYS];

@@ -176,9 +176,6 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
     const int q = warp & 3, hf = warp >> 2;   // TMEM lane quadrant, column half
     const int row = q * 32 + lane;            // the sample (or fan-in lane) this thread reads
 
-    // every CTA of this grid is resident once each has passed this point: a
-    // width-128 kernel launched behind it may then take the SMs it frees
-    pdl_launch_dependents();
     // ---- set-up: barrier, tensor memory, constant columns ---------------------
     if (tid == 0) {
         mbar_init(mbar, 1);
@@ -290,6 +287,53 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
         }
     };
 
+    // what a tile needs from the tile list and its object's records (two
+    // dependent global loads): read for the next tile during this tile's forward
+    struct TileHead {
+        long long sbase, part, src_off, img_off;
+        const float* P;
+        float cx, cy, cz, sc, invR;
+        int k, nr, ray0, S;
+        bool first, last;
+    };
+    auto load_head = [&](long long tl) {
+        TileHead h;
+        const TileDev td = ta.tiles[tl];
+        h.k = td.obj;
+        h.nr = td.nr;
+        h.ray0 = td.ray0;
+        h.part = td.part;
+        h.first = tl == t0 || ta.tiles[tl - 1].obj != h.k;
+        h.last = tl + 1 == t1 || ta.tiles[tl + 1].obj != h.k;
+        const ObjDev& o = ta.objs[h.k];
+        const ObjBatch& b = ta.obs[h.k];
+        h.S = o.S;
+        h.sbase = b.sample_off + (long long)(td.ray0 - b.ray_off) * o.S;
+        h.src_off = b.src_off;
+        h.P = ta.params + o.param_off;
+        h.cx = o.c[0];
+        h.cy = o.c[1];
+        h.cz = o.c[2];
+        h.sc = o.scale;
+        h.invR = 1.f / (float)b.R;
+        h.img_off = ba.img_off[h.k];
+        return h;
+    };
+    TileHead nxt{};
+    bool have_nxt = false;
+    if (t0 < t1) {   // the first tile's head reads only the batch layout
+        nxt = load_head(t0);
+        have_nxt = true;
+    }
+    // Launched behind the sampler (programmatic dependent launch), the kernel
+    // has done its set-up so far; the sampler's picks and depths are complete
+    // past this wait. Dependents are released only after it, so a width-128
+    // kernel launched behind this one (which reads the sampler's output too)
+    // starts after the sampler's completion; every CTA of this grid is
+    // resident once each has passed this point.
+    pdl_wait();
+    pdl_launch_dependents();
+
 #pragma unroll 1
     for (long long tl = t0; tl < t1 && !abort; ++tl) {
         bufi ^= 1;
@@ -297,22 +341,21 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
         pre_next = false;
         float* tsm = reinterpret_cast<float*>(sm + C::TSO) + bufi * TM;
         float* rays = reinterpret_cast<float*>(sm + C::RAYS) + bufi * (RTMAX * RAYF);
-        const TileDev td = ta.tiles[tl];
-        const int k = td.obj, nr = td.nr;
-        const bool first = tl == t0 || ta.tiles[tl - 1].obj != k;
-        const bool last = tl + 1 == t1 || ta.tiles[tl + 1].obj != k;
-        const ObjDev& ob = ta.objs[k];
-        const int S = ob.S, M = nr * S;
-        const long long sbase = ta.obs[k].sample_off + (long long)(td.ray0 - ta.obs[k].ray_off) * S;
-        const float* P = ta.params + ob.param_off;
-        const float cx = ob.c[0], cy = ob.c[1], cz = ob.c[2], sc = ob.scale;
+        const TileHead th = have_nxt ? nxt : load_head(tl);
+        have_nxt = false;
+        const int k = th.k, nr = th.nr;
+        const bool first = th.first, last = th.last;
+        const int S = th.S, M = nr * S;
+        const long long sbase = th.sbase;
+        const float* P = th.P;
+        const float cx = th.cx, cy = th.cy, cz = th.cz, sc = th.sc;
 
         // ---- rays, depths, points; weights at the start of a run ---------------
         // (after the first tile of a training range, the previous tile's
         // forward already started this tile's rays and depths by cp.async)
         if (!pre) {
             for (int r = tid; r < nr; r += blockDim.x) {
-                const float* rec = ta.pool + (ta.obs[k].src_off + ta.pick[td.ray0 + r]) * REC;
+                const float* rec = ta.pool + (th.src_off + ta.pick[th.ray0 + r]) * REC;
                 float* d = rays + r * RAYF;
 #pragma unroll
                 for (int u = 0; u < 11; ++u) d[u] = rec[u];
@@ -324,7 +367,7 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
             // the weight image arrives by bulk copy while the tile is encoded
             if (tid == 0) {
                 mbar_expect_tx(wbar, (uint32_t)C::WIMG_BYTES);
-                bulk_load(W1, ba.img + ba.img_off[k], (uint32_t)C::WIMG_BYTES, wbar);
+                bulk_load(W1, ba.img + th.img_off, (uint32_t)C::WIMG_BYTES, wbar);
                 wpend = true;
             }
             for (int i = tid; i < 3 * RTMAX; i += blockDim.x) lossacc[i] = 0.f;
@@ -383,27 +426,24 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
         // the next tile of this range: its picks now, its rays and depths (into the
         // other buffers) once the picks have arrived
         const bool has_next = GRAD && tl + 1 < t1;
-        TileDev tdn{};
         if (has_next) {
-            tdn = ta.tiles[tl + 1];
-            if (tid < tdn.nr) npick = ta.pick[tdn.ray0 + tid];
+            nxt = load_head(tl + 1);
+            have_nxt = true;
+            if (tid < nxt.nr) npick = ta.pick[nxt.ray0 + tid];
         }
         wait_mma();
         if (abort) break;
         if (has_next) {
-            const ObjBatch& obn = ta.obs[tdn.obj];
-            const int Sn = ta.objs[tdn.obj].S;
             float* rays_n = reinterpret_cast<float*>(sm + C::RAYS) + (bufi ^ 1) * (RTMAX * RAYF);
             float* tsm_n = reinterpret_cast<float*>(sm + C::TSO) + (bufi ^ 1) * TM;
-            if (tid < tdn.nr) {
-                const float* rec = ta.pool + (obn.src_off + npick) * REC;
+            if (tid < nxt.nr) {
+                const float* rec = ta.pool + (nxt.src_off + npick) * REC;
                 float* d = rays_n + tid * RAYF;
                 cp_async16(d, rec);
                 cp_async16(d + 4, rec + 4);
                 cp_async16(d + 8, rec + 8);
             }
-            const long long sb = obn.sample_off + (long long)(tdn.ray0 - obn.ray_off) * Sn;
-            if (tid < tdn.nr * Sn) cp_async4(tsm_n + tid, ta.tbuf + sb + tid);
+            if (tid < nxt.nr * nxt.S) cp_async4(tsm_n + tid, ta.tbuf + nxt.sbase + tid);
             cp_async_commit();
             pre_next = true;
         }
@@ -456,7 +496,7 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
         if (abort) break;
 
         // ---- rendering, loss, dL/dy (FP32) ----------------------------------------
-        const float invR = 1.f / (float)ta.obs[k].R;
+        const float invR = th.invR;
         for (int r = warp; r < nr; r += NTHREADS / 32) {
             float* d = rays + r * RAYF;
             render_ray_warp<GRAD, TM, true>(sp, yb, tsm, d, r, S, invR);
@@ -471,7 +511,7 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
         __syncthreads();
         if (!GRAD) {
             __syncthreads();
-            if (last) flush_run(td.part);
+            if (last) flush_run(th.part);
             __syncthreads();
             continue;
         }
@@ -578,7 +618,7 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
             wait_dw12();
             agree();
             if (abort) break;
-            flush_run(td.part);
+            flush_run(th.part);
         }
         tc_fence_before();
         __syncthreads();

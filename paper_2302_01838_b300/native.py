@@ -74,6 +74,7 @@ SIGNATURES = {
     "vmap_profile_read": (_I, [_P, _I, ctypes.POINTER(ctypes.c_char_p), _LLP,
                                 ctypes.POINTER(ctypes.c_double)]),
     "vmap_train_step": (_I, [_P, _P]),
+    "vmap_step": (_I, [_P, _IP, _P]),
     "vmap_set_graph": (_I, [_P, _I]),
     "vmap_get_launch": (_I, [_P, _IP, _IP]),
     "vmap_set_launch": (_I, [_P, _IP, _IP]),

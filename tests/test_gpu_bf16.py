@@ -256,3 +256,71 @@ def test_changing_ray_counts_rebuild_the_layout_in_graph_mode():
         assert np.all(rel <= 1e-5), (R, rel)
     assert torch.equal(a.get_params(), b.get_params())
     assert [a.get_object_state(k)[3] for k in range(3)] == [5, 7, 7]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_train_step_writes_losses_to_the_callers_buffer_in_graph_mode(precision):
+    """The step's reduce writes the losses straight to the caller's buffer, whose
+    address the replayed graph reads from device memory: switching buffers (or
+    passing none) between replays gives the eager losses bitwise, NaN for an
+    object outside the batch, and leaves the other buffers untouched."""
+    from paper_2302_01838_b300.native import VMAP_FP32
+    prec = VMAP_BF16 if precision == "bf16" else VMAP_FP32
+    sc = scenes.scene_small(seed=49, n_objects=3, rays=60)
+    a = vh.library_context(sc, max_rays=400, precision=prec)
+    b = vh.library_context(sc, max_rays=400, precision=prec)
+    b.set_graph(True)
+    x = torch.full((3,), 7.0, device="cuda")
+    y = torch.full((3,), 7.0, device="cuda")
+    plans = [([60, 60, 60], x), ([60, 60, 60], y), ([0, 45, 60], x), ([60, 60, 60], None), ([30, 0, 60], y),
+             ([60, 60, 60], x)]
+    for R, dest in plans:
+        ref = torch.empty(3, device="cuda")
+        a.sample_rays(R); a.train_step(ref)
+        before = {id(t): t.clone() for t in (x, y)}
+        b.sample_rays(R); b.train_step(dest)
+        torch.cuda.synchronize()
+        for t in (x, y):
+            if t is not dest:
+                assert torch.allclose(t, before[id(t)], rtol=0, atol=0, equal_nan=True)
+        if dest is None:
+            continue
+        gone = [k for k in range(3) if R[k] == 0]
+        assert torch.isnan(ref[gone]).all() and torch.isnan(dest[gone]).all()
+        live = [k for k in range(3) if R[k] > 0]
+        assert torch.isfinite(ref[live]).all()
+        assert torch.equal(ref[live], dest[live])
+    assert torch.equal(a.get_params(), b.get_params())
+
+
+def test_combined_step_matches_separate_calls_bitwise():
+    """vmap_step (the sampler, then the tile kernel launched behind it with a
+    programmatic dependency, then the width-128 kernels behind that) gives the
+    results of vmap_sample_rays + vmap_train_step bitwise: eager, replayed, and
+    with profiling events between every launch; across layout rebuilds, with a
+    paused object, with no hidden-32 rays at all (the tile kernel's CTAs have no
+    tiles and the width-128 kernels still read the sampler's output) and with
+    no background rays."""
+    sc = _wide_scene(50, n_small=3, bg_rays=600)
+    R0 = [o["rays"] for o in sc["objects"]]
+    K = len(R0)
+    ctxs = [vh.library_context(sc, precision=VMAP_BF16, max_rays=4000) for _ in range(4)]
+    sep, eager, graph, prof = ctxs
+    graph.set_graph(True)
+    prof.profile_enable(True)
+    plans = [R0, R0, [1500] + R0[1:], [1500] + R0[1:], [600, 0, 100, 100], [600, 0, 0, 0], [600, 0, 0, 0],
+             [0, 100, 100, 100], R0, R0]
+    for R in plans:
+        ref = torch.empty(K, device="cuda")
+        sep.sample_rays(R); sep.train_step(ref)
+        live = [k for k in range(K) if R[k] > 0]
+        gone = [k for k in range(K) if R[k] == 0]
+        for vm in (eager, graph, prof):
+            out = torch.empty(K, device="cuda")
+            vm.step(R, out)
+            assert torch.equal(out[live], ref[live]), (R, out, ref)
+            assert torch.isnan(out[gone]).all() and torch.isnan(ref[gone]).all()
+    p = sep.get_params()
+    for vm in (eager, graph, prof):
+        assert torch.equal(vm.get_params(), p)
+        assert vm.sync_status() == []
