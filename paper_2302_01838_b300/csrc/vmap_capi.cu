@@ -519,18 +519,31 @@ vmap_status launch_tiles(vmap_ctx* ctx, int mask) {
     return VMAP_OK;
 }
 
+// In a training step with no profiling event before it, the reduce is
+// launched with programmatic stream serialization behind the step's last tile
+// kernel: its blocks load the tables, step counts, weights and moments on SMs
+// that kernel frees, then wait for it before reading the run slots.
 vmap_status launch_reduce(vmap_ctx* ctx, int mode, const float* grad_loss, float* grad_out, float* loss_out,
                           float* dcenter_out, bool train = false) {
     const int pi = prof_begin(ctx, PS_REDUCE);
-    k_reduce<<<ctx->n_sm * 3, REDUCE_THREADS, 0, ctx->stream>>>(ctx->sp, ctx->objs_d, ctx->ob_d, ctx->items_d,
-                                                     ctx->counts_d, ctx->part_d, ctx->params_d, ctx->bf16 ? nullptr : ctx->wt_d,
-                                                     ctx->m_d, ctx->v_d, ctx->steps_d, ctx->status_d, mode,
-                                                     grad_loss, grad_out, loss_out, dcenter_out,
-                                                     ctx->bf16 ? ctx->img_d : nullptr, ctx->img_off_d,
-                                                     ctx->done_d, train ? ctx->n_obj_d : nullptr,
-                                                     train ? ctx->loss_pp_d : nullptr);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(ctx->n_sm * 3));
+    cfg.blockDim = dim3(REDUCE_THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = train && pi < 0 && (!ctx->prof_on || ctx->capturing) ? 1 : 0;
+    cudaError_t e = cudaLaunchKernelEx(
+        &cfg, k_reduce, ctx->sp, (const ObjDev*)ctx->objs_d, (const ObjBatch*)ctx->ob_d, (const int2*)ctx->items_d,
+        (const int*)ctx->counts_d, (const float*)ctx->part_d, ctx->params_d, ctx->bf16 ? nullptr : ctx->wt_d, ctx->m_d,
+        ctx->v_d, ctx->steps_d, ctx->status_d, mode, grad_loss, grad_out, loss_out, dcenter_out,
+        ctx->bf16 ? ctx->img_d : nullptr, (const long long*)ctx->img_off_d, ctx->done_d,
+        (const int*)(train ? ctx->n_obj_d : nullptr), (float* const*)(train ? ctx->loss_pp_d : nullptr));
     prof_end(ctx, pi);
-    CHECK_LAUNCH("k_reduce");
+    if (e != cudaSuccess) return fail(ctx, VMAP_ERR_CUDA, "k_reduce launch failed: %s", cudaGetErrorString(e));
     return VMAP_OK;
 }
 

@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(REDUCE_THREADS, 3) k_reduce(StepParams sp, con
                                                            const ObjBatch* __restrict__ obs,
                                                            const int2* __restrict__ items,
                                                            const int* __restrict__ counts,
-                                                           const float* __restrict__ part, float* params,
+                                                           const float* part, float* params,
                                                            float* wt, float* mom, float* vel,
                                                            int* steps, int* status,
                                                            int mode, const float* __restrict__ grad_loss,
@@ -137,24 +137,30 @@ __global__ void __launch_bounds__(REDUCE_THREADS, 3) k_reduce(StepParams sp, con
         const long long stride = P + NEXTRA;
         const int nr = bt.n_runs;
         const float* e = part + bt.part_off + P;   // run t's loss sums at e[t * stride + 0..2]
-        // loss terms of the first 32 runs, in flight with the gradient loads below
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-        if (lane < nr) {
-            const float* el = e + (long long)lane * stride;
-            s0 = el[0]; s1 = el[1]; s2 = el[2];
-        }
         const int t1 = mode == RED_ADAM ? steps[k] + 1 : 1;
         const bool frozen = status[k] != 0;
         const int p = chunk * REDUCE_CHUNK + half * (REDUCE_CHUNK / 2) + 4 * lane;
         const bool act = mode != RED_LOSS && p < P;
         const long long q = ob.param_off + p;
         float4 g = make_float4(0.f, 0.f, 0.f, 0.f), th0 = g, m0 = g, v0 = g;
+        if (act && mode == RED_ADAM) {
+            th0 = ld4(params + q);
+            m0 = ld4(mom + q);
+            v0 = ld4(vel + q);
+        }
+        // Launched behind the step's last tile kernel (programmatic dependent
+        // launch), everything above (tables, step counts, weights, moments: none
+        // written by the tile kernels) overlapped its end; the run slots are the
+        // tile kernels' output. (`part` is not __restrict__: loads through a
+        // restrict-qualified read-only pointer may be hoisted above this wait.)
+        pdl_wait();
+        // loss terms of the first 32 runs, in flight with the gradient loads below
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+        if (lane < nr) {
+            const float* el = e + (long long)lane * stride;
+            s0 = el[0]; s1 = el[1]; s2 = el[2];
+        }
         if (act) {
-            if (mode == RED_ADAM) {
-                th0 = ld4(params + q);
-                m0 = ld4(mom + q);
-                v0 = ld4(vel + q);
-            }
             const float* src = part + bt.part_off + p;
             for (int t = 0; t < nr; t += 4) {   // four (predicated) slot loads in flight, added in slot order
                 float4 v[4];

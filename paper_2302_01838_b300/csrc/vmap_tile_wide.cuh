@@ -474,6 +474,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_wide_dw(WideArgs wa) {
     const long long t0 = (long long)rg * n_tiles / ranges;
     const long long t1 = (long long)(rg + 1) * n_tiles / ranges;
     const int n = (int)(t1 - t0);
+    // every CTA is resident once each has passed this point: the reduce
+    // launched behind this kernel may start its table loads on free SMs
+    pdl_launch_dependents();
 
     if (wa.loss_only) {
         pdl_wait();   // the tile losses come from k_wide_fb
