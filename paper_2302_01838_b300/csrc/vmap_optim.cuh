@@ -143,17 +143,24 @@ __global__ void __launch_bounds__(REDUCE_THREADS, 3) k_reduce(StepParams sp, con
         const bool act = mode != RED_LOSS && p < P;
         const long long q = ob.param_off + p;
         float4 g = make_float4(0.f, 0.f, 0.f, 0.f), th0 = g, m0 = g, v0 = g;
+        float ibc1 = 1.f, ibc2 = 1.f;   // reciprocal Adam bias corrections
+        long long ioff = -1;            // the object's BF16 image, if any
         if (act && mode == RED_ADAM) {
             th0 = ld4(params + q);
             m0 = ld4(mom + q);
             v0 = ld4(vel + q);
+            ibc1 = 1.f / (1.f - powf(sp.beta1, (float)t1));
+            ibc2 = 1.f / (1.f - powf(sp.beta2, (float)t1));
+            if (img) ioff = img_off[k];
         }
         // Launched behind the step's last tile kernel (programmatic dependent
-        // launch), everything above (tables, step counts, weights, moments: none
-        // written by the tile kernels) overlapped its end; the run slots are the
-        // tile kernels' output. (`part` is not __restrict__: loads through a
-        // restrict-qualified read-only pointer may be hoisted above this wait.)
-        pdl_wait();
+        // launch), everything above (tables, step counts, weights, moments, Adam
+        // bias corrections: none depend on the tile kernels) overlapped its end;
+        // the run slots are the tile kernels' output. The wait names the values
+        // computed above, so they are formed before it; `part` is not
+        // __restrict__, as loads through a restrict-qualified read-only pointer
+        // may be hoisted above the wait.
+        asm volatile("griddepcontrol.wait;" : "+f"(ibc1), "+f"(ibc2), "+l"(ioff)::"memory");
         // loss terms of the first 32 runs, in flight with the gradient loads below
         float s0 = 0.f, s1 = 0.f, s2 = 0.f;
         if (lane < nr) {
@@ -210,8 +217,6 @@ __global__ void __launch_bounds__(REDUCE_THREADS, 3) k_reduce(StepParams sp, con
             for (int i = 0; i < 4; ++i) grad_out[q + i] = gl * at4(g, i);
             return;
         }
-        const float bc1 = 1.f - powf(sp.beta1, (float)t1);   // Adam bias corrections
-        const float bc2 = 1.f - powf(sp.beta2, (float)t1);
         float4 m = m0, v = v0, th = th0;
         bool bad = false;
 #pragma unroll
@@ -225,7 +230,7 @@ __global__ void __launch_bounds__(REDUCE_THREADS, 3) k_reduce(StepParams sp, con
             const float vi = sp.beta2 * at4(v0, i) + (1.f - sp.beta2) * gi * gi;
             at4(m, i) = mi;
             at4(v, i) = vi;
-            at4(th, i) = at4(th0, i) - sp.lr * (mi / bc1) / (sqrtf(vi / bc2) + sp.eps);
+            at4(th, i) = at4(th0, i) - sp.lr * (mi * ibc1) / (sqrtf(vi * ibc2) + sp.eps);
         }
         if (bad) atomicOr(status + k, 2);
         st4(mom + q, m);
@@ -239,9 +244,9 @@ __global__ void __launch_bounds__(REDUCE_THREADS, 3) k_reduce(StepParams sp, con
             const float x = at4(th, i);
             const int N = l == 4 ? NOUT : H;
             if (wt) wt[ob.wt_off + wt_layer_off(H, l) + (long long)wk * N + wn] = x;   // transposed shadow
-            if (img && img_off[k] >= 0) {                                       // BF16 operand image
+            if (ioff >= 0) {                                                     // BF16 operand image
                 const long long base = l == 0 ? 0 : (long long)H * DINP + (long long)(l - 1) * H * H;
-                img[img_off[k] + base + cm_off(wn, wk, l == 0 ? DINP : H) / 2] = __float2bfloat16(x);
+                img[ioff + base + cm_off(wn, wk, l == 0 ? DINP : H) / 2] = __float2bfloat16(x);
             }
         }
     };
