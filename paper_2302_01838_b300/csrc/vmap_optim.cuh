@@ -127,6 +127,7 @@ __global__ void __launch_bounds__(REDUCE_THREADS, 3) k_reduce(StepParams sp, con
                 if (loss_user) loss_user[k] = __int_as_float(0x7fc00000);
             }
     }
+    bool wrote_status = false;   // this lane froze its unit's object
     // one unit: half `half` of chunk `chunk` of object k
     auto reduce_unit = [&](const int k, const int chunk, const int half) {
         const bool head = chunk == 0 && half == 0;   // the warp that reports per-object results
@@ -208,7 +209,10 @@ __global__ void __launch_bounds__(REDUCE_THREADS, 3) k_reduce(StepParams sp, con
         }
         if (mode == RED_LOSS) return;
         if (mode == RED_ADAM && (frozen || !isfinite(L))) {
-            if (!frozen && head && lane == 0) status[k] = 1;
+            if (!frozen && head && lane == 0) {
+                status[k] = 1;
+                wrote_status = true;
+            }
             return;
         }
         if (!act) return;
@@ -232,7 +236,10 @@ __global__ void __launch_bounds__(REDUCE_THREADS, 3) k_reduce(StepParams sp, con
             at4(v, i) = vi;
             at4(th, i) = at4(th0, i) - sp.lr * (mi * ibc1) / (sqrtf(vi * ibc2) + sp.eps);
         }
-        if (bad) atomicOr(status + k, 2);
+        if (bad) {
+            atomicOr(status + k, 2);
+            wrote_status = true;
+        }
         st4(mom + q, m);
         st4(vel + q, v);
         st4(params + q, th);
@@ -254,11 +261,15 @@ __global__ void __launch_bounds__(REDUCE_THREADS, 3) k_reduce(StepParams sp, con
     for (int u = blockIdx.x * wpb + (threadIdx.x >> 5); u < n_units; u += gridDim.x * wpb) {
         const int2 item = items[u >> 1];
         const int k = item.x;
+        wrote_status = false;
         reduce_unit(k, item.y, u & 1);
         if (mode == RED_ADAM && done) {
+            // a status write must be visible before the arrival that may let the
+            // last warp read the status; nothing else this warp wrote is read here
             __syncwarp();
+            const bool fence = __any_sync(0xffffffffu, wrote_status);
             if (lane == 0) {
-                __threadfence();
+                if (fence) __threadfence();
                 const int units = 2 * (int)((param_count(objs[k].hidden) + REDUCE_CHUNK - 1) / REDUCE_CHUNK);
                 if (atomicAdd(done + k, 1) == units - 1) {
                     done[k] = 0;
