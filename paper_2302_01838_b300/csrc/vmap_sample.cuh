@@ -29,8 +29,7 @@ __device__ __forceinline__ int upper_index(const int* off, int n, int i) {
 // material's termination of rays that cross the box but belong to another
 // surface): its stratified range stops at t_s, its Gaussian samples are
 // clamped above at t_s. Slots
-// 0..N_s-1 hold the surface samples, N_s.. the stratified ones; the stable
-// ascending order is each value's rank (ties broken by slot).
+// 0..N_s-1 hold the surface samples, N_s.. the stratified ones, sorted ascending.
 constexpr int SAMPLE_RAYS_PER_BLOCK = 8;
 
 __global__ void __launch_bounds__(32 * SAMPLE_RAYS_PER_BLOCK) k_sample(
@@ -91,12 +90,19 @@ __global__ void __launch_bounds__(32 * SAMPLE_RAYS_PER_BLOCK) k_sample(
         const float u = word_to_unit(wa);
         t = lo + ((float)q + u) / (float)Nc * span;
     }
-    int rank = 0;
-    for (int b = 0; b < S; ++b) {
-        const float o = __shfl_sync(0xffffffffu, t, b);
-        rank += (o < t || (o == t && b < lane)) ? 1 : 0;
+    // ascending order: a bitonic network over the warp's 32 lanes (lanes past S
+    // hold +inf and sort last); equal values are interchangeable, so the
+    // stored depths are the stable order's
+#pragma unroll
+    for (int kb = 2; kb <= 32; kb <<= 1) {
+#pragma unroll
+        for (int jb = kb >> 1; jb > 0; jb >>= 1) {
+            const float o = __shfl_xor_sync(0xffffffffu, t, jb);
+            const bool keep_min = ((lane & jb) == 0) == ((lane & kb) == 0);
+            t = keep_min ? fminf(t, o) : fmaxf(t, o);
+        }
     }
-    if (lane < S) t_out[bt.sample_off + (long long)r * S + rank] = t;
+    if (lane < S) t_out[bt.sample_off + (long long)r * S + lane] = t;
 }
 
 }  // namespace vmapk
