@@ -354,6 +354,8 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
         // (after the first tile of a training range, the previous tile's
         // forward already started this tile's rays and depths by cp.async)
         if (!pre) {
+            // depths in flight with the picks and records
+            for (int i = tid; i < M; i += blockDim.x) tsm[i] = ta.tbuf[sbase + i];
             for (int r = tid; r < nr; r += blockDim.x) {
                 const float* rec = ta.pool + (th.src_off + ta.pick[th.ray0 + r]) * REC;
                 float* d = rays + r * RAYF;
@@ -392,8 +394,7 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
             float x0 = 0.f, x1 = 0.f, x2 = 0.f;
             if (m < M) {
                 const float* d = rays + (m / S) * RAYF;
-                const float t = pre ? tsm[m] : ta.tbuf[sbase + m];
-                if (!pre && half == 0) tsm[m] = t;
+                const float t = tsm[m];
                 x0 = (fmaf(t, d[3], d[0]) - cx) / sc;
                 x1 = (fmaf(t, d[4], d[1]) - cy) / sc;
                 x2 = (fmaf(t, d[5], d[2]) - cz) / sc;

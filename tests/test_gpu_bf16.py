@@ -324,3 +324,29 @@ def test_combined_step_matches_separate_calls_bitwise():
     for vm in (eager, graph, prof):
         assert torch.equal(vm.get_params(), p)
         assert vm.sync_status() == []
+
+
+def test_host_buffer_step_in_graph_mode_matches_separate_calls_bitwise():
+    """vmap_train_step_host (pinned host rays, one replayed launch sequence with
+    the sampler, host losses) equals vmap_sample_rays_given + vmap_train_step on
+    the same rays, including the width-128 background, a changed ray count (a
+    layout rebuild) and an object outside the batch."""
+    sc = _wide_scene(51, n_small=2, bg_rays=300)
+    K = len(sc["objects"])
+    dev = vh.library_context(sc, precision=VMAP_BF16, max_rays=2000)
+    host = vh.library_context(sc, precision=VMAP_BF16, max_rays=2000)
+    host.set_graph(True)
+    rng = np.random.default_rng(9)
+    loss_d = torch.empty(K, device="cuda")
+    loss_h = torch.empty(K).pin_memory()
+    for R in ([300, 100, 100], [300, 100, 100], [500, 0, 60], [500, 0, 60], [300, 100, 100]):
+        given = [o["pool"][rng.integers(0, o["pool"].shape[0], max(R[k], 1))][:R[k]]
+                 for k, o in enumerate(sc["objects"])]
+        flat = np.concatenate([g for g in given if g.shape[0]]).astype(np.float32)
+        dev.sample_rays_given(torch.from_numpy(flat).cuda(), R)
+        dev.train_step(loss_d)
+        host.train_step_host(torch.from_numpy(flat).pin_memory(), R, loss_h)
+        assert np.array_equal(loss_d.cpu().numpy(), loss_h.numpy(), equal_nan=True)
+        assert all(np.isnan(loss_h.numpy()[k]) == (R[k] == 0) for k in range(K))
+    assert torch.equal(dev.get_params(), host.get_params())
+    assert dev.sync_status() == [] and host.sync_status() == []
