@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE (see oracle/__init__.py).
 
-The paper has no such network; it is this build's learned extension: from a
+The paper has no such network; it is a learned extension of the method: from a
 set of N points (x~, occupancy, rgb) taken from a newly seen object's first
 keyframe, predict initial weights for the object's MLP.
 

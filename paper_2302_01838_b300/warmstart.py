@@ -143,7 +143,7 @@ def time_to_target(objs, B, seed, form, hyper=None, target=0.04, max_steps=3000,
 
 
 def initial_loss(objs, B, seed, hyper=None):
-    """The plain training loss of step 0 (the judge of a warm start's error)."""
+    """The plain training loss of step 0 (the measure of a warm start's error)."""
     vm = _context(objs, B, seed, VMAP_FP32)
     if hyper is not None:
         for k, o in enumerate(objs):
