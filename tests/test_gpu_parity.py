@@ -543,3 +543,28 @@ def test_scene_render_composes_objects_by_rendered_depth():
     # a listed subset composes only those objects
     vm.render_scene(torch.from_numpy(rays).cuda(), [2], [half[2]], 24, depth)
     assert np.max(np.abs(depth.cpu().numpy() - recs[2][1])) <= tol
+
+
+def test_combined_step_matches_separate_calls_fp32():
+    """vmap_step (sampler and training step as one launch sequence) on the FP32
+    path gives vmap_sample_rays + vmap_train_step's losses and weights bitwise,
+    eager and replayed, across a changed ray count and a paused object."""
+    sc = vh.mixed_scene(seed=52)
+    K = len(sc["objects"])
+    R0 = [o["rays"] for o in sc["objects"]]
+    sep = vh.library_context(sc)
+    eager = vh.library_context(sc)
+    graph = vh.library_context(sc)
+    graph.set_graph(True)
+    R1 = [r * 2 for r in R0]
+    R2 = [0] + R0[1:]
+    for R in (R0, R0, R1, R2, R2, R0):
+        ref = torch.empty(K, device="cuda")
+        sep.sample_rays(R); sep.train_step(ref)
+        for vm in (eager, graph):
+            out = torch.empty(K, device="cuda")
+            vm.step(R, out)
+            assert torch.allclose(out, ref, rtol=0, atol=0, equal_nan=True), (R, out, ref)
+    for vm in (eager, graph):
+        for k in range(K):
+            assert torch.equal(vm.get_object_state(k)[0], sep.get_object_state(k)[0])
