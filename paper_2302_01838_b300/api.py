@@ -53,6 +53,14 @@ class VMap:
         self.cfg = cfg
 
     # ------------------------------------------------------------------
+    def _counts(self, rays_per_object):
+        """Host int array of the rays per object (the last one is reused while unchanged)."""
+        key = tuple(rays_per_object)
+        if key != getattr(self, "_counts_key", None):
+            self._counts_arr = (ctypes.c_int * len(key))(*[int(r) for r in key])
+            self._counts_key = key
+        return self._counts_arr
+
     def _check(self, st):
         if st != 0:
             raise VmapError(st, self.lib.vmap_last_error(self.h).decode())
@@ -97,18 +105,18 @@ class VMap:
         return n.value
 
     def sample_rays(self, rays_per_object):
-        arr = (ctypes.c_int * len(rays_per_object))(*[int(r) for r in rays_per_object])
+        arr = self._counts(rays_per_object)
         self._check(self.lib.vmap_sample_rays(self.h, arr))
 
     def sample_rays_given(self, rays, rays_per_object):
-        arr = (ctypes.c_int * len(rays_per_object))(*[int(r) for r in rays_per_object])
+        arr = self._counts(rays_per_object)
         self._check(self.lib.vmap_sample_rays_given(self.h, _ptr(rays), arr))
 
     def train_step_host(self, rays, rays_per_object, loss_out):
         """rays, loss_out: CPU tensors (pinned for an asynchronous copy)."""
         if rays.is_cuda or loss_out.is_cuda:
             raise ValueError("train_step_host takes host tensors")
-        arr = (ctypes.c_int * len(rays_per_object))(*[int(r) for r in rays_per_object])
+        arr = self._counts(rays_per_object)
         self._check(self.lib.vmap_train_step_host(self.h, ctypes.c_void_p(rays.data_ptr()), arr,
                                                   ctypes.c_void_p(loss_out.data_ptr())))
         return loss_out
@@ -154,7 +162,7 @@ class VMap:
         self._check(self.lib.vmap_set_launch(self.h, rt, gm))
 
     def autotune(self, rays_per_object, reps=3):
-        arr = (ctypes.c_int * len(rays_per_object))(*[int(r) for r in rays_per_object])
+        arr = self._counts(rays_per_object)
         best = (ctypes.c_float * 4)()
         self._check(self.lib.vmap_autotune(self.h, arr, int(reps), best))
         return list(best)
@@ -165,7 +173,7 @@ class VMap:
 
     def step(self, rays_per_object, out_loss=None):
         """sample_rays(rays_per_object) then train_step(out_loss), as one launch sequence."""
-        arr = (ctypes.c_int * len(rays_per_object))(*[int(r) for r in rays_per_object])
+        arr = self._counts(rays_per_object)
         self._check(self.lib.vmap_step(self.h, arr, _ptr(out_loss)))
         return out_loss
 
