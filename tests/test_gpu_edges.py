@@ -91,3 +91,32 @@ def test_empty_batch_and_exact_capacity():
     vm.train_step(L)
     assert torch.isfinite(L[0]) and torch.isnan(L[1])
     assert vm.get_object_state(0)[3] == 2 and vm.get_object_state(1)[3] == 1
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_combined_step_on_degenerate_batches_and_capacity(precision):
+    """vmap_step, replayed, on the degenerate batches above (one sample per ray,
+    32 samples, rays without depth, a single ray, hidden 128), an empty batch
+    and a half-empty one equals the separate calls bitwise; a request past the
+    capacity is refused before anything is launched and the context trains on."""
+    sc = _scene(95, SPECS)
+    R = [o["rays"] for o in sc["objects"]]
+    K = len(R)
+    kw = dict(precision=VMAP_BF16) if precision == "bf16" else {}
+    a = vh.library_context(sc, **kw)
+    b = vh.library_context(sc, **kw)
+    b.set_graph(True)
+    half = [r if k % 2 else 0 for k, r in enumerate(R)]
+    for plan in (R, [0] * K, R, half, half, R):
+        la, lb = torch.empty(K, device="cuda"), torch.empty(K, device="cuda")
+        a.sample_rays(plan); a.train_step(la)
+        b.step(plan, lb)
+        assert torch.allclose(la, lb, rtol=0, atol=0, equal_nan=True), (plan, la, lb)
+        assert all(bool(torch.isnan(lb[k])) == (plan[k] == 0) for k in range(K))
+    with pytest.raises(VmapError, match="ERR_CAPACITY"):
+        b.step([10 ** 6] + R[1:], lb)
+    a.sample_rays(R); a.train_step(la)
+    b.step(R, lb)
+    assert torch.equal(la, lb)
+    assert torch.equal(a.get_params(), b.get_params())
+    assert a.sync_status() == [] and b.sync_status() == []
