@@ -365,10 +365,11 @@ WideArgs wide_args(vmap_ctx* ctx) {
 }
 
 // overlap: with `after_tile` (the previous kernel in the stream is a BF16 tile
-// kernel, which signals its dependents once all its CTAs are resident), the
-// width-128 kernel is launched with programmatic stream serialization, so its
-// CTAs start on SMs as the tile kernel's CTAs finish; it waits for the tile
-// kernel's completion before it exits (the two touch disjoint objects)
+// kernel, which signals its dependents once all its CTAs are resident and past
+// their wait for the sampler), the width-128 kernel is launched with
+// programmatic stream serialization, so its CTAs start on SMs as the tile
+// kernel's CTAs finish; it waits for the tile kernel's completion before it
+// exits (the two touch disjoint objects)
 template <int MODE>
 cudaError_t launch_wide_fb(vmap_ctx* ctx, bool after_tile = false) {
     static bool attr_set = false;
