@@ -350,3 +350,34 @@ def test_host_buffer_step_in_graph_mode_matches_separate_calls_bitwise():
         assert all(np.isnan(loss_h.numpy()[k]) == (R[k] == 0) for k in range(K))
     assert torch.equal(dev.get_params(), host.get_params())
     assert dev.sync_status() == [] and host.sync_status() == []
+
+
+def test_mixed_pool_and_host_steps_in_graph_mode():
+    """Alternating vmap_step (pool rays), vmap_train_step_host (caller rays) and the
+    separate calls on one replayed context (each switch of ray source rebuilds
+    the layout) trains exactly like a context doing the same with separate calls."""
+    sc = _wide_scene(53, n_small=2, bg_rays=300)
+    K = len(sc["objects"])
+    R = [o["rays"] for o in sc["objects"]]
+    ref = vh.library_context(sc, precision=VMAP_BF16, max_rays=2000)
+    mix = vh.library_context(sc, precision=VMAP_BF16, max_rays=2000)
+    mix.set_graph(True)
+    rng = np.random.default_rng(4)
+    lr, lm = torch.empty(K, device="cuda"), torch.empty(K, device="cuda")
+    lh = torch.empty(K).pin_memory()
+    for kind in ("step", "host", "step", "sep", "host", "host", "step"):
+        if kind == "host":
+            flat = np.concatenate([o["pool"][rng.integers(0, o["pool"].shape[0], R[k])]
+                                   for k, o in enumerate(sc["objects"])]).astype(np.float32)
+            ref.sample_rays_given(torch.from_numpy(flat).cuda(), R); ref.train_step(lr)
+            mix.train_step_host(torch.from_numpy(flat).pin_memory(), R, lh)
+            assert np.array_equal(lr.cpu().numpy(), lh.numpy())
+        else:
+            ref.sample_rays(R); ref.train_step(lr)
+            if kind == "step":
+                mix.step(R, lm)
+            else:
+                mix.sample_rays(R); mix.train_step(lm)
+            assert torch.equal(lr, lm)
+    assert torch.equal(ref.get_params(), mix.get_params())
+    assert mix.sync_status() == []
