@@ -46,3 +46,21 @@ def test_default_config_without_a_gpu():
     lib.vmap_default_config(ctypes.byref(cfg))
     assert abs(cfg.d_sigma - 0.03) < 1e-9 and cfg.lambda_colour == 5.0 and abs(cfg.lr - 1e-3) < 1e-9
     assert cfg.precision == native.VMAP_FP32
+
+
+def test_binding_reuses_the_ray_count_array_only_while_the_counts_are_unchanged():
+    """The binding's host array of rays per object is rebuilt whenever the
+    counts change, also when the caller mutates the same list in place."""
+    import types
+    from paper_2302_01838_b300.api import VMap
+    holder = types.SimpleNamespace()
+    counts = [3, 0, 7]
+    a = VMap._counts(holder, counts)
+    assert list(a) == [3, 0, 7]
+    assert VMap._counts(holder, [3, 0, 7]) is a
+    counts[1] = 5
+    b = VMap._counts(holder, counts)
+    assert list(b) == [3, 5, 7]
+    assert list(VMap._counts(holder, (1, 2))) == [1, 2]
+    import numpy as np
+    assert list(VMap._counts(holder, np.array([4, 4, 4]))) == [4, 4, 4]
