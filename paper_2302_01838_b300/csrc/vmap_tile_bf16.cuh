@@ -349,6 +349,7 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
         const long long sbase = th.sbase;
         const float* P = th.P;
         const float cx = th.cx, cy = th.cy, cz = th.cz, sc = th.sc;
+        const float isc = 1.f / sc;   // points are normalised by one multiply (within 1 ulp of dividing)
 
         // ---- rays, depths, points; weights at the start of a run ---------------
         // (after the first tile of a training range, the previous tile's
@@ -395,9 +396,9 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
             if (m < M) {
                 const float* d = rays + (m / S) * RAYF;
                 const float t = tsm[m];
-                x0 = (fmaf(t, d[3], d[0]) - cx) / sc;
-                x1 = (fmaf(t, d[4], d[1]) - cy) / sc;
-                x2 = (fmaf(t, d[5], d[2]) - cz) / sc;
+                x0 = (fmaf(t, d[3], d[0]) - cx) * isc;
+                x1 = (fmaf(t, d[4], d[1]) - cy) * isc;
+                x2 = (fmaf(t, d[5], d[2]) - cz) * isc;
             }
             encode_row_half(sp, x0, x1, x2, m, half, G0, nullptr);
         }
