@@ -41,19 +41,25 @@ FP32_LANES_PER_SM = 128      # FFMA lanes per SM (4 SMSPs x 32)
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1500)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--precision", choices=["fp32", "bf16"], default="bf16",
                     help="bf16: tcgen05 BF16 GEMMs, FP32 accumulation (default); fp32: plain FP32 SIMT path")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch kernel by kernel instead of graph replay")
     ap.add_argument("--prof-steps", type=int, default=200, help="steps of the profiled kernel-by-kernel pass")
-    ap.add_argument("--fp32-steps", type=int, default=300, help="steps of the FP32 comparison (0: skip)")
+    ap.add_argument("--fp32-steps", type=int, default=1, help="0: skip the FP32 comparison")
     ap.add_argument("--no-ttd", action="store_true", help="skip the time-to-depth-L1 comparison")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=12, help="oracle steps of the CPU baseline sample")
     ap.add_argument("--e2e-steps", type=int, default=1000)
+    ap.add_argument("--window-s", type=float, default=2.0,
+                    help="repeat the K-step timed window for at least this many seconds (clock sampling)")
+    ap.add_argument("--min-windows", type=int, default=5)
+    ap.add_argument("--no-workloads", action="store_true", help="skip the precision200 / many1000 lines")
+    ap.add_argument("--sweep", action="store_true",
+                    help="print the object-count / hidden-width sweep instead of the bench line")
     return ap.parse_args()
 
 
@@ -131,7 +137,11 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index):
-        self.index = index
+        # nvidia-smi numbers the physical GPUs; map the process's device index
+        # through CUDA_VISIBLE_DEVICES when that lists indices
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        self.index = ids[index] if index < len(ids) and all(v.isdigit() for v in ids) else index
         self.proc = None
         self.file = None
 
@@ -254,24 +264,28 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
-def make_context(sc, precision, autotune, reps=3):
+def make_context(sc, precision, autotune, reps=3, extra=8, n_add=None):
+    """A context sized for the whole scene holding its first n_add objects
+    (all by default), launch shape autotuned on their batch."""
     from paper_2302_01838_b300.api import VMap
     from paper_2302_01838_b300.native import VMAP_BF16, VMAP_FP32
     objs = sc["objects"]
+    n_add = len(objs) if n_add is None else n_add
     R = [o["rays"] for o in objs]
     prec = VMAP_BF16 if precision == "bf16" else VMAP_FP32
-    vm = VMap(max_objects=len(objs) + 8, max_rays_total=2 * sum(R),
+    vm = VMap(max_objects=len(objs) + extra, max_rays_total=2 * sum(R) + 8192,
               max_pool_rays=sum(o["pool"].shape[0] for o in objs) + 16, B=sc["B"], seed=sc["seed"], precision=prec)
-    for k, o in enumerate(objs):
+    for k, o in enumerate(objs[:n_add]):
         vm.add_object(o["pool"], hidden=o["H"], center=o["center"], scale=float(o["scale"]),
                       n_surface=o["n_surface"], n_strat=o["n_strat"], init_params=o["init"], stream_id=k)
     if autotune:
-        vm.autotune(R, reps=reps)
+        vm.autotune(R[:n_add], reps=reps)
     return vm
 
 
-def timed_steps(vm, R, steps, flush, loss):
-    """Device milliseconds of `steps` steps, L2 flushed between steps (outside the intervals)."""
+def step_intervals(vm, R, steps, flush, loss):
+    """Device milliseconds of each of `steps` steps (CUDA events on the
+    context's stream), L2 flushed between steps (outside the intervals)."""
     import torch
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     for i in range(steps):
@@ -280,36 +294,208 @@ def timed_steps(vm, R, steps, flush, loss):
         vm.step(R, loss)   # sample_rays + train_step as one launch sequence
         ev[i][1].record()
     torch.cuda.synchronize()
-    return sum(a.elapsed_time(b) for a, b in ev)
+    return [a.elapsed_time(b) for a, b in ev]
 
 
-def time_to_depth(seed=100, n_train=1000, train_steps=1000, epochs=100, n_held=200, target=0.04):
+def timed_windows(vm, R, K, flush, loss, min_s, min_windows, world=1):
+    """Windows of exactly K steps, each bracketed by a barrier and a
+    synchronize, repeated until min_s seconds and min_windows windows have
+    passed (so the clock sampler sees the timed work); returns the device
+    milliseconds of every window (max over ranks)."""
+    import torch
+    import torch.distributed as dist
+    from paper_2302_01838_b300 import sharding
+    out = []
+    t0 = time.perf_counter()
+    while len(out) < min_windows or time.perf_counter() - t0 < min_s:
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ms = sum(step_intervals(vm, R, K, flush, loss))
+        if world > 1:
+            dist.barrier()
+        out.append(sharding.max_over_ranks(ms) if world > 1 else ms)
+        if len(out) >= 100000:
+            break
+    return out
+
+
+def median(x):
+    y = sorted(x)
+    n = len(y)
+    return 0.5 * (y[(n - 1) // 2] + y[n // 2])
+
+
+def profile_pass(vm, R, steps, flush, loss):
+    """Kernel by kernel (every launch bracketed by the library's CUDA events):
+    {kernel: (launches, total device ms)}."""
+    for _ in range(3):
+        vm.step(R, loss)
+    vm.profile_reset()
+    vm.profile_enable(True)
+    step_intervals(vm, R, steps, flush, loss)
+    vm.profile_enable(False)
+    return vm.profile()
+
+
+def fp32_peak_tflops(props, peaks):
+    sm_max = peaks.get("sm_max_mhz", 2032.0)
+    return props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12, sm_max
+
+
+def roofline_of(prof, objs, precision, peaks, props, prof_steps):
+    """Roofline of the dominant tile kernel: algorithmic flops per launch /
+    its mean CUDA-event duration, against the measured BF16 burst peak
+    (tensor-core kernels) or the FP32 FFMA peak (FP32 SIMT kernels)."""
+    tiles = {k: v for k, v in prof.items() if k.startswith(("k_tile", "k_wide"))}
+    dom = max(tiles, key=lambda k: tiles[k][1])
+    flops = kernel_flops(dom, objs)
+    n_l, dom_ms = tiles[dom]
+    achieved = flops / (dom_ms / n_l * 1e-3) / 1e12
+    if dom.startswith(("k_tile_bf16", "k_wide")):
+        peak, bound = peaks.get("bf16_tflops", 1800.0), "tensor"
+        note = "measured cuBLAS BF16 burst (MEASURED_PEAKS.json bf16_tflops)"
+    else:
+        peak, sm_max = fp32_peak_tflops(props, peaks)
+        bound = "alu"
+        note = f"FP32 FFMA: {props.multi_processor_count} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {sm_max:.0f} MHz"
+    return {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": traffic_for(dom), "peak_note": note, "flops_per_launch": flops,
+            "avg_launch_ms": dom_ms / n_l,
+            "timing": f"CUDA events around each launch, {prof_steps}-step kernel-by-kernel pass"}
+
+
+def kernel_table(prof):
+    total = sum(v[1] for v in prof.values())
+    return {k: {"launches": n, "total_ms": round(t_, 4), "share": round(t_ / total, 4)} for k, (n, t_) in prof.items()}
+
+
+def measure_workload(sc, precision, K, W, flush, args, peaks, props, clocks=False, admit=0):
+    """One workload, one precision: autotuned launch shape, graph replay,
+    median of repeated K-step windows; the dominant kernel's roofline from a
+    kernel-by-kernel pass. admit > 0: the last `admit` objects are held back
+    and admitted after the timed windows into the captured step (no
+    re-capture), and a second set of windows is timed."""
+    import torch
+    objs = sc["objects"]
+    R = [o["rays"] for o in objs]
+    n_first = len(objs) - admit
+    vm = make_context(sc, precision, not args.no_autotune, n_add=n_first)
+    R0 = R[:n_first]
+    loss = torch.empty(len(objs) + 8, device="cuda")
+    prof = profile_pass(vm, R0, args.prof_steps, flush, loss)
+    vm.set_graph(not args.no_graph)
+    for _ in range(max(W, 3)):
+        vm.step(R0, loss)
+    sampler = ClockSampler(torch.cuda.current_device()) if clocks else None
+    if sampler:
+        sampler.start()
+    win = timed_windows(vm, R0, K, flush, loss, args.window_s, args.min_windows)
+    clk = sampler.stop() if sampler else None
+    sps = sum(r * (o["n_surface"] + o["n_strat"]) for r, o in zip(R0, objs))
+    ms = median(win) / K
+    out = {"value": sps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps_per_s": 1e3 / ms,
+           "steps": K, "windows": len(win), "samples_per_step": sps, "objects": n_first,
+           "dtype": "f32" if precision == "fp32" else "bf16+f32",
+           "launch_shape": vm.get_launch() if not args.no_autotune else None,
+           "roofline": roofline_of(prof, objs[:n_first], precision, peaks, props, args.prof_steps),
+           "kernels": kernel_table(prof), "clocks": clk, "frozen_objects": len(vm.sync_status())}
+    if admit:
+        for k in range(n_first, len(objs)):
+            o = objs[k]
+            vm.add_object(o["pool"], hidden=o["H"], center=o["center"], scale=float(o["scale"]),
+                          n_surface=o["n_surface"], n_strat=o["n_strat"], init_params=o["init"], stream_id=k)
+        for _ in range(3):
+            vm.step(R, loss)
+        win2 = timed_windows(vm, R, K, flush, loss, args.window_s / 2, args.min_windows)
+        sps2 = sum(r * (o["n_surface"] + o["n_strat"]) for r, o in zip(R, objs))
+        ms2 = median(win2) / K
+        out["after_admission"] = {"objects": len(objs), "admitted": admit, "value": sps2 / (ms2 * 1e-3),
+                                  "ms_per_step": ms2, "samples_per_step": sps2, "windows": len(win2),
+                                  "note": "admitted between steps into the captured step (no re-capture)",
+                                  "frozen_objects": len(vm.sync_status())}
+    vm.close()
+    return out
+
+
+def time_to_depth(seed=100, n_train=1000, train_steps=2000, epochs=100, n_held=200, target=0.04,
+                  max_steps=2000):
     """Reduced form of the warm-start experiment (paper_2302_01838_b300.warmstart):
-    steps and CUDA-event train time until the mean held-out depth-L1 < target."""
+    the hypernetwork learns from shapes trained 2,000 steps (converged: depth-L1
+    < 1 cm or 2,000 steps); for each form, steps and CUDA-event train time
+    until the mean held-out depth-L1 < target, and per object the first step
+    and train time at which its own depth-L1 < 1 cm (training runs on to
+    max_steps for that); the final depth-L1 also with the training sampler."""
     from paper_2302_01838_b300 import scenes, warmstart as ws
     t0 = time.time()
     X, T = ws.produce_dataset(n_train, seed, train_steps)
     hyp = ws.train_hypernet(X, T, epochs=epochs)
     prep = time.time() - t0
     held = scenes.scene_shapes(seed + 10 ** 6, n_held, offmask=ws.OFFMASK)
-    out = {"target_m": target, "heldout_objects": n_held, "train_shapes": n_train,
-           "train_steps_per_shape": train_steps, "hypernet_epochs": epochs, "prep_s": round(prep, 2)}
+    out = {"target_m": target, "obj_target_m": 0.01, "heldout_objects": n_held, "train_shapes": n_train,
+           "train_steps_per_shape": train_steps, "hypernet_epochs": epochs, "max_steps": max_steps,
+           "prep_s": round(prep, 2)}
     for form in ("plain", "batched", "warm"):
         r = ws.time_to_target(held["objects"], held["B"], seed, form, hyper=hyp if form == "warm" else None,
-                              target=target)
-        out[form] = {"reached": r["reached"], "steps": r["steps"], "train_ms": round(r["train_ms"], 2),
-                     "depth_l1_m": round(r["final_depth_l1"], 5)}
+                              target=target, max_steps=max_steps, run_to=max_steps, guided=True)
+        rnd = lambda x, n=5: None if x is None else round(x, n)
+        out[form] = {"reached": r["reached"], "steps": r["steps"], "train_ms": rnd(r["train_ms"], 2),
+                     "depth_l1_m": rnd(r["depth_l1_at_stop"]),
+                     "frac_below_1cm": r["obj_reached_frac"], "median_steps_to_1cm": r["obj_median_steps"],
+                     "median_ms_to_1cm": rnd(r["obj_median_ms"], 2), "total_steps": r["total_steps"],
+                     "total_ms": rnd(r["total_ms"], 2), "final_depth_l1_m": rnd(r["final_depth_l1"]),
+                     "final_depth_l1_median_m": rnd(r["final_depth_l1_median"]),
+                     "final_depth_l1_guided_m": rnd(r["final_depth_l1_guided"]),
+                     "final_depth_l1_guided_median_m": rnd(r["final_depth_l1_guided_median"]),
+                     "final_frac_below_1cm_guided": r["frac_below_1cm_guided"]}
     out["forms"] = {"plain": "FP32, kernel by kernel, seeded random init",
                     "batched": "BF16 tensor cores, CUDA graphs, autotuned, seeded random init",
                     "warm": "as batched, init predicted by the set-encoder hypernetwork"}
+    out["eval"] = ("depth_l1: 96 uniform midpoints between the ray's entry and exit of the object's box; "
+                   "guided: the training sampler's depth-guided samples (Eq. 1-2) on the same held-out rays")
     return out
+
+
+def run_sweep(args):
+    """The paper's scaling axes (section 4.3, Fig. vectorised-training ablation):
+    step time against the object count (120 rays, hidden 32) and against the
+    hidden width (50 objects x 120 rays), BF16 and FP32. One JSON line."""
+    import torch
+    from paper_2302_01838_b300 import scenes
+    torch.cuda.set_device(0)
+    peaks = measured_peaks()
+    props = torch.cuda.get_device_properties(0)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device="cuda")
+    pts = []
+
+    def scene_of(n, H):
+        sc = scenes.scene_small(seed=9, n_objects=n, rays=120)
+        rng = __import__("numpy").random.default_rng(99)
+        for o in sc["objects"]:
+            o["H"] = H
+            o["init"] = scenes.init_weights(rng, H)
+        return sc
+
+    axes = [("objects", n, 32) for n in (1, 10, 50, 100, 200, 1000)] + \
+           [("hidden", 50, H) for H in (16, 32, 64, 128)]
+    for axis, n, H in axes:
+        sc = scene_of(n, H)
+        for prec in ("bf16", "fp32"):
+            r = measure_workload(sc, prec, args.steps, args.warmup, flush, args, peaks, props)
+            pts.append({"axis": axis, "objects": n, "hidden": H, "precision": prec,
+                        "ms_per_step": r["ms_per_step"], "pts_per_s": r["value"],
+                        "samples_per_step": r["samples_per_step"],
+                        "roofline": {k: r["roofline"][k] for k in ("kernel", "bound", "achieved", "peak", "frac")}})
+            print(json.dumps(pts[-1]), flush=True, file=sys.stderr)
+    print(json.dumps({"sweep": "vectorised step time vs object count and hidden width (120 rays, 22 samples)",
+                      "unit": "ms/step", "points": pts}), flush=True)
 
 
 def run_ours(args):
     import numpy as np
     import torch
     import torch.distributed as dist
-    from paper_2302_01838_b300 import sharding
+    from paper_2302_01838_b300 import scenes, sharding
 
     rank, world, local = dist_env()
     if world > 1:
@@ -320,36 +506,27 @@ def run_ours(args):
     R = [o["rays"] for o in objs]
     K = len(objs)
     sps = samples_per_step(sc)
+    peaks = measured_peaks()
+    props = torch.cuda.get_device_properties(local)
     vm = make_context(sc, args.precision, not args.no_autotune)
     launch = vm.get_launch() if not args.no_autotune else None
     loss = torch.empty(K, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, device="cuda")
 
     # ---- profiled kernel-by-kernel pass: per-kernel device time ----------------
-    for _ in range(3):
-        vm.step(R, loss)
-    vm.profile_reset()
-    vm.profile_enable(True)
-    timed_steps(vm, R, args.prof_steps, flush, loss)
-    vm.profile_enable(False)
-    prof = vm.profile()
+    prof = profile_pass(vm, R, args.prof_steps, flush, loss)
     launches_per_step = sum(n for n, _ in prof.values()) / args.prof_steps
 
-    # ---- the timed region -------------------------------------------------------
+    # ---- the timed region: windows of exactly K steps, repeated -----------------
     if not args.no_graph:
         vm.set_graph(True)
     for _ in range(max(args.warmup, 3)):
         vm.step(R, loss)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
-    ms = timed_steps(vm, R, args.steps, flush, loss)
-    if world > 1:
-        dist.barrier()
+    win = timed_windows(vm, R, args.steps, flush, loss, args.window_s, args.min_windows, world)
     clk = clocks.stop()
-    ms_max = sharding.max_over_ranks(ms)
+    ms_max = median(win)
     assert np.all(np.isfinite(loss.cpu().numpy())), "non-finite loss"
     assert vm.sync_status() == [], "objects frozen during the bench"
 
@@ -374,38 +551,25 @@ def run_ours(args):
     e2e_s = sharding.max_over_ranks(e2e_s)
     vm.close()
 
-    # ---- the plain FP32 path on the same workload --------------------------------
+    # ---- the plain FP32 path on the same workload (precision-matched to the paper) --
     fp32 = None
-    if args.precision == "bf16" and args.fp32_steps > 0:
-        v32 = make_context(sc, "fp32", not args.no_autotune)
-        if not args.no_graph:
-            v32.set_graph(True)
-        for _ in range(3):
-            v32.step(R, loss)
-        ms32 = sharding.max_over_ranks(timed_steps(v32, R, args.fp32_steps, flush, loss))
-        v32.close()
-        fp32 = {"value": world * sps * args.fp32_steps / (ms32 * 1e-3), "unit": UNIT,
-                "ms_per_step": ms32 / args.fp32_steps, "steps_per_s": 1e3 * args.fp32_steps / ms32,
-                "steps": args.fp32_steps}
+    if args.precision == "bf16" and args.fp32_steps > 0 and world == 1:
+        fp32 = measure_workload(sc, "fp32", args.steps, args.warmup, flush, args, peaks, props, clocks=True)
+        fp32["note"] = "room50 on the FP32 SIMT kernels (the paper's precision), same windows"
+
+    # ---- the other named workloads, BF16 ------------------------------------------
+    workloads = {}
+    if world == 1 and not args.no_workloads:
+        workloads["precision200"] = measure_workload(scenes.scene_small(seed=3, n_objects=200, rays=120), "bf16",
+                                                     args.steps, args.warmup, flush, args, peaks, props)
+        workloads["precision200"]["config"] = "200 objects x 120 rays x 22 samples, hidden 32, BF16 tensor cores"
+        workloads["many1000"] = measure_workload(scenes.scene_many(), "bf16", args.steps, args.warmup, flush, args,
+                                                 peaks, props, admit=8)
+        workloads["many1000"]["config"] = ("1,000 objects, hidden {16,32,64}, rays log-uniform 16-1,024, "
+                                           "samples per ray {16,22,32}, BF16, one persistent launch per width "
+                                           "class, graph-replayed; 8 objects admitted after the first windows")
 
     if rank == 0:
-        peaks = measured_peaks()
-        props = torch.cuda.get_device_properties(local)
-        sm_max = peaks.get("sm_max_mhz", 2032.0)
-        fp32_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-        tiles = {k: v for k, v in prof.items() if k.startswith(("k_tile", "k_wide"))}
-        dom = max(tiles, key=lambda k: tiles[k][1])
-        flops = kernel_flops(dom, objs)
-        n_l, dom_ms = tiles[dom]
-        achieved = flops / (dom_ms / n_l * 1e-3) / 1e12
-        tensor = dom.startswith(("k_tile_bf16", "k_wide"))
-        if tensor:
-            peak, bound = peaks.get("bf16_tflops", 1800.0), "tensor"
-            peak_note = "measured cuBLAS BF16 burst (MEASURED_PEAKS.json bf16_tflops)"
-        else:
-            peak, bound = fp32_peak, "alu"
-            peak_note = f"FP32 FFMA: {props.multi_processor_count} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_max:.0f} MHz"
-        total_prof = sum(v[1] for v in prof.values())
         value = world * sps * args.steps / (ms_max * 1e-3)
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -418,13 +582,11 @@ def run_ours(args):
                        "precision": args.precision, "graph": not args.no_graph, "launch_shape": launch,
                        "objects_per_gpu": K, "samples_per_step_per_gpu": sps,
                        "rays_per_step_per_gpu": sum(R), "l2": "flushed (512 MB write) between timed steps",
+                       "timing": f"median of {len(win)} windows of {args.steps} steps (CUDA events per step, "
+                                 f"summed per window), windows repeated for >= {args.window_s} s",
                        "parallelism": f"objects sharded, {world} independent scene(s), no collective"},
-            "roofline": {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic_for(dom),
-                         "peak_note": peak_note, "flops_per_launch": flops, "avg_launch_ms": dom_ms / n_l,
-                         "timing": f"CUDA events around each launch, {args.prof_steps}-step kernel-by-kernel pass"},
-            "kernels": {k: {"launches": n, "total_ms": round(t_, 4), "share": round(t_ / total_prof, 4)}
-                        for k, (n, t_) in prof.items()},
+            "roofline": roofline_of(prof, objs, args.precision, peaks, props, args.prof_steps),
+            "kernels": kernel_table(prof),
             "gpu_launches": int(round(launches_per_step * args.steps)),
             "e2e": {"value": world * sps * args.e2e_steps / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": int(sum(R) * 48), "d2h_bytes_per_step": int(K * 4),
@@ -433,6 +595,8 @@ def run_ours(args):
         }
         if fp32:
             out["fp32"] = fp32
+        if workloads:
+            out["workloads"] = workloads
         if world == 1 and not args.no_ttd:
             out["time_to_depth_l1"] = time_to_depth()
         if world == 1 and not args.no_cpu_baseline:
@@ -446,6 +610,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.sweep:
+        run_sweep(args)
     else:
         run_ours(args)
 

@@ -263,8 +263,25 @@ vmap_status vmap_batch_info(vmap_ctx* ctx, int* n_rays, long long* n_samples);
 vmap_status vmap_get_samples(vmap_ctx* ctx, int* pick, float* t);
 
 /* Synchronise and report frozen objects: *n_faulted (HOST) and, if ids is
- * not NULL, up to max_ids of their indices. Returns VMAP_ERR_NAN if any. */
+ * not NULL, up to max_ids of their indices. Returns VMAP_ERR_NAN if any.
+ * Returns VMAP_ERR_TIMEOUT (and leaves *n_faulted unset) if a tensor-core
+ * kernel gave up one of its bounded waits since the last report; the flag is
+ * cleared by this report. While the flag is set, training steps update no
+ * object (every loss is NaN, no step count advances) and vmap_forward /
+ * vmap_backward write NaN losses and no gradient: a step whose wait gave up
+ * has incomplete gradient sums, so it is void rather than applied. */
 vmap_status vmap_sync_status(vmap_ctx* ctx, int* n_faulted, int* ids, int max_ids);
+
+/* Failure detection of the BF16 tensor-core kernels: every wait for an MMA
+ * commit or a bulk copy polls its mbarrier at most `polls` times (default
+ * 2^26, far longer than any MMA takes) before it gives up; the CTA then
+ * stops its work, waits (with the fixed default bound) for the MMAs and
+ * copies it has already issued, frees its tensor memory and exits, and the
+ * context's error flag is set (see vmap_sync_status). polls = 0 gives up at
+ * once: a way to exercise this path without making any MMA fail. Captured
+ * graphs are dropped when the limit changes. polls < 0: VMAP_ERR_ARG. The
+ * paper has no counterpart (it runs no custom kernels). */
+vmap_status vmap_set_wait_limit(vmap_ctx* ctx, long long polls);
 
 /* Tracing: with profiling enabled, every kernel launch is bracketed by CUDA
  * events on the context stream (in graph mode, every graph replay, as the
@@ -363,10 +380,14 @@ vmap_status vmap_warmstart(vmap_ctx* ctx, int obj, vmap_hyper* h, const float* X
  *   cuda_stream: cudaStream_t the work is queued on (asynchronous).
  * Returns VMAP_ERR_CAPACITY if n_rays exceeds 1024, VMAP_ERR_ARG for other
  * invalid arguments (nothing is queued then), VMAP_ERR_CUDA if a launch fails.
- * The first call on a device looks up the array's device address and sets
- * kernel attributes; make that first call before any stream capture. All
- * calls share the one array: calls whose work overlaps on the GPU (other
- * streams, other threads) race; serialise them on one stream. */
+ * The first call on a device (with that device current) looks up the
+ * array's device address and sets kernel attributes; make that first call
+ * before any stream capture. Each call hands its per-call values (the
+ * object record, ray count and step count) to the device as kernel
+ * arguments, so no host-to-device copy is queued. All calls share the one
+ * array, which keeps the last call's contents (every call rewrites what it
+ * reads): calls whose work overlaps on the GPU (other streams, other
+ * threads) race; serialise them on one stream. */
 vmap_status vmap_object_grad_static(const vmap_config* cfg, const vmap_object_desc* desc,
                                     const float* params, int step, float* grad, float* loss,
                                     void* cuda_stream);

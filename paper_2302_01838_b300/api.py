@@ -151,6 +151,10 @@ class VMap:
     def set_graph(self, on=True):
         self._check(self.lib.vmap_set_graph(self.h, int(bool(on))))
 
+    def set_wait_limit(self, polls):
+        """Polls before a tensor-core wait gives up (default 2**26; 0: at once)."""
+        self._check(self.lib.vmap_set_wait_limit(self.h, int(polls)))
+
     def get_launch(self):
         rt, gm = (ctypes.c_int * 4)(), (ctypes.c_int * 4)()
         self._check(self.lib.vmap_get_launch(self.h, rt, gm))

@@ -125,6 +125,7 @@ struct vmap_ctx {
     long long img_used = 0, img_cap = 0;
     std::vector<long long> img_off;
     int* err_d = nullptr;   // set by a kernel whose bounded wait gave up
+    long long wait_polls = MMA_WAIT_LIMIT;   // polls before a tensor-core wait gives up
     // the training step's second loss destination (the caller's out_loss): its
     // address lives on the device, so a captured step writes wherever it points
     float** loss_pp_d = nullptr;
@@ -361,7 +362,7 @@ WideArgs wide_args(vmap_ctx* ctx) {
     TileArgs ta = base_args(ctx);
     ta.tiles = ctx->tiles_d + 3LL * ctx->tile_cap;
     ta.n_tiles = ctx->counts_d + BC_TILES + 3;
-    return WideArgs{ta, ctx->img_d, ctx->img_off_d, ctx->err_d, ctx->act_pp_d, ctx->tile_loss_d, 0};
+    return WideArgs{ta, ctx->img_d, ctx->img_off_d, ctx->err_d, ctx->act_pp_d, ctx->tile_loss_d, 0, ctx->wait_polls};
 }
 
 // overlap: with `after_tile` (the previous kernel in the stream is a BF16 tile
@@ -433,7 +434,7 @@ cudaError_t launch_class(vmap_ctx* ctx, int c, bool after_sample = false) {
     }
     if (uses_tc(ctx, c)) {
         constexpr int BM = MODE == MODE_FORWARD ? MODE_FORWARD : MODE_TRAIN;
-        Bf16Args ba{ta, ctx->img_d, ctx->img_off_d, ctx->err_d};
+        Bf16Args ba{ta, ctx->img_d, ctx->img_off_d, ctx->err_d, ctx->wait_polls};
         switch (c) {
             case 0: return launch_tile_bf16<16, BM>(grid, ctx->stream, ctx->sp, ba, after_sample);
             case 1: return launch_tile_bf16<32, BM>(grid, ctx->stream, ctx->sp, ba, after_sample);
@@ -542,7 +543,8 @@ vmap_status launch_reduce(vmap_ctx* ctx, int mode, const float* grad_loss, float
         (const int*)ctx->counts_d, (const float*)ctx->part_d, ctx->params_d, ctx->bf16 ? nullptr : ctx->wt_d, ctx->m_d,
         ctx->v_d, ctx->steps_d, ctx->status_d, mode, grad_loss, grad_out, loss_out, dcenter_out,
         ctx->bf16 ? ctx->img_d : nullptr, (const long long*)ctx->img_off_d, ctx->done_d,
-        (const int*)(train ? ctx->n_obj_d : nullptr), (float* const*)(train ? ctx->loss_pp_d : nullptr));
+        (const int*)(train ? ctx->n_obj_d : nullptr), (float* const*)(train ? ctx->loss_pp_d : nullptr),
+        (const int*)(ctx->bf16 ? ctx->err_d : nullptr));
     prof_end(ctx, pi);
     if (e != cudaSuccess) return fail(ctx, VMAP_ERR_CUDA, "k_reduce launch failed: %s", cudaGetErrorString(e));
     return VMAP_OK;
@@ -1344,7 +1346,10 @@ vmap_status vmap_sync_status(vmap_ctx* ctx, int* n_faulted, int* ids, int max_id
     CU(cudaStreamSynchronize(ctx->stream));
     int timed_out = 0;
     CU(cudaMemcpy(&timed_out, ctx->err_d, sizeof(int), cudaMemcpyDeviceToHost));
-    if (timed_out) return fail(ctx, VMAP_ERR_TIMEOUT, "a tensor-core wait gave up (MMA did not complete)");
+    if (timed_out) {   // reported once: the flag is cleared, the next steps update objects again
+        CU(cudaMemset(ctx->err_d, 0, sizeof(int)));
+        return fail(ctx, VMAP_ERR_TIMEOUT, "a tensor-core wait gave up (MMA or copy not complete within the poll limit)");
+    }
     int nf = 0;
     for (int k = 0; k < K; ++k)
         if (st[k]) {
@@ -1408,6 +1413,16 @@ vmap_status vmap_warmstart(vmap_ctx* ctx, int obj, vmap_hyper* h, const float* X
     CU(cudaMemsetAsync(ctx->steps_d + obj, 0, sizeof(int), ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
     ctx->batch_ready = false;
+    return VMAP_OK;
+}
+
+vmap_status vmap_set_wait_limit(vmap_ctx* ctx, long long polls) {
+    if (!ctx) return VMAP_ERR_ARG;
+    if (polls < 0) return fail(ctx, VMAP_ERR_ARG, "negative poll limit");
+    if (polls != ctx->wait_polls) {
+        drop_graphs(ctx);   // captured launches carry the limit as an argument
+        ctx->wait_polls = polls;
+    }
     return VMAP_OK;
 }
 

@@ -8,8 +8,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "../../include/vmap.h"
 
@@ -53,7 +55,21 @@ constexpr size_t SCRATCH_BYTES = align256(OFF_PART + sizeof(float) * (NA_GRID + 
 // Shared by every call on a device (about 4.8 MB); see vmap_object_grad_static.
 static __device__ __align__(256) unsigned char g_scratch[SCRATCH_BYTES];
 
-unsigned char* g_scratch_dev[NA_MAX_DEVICES] = {nullptr};
+// Per device: the array's device address, looked up once (under na_mutex).
+std::atomic<unsigned char*> g_scratch_dev[NA_MAX_DEVICES];
+std::mutex na_mutex;
+
+// The call's object record and header ints reach the scratch array through
+// this kernel's by-value arguments, so no host-to-device copy is queued.
+__global__ void k_na_init(ObjDev o, int4 head, ObjDev* objs, int* ints) {
+    if (threadIdx.x == 0) {
+        *objs = o;
+        ints[0] = head.x;
+        ints[1] = head.y;
+        ints[2] = head.z;
+        ints[3] = head.w;
+    }
+}
 
 template <int H>
 cudaError_t prepare_tile() {
@@ -90,15 +106,20 @@ extern "C" vmap_status vmap_object_grad_static(const vmap_config* cfg, const vma
     // one-time set-up per device, with that device current
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) return VMAP_ERR_CUDA;
-    if (!g_scratch_dev[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return VMAP_ERR_CUDA;
-        if (prepare_tile<16>() != cudaSuccess || prepare_tile<32>() != cudaSuccess ||
-            prepare_tile<64>() != cudaSuccess || prepare_tile<128>() != cudaSuccess)
-            return VMAP_ERR_CUDA;
-        g_scratch_dev[dev] = (unsigned char*)p;
+    unsigned char* base = g_scratch_dev[dev].load(std::memory_order_acquire);
+    if (!base) {
+        std::lock_guard<std::mutex> lock(na_mutex);
+        base = g_scratch_dev[dev].load(std::memory_order_relaxed);
+        if (!base) {
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return VMAP_ERR_CUDA;
+            if (prepare_tile<16>() != cudaSuccess || prepare_tile<32>() != cudaSuccess ||
+                prepare_tile<64>() != cudaSuccess || prepare_tile<128>() != cudaSuccess)
+                return VMAP_ERR_CUDA;
+            base = (unsigned char*)p;
+            g_scratch_dev[dev].store(base, std::memory_order_release);
+        }
     }
-    unsigned char* base = g_scratch_dev[dev];
     cudaStream_t st = (cudaStream_t)cuda_stream;
 
     ObjDev* objs = (ObjDev*)(base + OFF_OBJ);
@@ -140,10 +161,8 @@ extern "C" vmap_status vmap_object_grad_static(const vmap_config* cfg, const vma
     o.pool_n = desc->n_rays;
     o.stream = desc->stream;
     o.active = 1;
-    const int head[4] = {1, (int)desc->n_rays, 0, step};
-    // pageable sources: both copies are staged before the calls return
-    if (cudaMemcpyAsync(objs, &o, sizeof o, cudaMemcpyHostToDevice, st) != cudaSuccess) return VMAP_ERR_CUDA;
-    if (cudaMemcpyAsync(ints, head, sizeof head, cudaMemcpyHostToDevice, st) != cudaSuccess) return VMAP_ERR_CUDA;
+    // n_obj, requested rays, status (0: the reduce writes gradient and loss), step count
+    k_na_init<<<1, 32, 0, st>>>(o, make_int4(1, (int)desc->n_rays, 0, step), objs, ints);
 
     k_shadow<<<16, 256, 0, st>>>(params, wt, H);
 
@@ -169,8 +188,8 @@ extern "C" vmap_status vmap_object_grad_static(const vmap_config* cfg, const vma
     a.items = items;
     a.counts = counts;
     k_build<<<1, BUILD_THREADS, 0, st>>>(a);
-    k_sample<<<(NA_MAX_RAYS + SAMPLE_RAYS_PER_BLOCK - 1) / SAMPLE_RAYS_PER_BLOCK, 32 * SAMPLE_RAYS_PER_BLOCK, 0, st>>>(sp, objs, ob, bobj, bray, nullptr, counts, desc->rays, 1, ints + 3,
-                                                       pick, tbuf);
+    k_sample<<<(desc->n_rays + SAMPLE_RAYS_PER_BLOCK - 1) / SAMPLE_RAYS_PER_BLOCK, 32 * SAMPLE_RAYS_PER_BLOCK, 0,
+               st>>>(sp, objs, ob, bobj, bray, nullptr, counts, desc->rays, 1, ints + 3, pick, tbuf);
     TileArgs ta{};
     ta.objs = objs;
     ta.obs = ob;
@@ -190,6 +209,6 @@ extern "C" vmap_status vmap_object_grad_static(const vmap_config* cfg, const vma
     // the step slot holds `step`, the status slot 0: the reduce writes the gradient and the loss
     k_reduce<<<8, REDUCE_THREADS, 0, st>>>(sp, objs, ob, items, counts, part, nullptr, nullptr, nullptr, nullptr,
                                 ints + 3, ints + 2, RED_GRAD, nullptr, grad, loss, nullptr, nullptr, nullptr,
-                                nullptr, nullptr, nullptr);
+                                nullptr, nullptr, nullptr, nullptr);
     return cudaGetLastError() == cudaSuccess ? VMAP_OK : VMAP_ERR_CUDA;
 }

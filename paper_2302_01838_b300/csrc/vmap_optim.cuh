@@ -112,7 +112,8 @@ __global__ void __launch_bounds__(REDUCE_THREADS, 3) k_reduce(StepParams sp, con
                                                            float* __restrict__ dcenter_out,
                                                            __nv_bfloat16* img, const long long* __restrict__ img_off,
                                                            int* done, const int* __restrict__ n_obj,
-                                                           float* const* __restrict__ loss_user_pp) {
+                                                           float* const* __restrict__ loss_user_pp,
+                                                           const int* gave_up) {
     const int lane = threadIdx.x & 31;
     const int wpb = blockDim.x >> 5;
     const int n_units = 2 * counts[BC_ITEMS];   // (item, half)
@@ -128,8 +129,8 @@ __global__ void __launch_bounds__(REDUCE_THREADS, 3) k_reduce(StepParams sp, con
             }
     }
     bool wrote_status = false;   // this lane froze its unit's object
-    // one unit: half `half` of chunk `chunk` of object k
-    auto reduce_unit = [&](const int k, const int chunk, const int half) {
+    // one unit: half `half` of chunk `chunk` of object k; false: the step is void
+    auto reduce_unit = [&](const int k, const int chunk, const int half) -> bool {
         const bool head = chunk == 0 && half == 0;   // the warp that reports per-object results
         const ObjDev& ob = objs[k];
         const ObjBatch& bt = obs[k];
@@ -162,6 +163,16 @@ __global__ void __launch_bounds__(REDUCE_THREADS, 3) k_reduce(StepParams sp, con
         // __restrict__, as loads through a restrict-qualified read-only pointer
         // may be hoisted above the wait.
         asm volatile("griddepcontrol.wait;" : "+f"(ibc1), "+f"(ibc2), "+l"(ioff)::"memory");
+        // a tensor-core kernel of this step gave up a wait: its run slots are
+        // incomplete, so no object is updated (losses NaN, steps not advanced)
+        // until the host has read and cleared the flag
+        if (gave_up && *(volatile const int*)gave_up) {
+            if (head && lane == 0) {
+                if (loss_out) loss_out[k] = __int_as_float(0x7fc00000);
+                if (loss_user) loss_user[k] = __int_as_float(0x7fc00000);
+            }
+            return false;
+        }
         // loss terms of the first 32 runs, in flight with the gradient loads below
         float s0 = 0.f, s1 = 0.f, s2 = 0.f;
         if (lane < nr) {
@@ -207,19 +218,19 @@ __global__ void __launch_bounds__(REDUCE_THREADS, 3) k_reduce(StepParams sp, con
                 for (int c = 0; c < 3; ++c) dcenter_out[3 * k + c] = gl * d[c];
             }
         }
-        if (mode == RED_LOSS) return;
+        if (mode == RED_LOSS) return true;
         if (mode == RED_ADAM && (frozen || !isfinite(L))) {
             if (!frozen && head && lane == 0) {
                 status[k] = 1;
                 wrote_status = true;
             }
-            return;
+            return true;
         }
-        if (!act) return;
+        if (!act) return true;
         if (mode == RED_GRAD) {
 #pragma unroll
             for (int i = 0; i < 4; ++i) grad_out[q + i] = gl * at4(g, i);
-            return;
+            return true;
         }
         float4 m = m0, v = v0, th = th0;
         bool bad = false;
@@ -256,13 +267,14 @@ __global__ void __launch_bounds__(REDUCE_THREADS, 3) k_reduce(StepParams sp, con
                 img[ioff + base + cm_off(wn, wk, l == 0 ? DINP : H) / 2] = __float2bfloat16(x);
             }
         }
+        return true;
     };
 #pragma unroll 1
     for (int u = blockIdx.x * wpb + (threadIdx.x >> 5); u < n_units; u += gridDim.x * wpb) {
         const int2 item = items[u >> 1];
         const int k = item.x;
         wrote_status = false;
-        reduce_unit(k, item.y, u & 1);
+        const bool valid = reduce_unit(k, item.y, u & 1);
         if (mode == RED_ADAM && done) {
             // a status write must be visible before the arrival that may let the
             // last warp read the status; nothing else this warp wrote is read here
@@ -273,7 +285,7 @@ __global__ void __launch_bounds__(REDUCE_THREADS, 3) k_reduce(StepParams sp, con
                 const int units = 2 * (int)((param_count(objs[k].hidden) + REDUCE_CHUNK - 1) / REDUCE_CHUNK);
                 if (atomicAdd(done + k, 1) == units - 1) {
                     done[k] = 0;
-                    if (atomicAdd(status + k, 0) == 0) steps[k] += 1;
+                    if (valid && atomicAdd(status + k, 0) == 0) steps[k] += 1;
                 }
             }
         }

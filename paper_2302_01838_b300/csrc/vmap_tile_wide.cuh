@@ -86,6 +86,7 @@ struct WideArgs {
     unsigned char* const* act;    // device cell holding the activation buffer (tile-indexed)
     float* tile_loss;             // [tiles][4]: depth, colour, occupancy sums of each tile
     int loss_only;                // k_wide_dw: only fold the tile losses into the run slots
+    long long polls;              // polls before an MMA or copy wait gives up
 };
 
 // bits (v[j] > 0) of 8 values, placed at bit offset `at` of a 64-bit word
@@ -144,10 +145,17 @@ __global__ void __launch_bounds__(WIDE_THREADS, 1) k_wide_fb(StepParams sp, Wide
     int npick = 0;                       // pick of the next tile's ray `tid`
 
     // Every thread waits for an MMA commit by itself (no CTA barrier); a wait
-    // that gave up is agreed on at the next CTA barrier.
-    bool wfail = false;
+    // that gave up is agreed on at the next CTA barrier, before any further MMA
+    // is issued, so a give-up leaves at most one commit outstanding: its parity
+    // is kept and drained before tensor memory is freed.
+    bool wfail = false, lost = false;
+    uint32_t lpar = 0;
     auto wait_mma = [&]() {
-        wfail |= !mbar_wait(mbar, phase, MMA_WAIT_LIMIT);
+        if (!mbar_wait(mbar, phase, wa.polls)) {
+            wfail = true;
+            lost = true;
+            lpar = phase;
+        }
         phase ^= 1;
         tc_fence_after();
     };
@@ -250,7 +258,7 @@ __global__ void __launch_bounds__(WIDE_THREADS, 1) k_wide_fb(StepParams sp, Wide
         if (abort) break;
         if (GRAD) record(at + WideAct::G0, G0, TM * DINP * 2);
         if (first) {
-            const bool ok = mbar_wait(wbar, wphase, MMA_WAIT_LIMIT);
+            const bool ok = mbar_wait(wbar, wphase, wa.polls);
             if (__syncthreads_or(!ok)) {
                 abort = true;
                 if (tid == 0) atomicExch(wa.err, 1);
@@ -429,7 +437,10 @@ __global__ void __launch_bounds__(WIDE_THREADS, 1) k_wide_fb(StepParams sp, Wide
         __syncthreads();
         tc_fence_after();
     }
-    if (abort && wpend) mbar_wait(wbar, wphase, MMA_WAIT_LIMIT);
+    // drain (bounded) what a give-up left in flight: the MMA commit given up on
+    // and a weight copy; then prefetches and activation-record stores
+    if (lost) mbar_wait(mbar, lpar, DRAIN_POLLS);
+    if (wpend) mbar_wait(wbar, wphase, DRAIN_POLLS);
     cp_async_wait_all();   // prefetches issued before an abort land before the CTA exits
     if (tid == 0) bulk_wait_all();   // every activation record is written before the CTA exits
     // when launched behind a tile kernel (programmatic stream serialization),
@@ -557,7 +568,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_wide_dw(WideArgs wa) {
             lacc[0] += l4.x; lacc[1] += l4.y; lacc[2] += l4.z;
         }
         // stage s holds tile i
-        const bool ok = mbar_wait(full + s, par, MMA_WAIT_LIMIT);
+        const bool ok = mbar_wait(full + s, par, wa.polls);
         if (__syncthreads_or(!ok)) {
             abort = true;
             if (tid == 0) atomicExch(wa.err, 1);
@@ -590,7 +601,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_wide_dw(WideArgs wa) {
             const uint32_t pp = (uint32_t)(((i - 1) / C::NST) & 1);
             bool okr = true;
             if (tid == 0) {
-                okr = mbar_wait(empty + sp_, pp, MMA_WAIT_LIMIT);
+                okr = mbar_wait(empty + sp_, pp, wa.polls);
                 if (okr) issue_load(i - 1 + C::NST);
             }
             if (__syncthreads_or(!okr)) {
@@ -608,7 +619,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_wide_dw(WideArgs wa) {
             gp[PC + 3] = 0.f; gp[PC + 4] = 0.f; gp[PC + 5] = 0.f;
         }
         // tile i's MMAs were the run's last (commit order = issue order)
-        const bool okf = mbar_wait(empty + s, par, MMA_WAIT_LIMIT);
+        const bool okf = mbar_wait(empty + s, par, wa.polls);
         if (__syncthreads_or(!okf)) {
             abort = true;
             if (tid == 0) atomicExch(wa.err, 1);
@@ -653,11 +664,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_wide_dw(WideArgs wa) {
         __syncthreads();
         tc_fence_after();
     }
-    if (abort) {
-        // let the bulk copies still in flight land before the CTA exits (bounded)
-        if (tid == 0)
-            for (int u = consumed; u < issued; ++u)
-                mbar_wait(full + u % C::NST, (uint32_t)((u / C::NST) & 1), MMA_WAIT_LIMIT);
+    if (abort && tid == 0) {
+        // drain (bounded) before tensor memory is freed: the bulk copies still in
+        // flight, and the MMAs of the last tile whose MMAs were issued (its
+        // commit is that stage's latest phase and covers every earlier MMA)
+        for (int u = consumed; u < issued; ++u)
+            mbar_wait(full + u % C::NST, (uint32_t)((u / C::NST) & 1), DRAIN_POLLS);
+        if (consumed > 0) {
+            const int u = consumed - 1;
+            mbar_wait(empty + u % C::NST, (uint32_t)((u / C::NST) & 1), DRAIN_POLLS);
+        }
     }
     tc_fence_before();
     __syncthreads();

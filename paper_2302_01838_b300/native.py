@@ -76,6 +76,7 @@ SIGNATURES = {
     "vmap_train_step": (_I, [_P, _P]),
     "vmap_step": (_I, [_P, _IP, _P]),
     "vmap_set_graph": (_I, [_P, _I]),
+    "vmap_set_wait_limit": (_I, [_P, _LL]),
     "vmap_get_launch": (_I, [_P, _IP, _IP]),
     "vmap_set_launch": (_I, [_P, _IP, _IP]),
     "vmap_autotune": (_I, [_P, _IP, _I, ctypes.POINTER(ctypes.c_float)]),

@@ -108,9 +108,36 @@ def depth_l1(vm, objs, ev, dep):
     return np.array([float((dep[k] - ev[k][:, 6]).abs().mean()) for k in range(len(objs))])
 
 
-def time_to_target(objs, B, seed, form, hyper=None, target=0.04, max_steps=3000, every=25):
+def depth_l1_guided(vm, objs, B, seed, ev):
+    """Held-out depth-L1 of every object rendered with the training sampler
+    (Eq. 1-2 depth-guided samples around the measured depth) instead of the
+    96 uniform midpoints: an FP32 context holding the trained weights, with
+    the colour and occupancy terms off, evaluates the loss (= mean |D^ - D|)
+    on the held-out rays. Tells floaters in free space that training never
+    samples apart from error near the surface."""
+    K = len(objs)
+    n = [int(e.shape[0]) for e in ev]
+    ctx = VMap(max_objects=K, max_rays_total=sum(n) + 16, max_pool_rays=sum(o["pool"].shape[0] for o in objs) + 16,
+               B=B, seed=seed, precision=VMAP_FP32, lambda_colour=0.0, lambda_occ=0.0)
+    for k, o in enumerate(objs):
+        p = vm.get_object_state(k)[0]
+        ctx.add_object(o["pool"], hidden=o["H"], center=o["center"], scale=float(o["scale"]),
+                       n_surface=o["n_surface"], n_strat=o["n_strat"], init_params=p.cpu().numpy(), stream_id=k)
+    ctx.sample_rays_given(torch.cat(ev).contiguous(), n)
+    L = torch.empty(K, device="cuda")
+    ctx.forward(L)
+    out = L.cpu().numpy().astype(np.float64)
+    ctx.close()
+    return out
+
+
+def time_to_target(objs, B, seed, form, hyper=None, target=0.04, max_steps=3000, every=25,
+                   obj_target=0.01, run_to=0, guided=False):
     """Steps and summed step wall time (CUDA events, evaluation excluded) until
-    the mean held-out depth-L1 drops below `target` metres."""
+    the mean held-out depth-L1 drops below `target` metres. With run_to > 0
+    training goes on to at least run_to steps (up to max_steps, or until every
+    object is below obj_target), recording per object the first evaluation at
+    which its own depth-L1 is below obj_target (step and train time then)."""
     prec = VMAP_FP32 if form == "plain" else VMAP_BF16
     vm = _context(objs, B, seed, prec, graph=form != "plain", autotune=form != "plain")
     if hyper is not None:
@@ -118,14 +145,25 @@ def time_to_target(objs, B, seed, form, hyper=None, target=0.04, max_steps=3000,
             vm.warmstart(k, hyper, torch.from_numpy(o["set_input"]).cuda())
     ev, dep = _eval_setup(objs)
     R = [o["rays"] for o in objs]
-    loss = torch.empty(len(objs), device="cuda")
+    K = len(objs)
+    loss = torch.empty(K, device="cuda")
     # graphs are captured lazily at the first step; the capture is part of the timed work
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ms, curve, step = 0.0, [], 0
+    first_step = np.full(K, -1)
+    first_ms = np.full(K, np.nan)
+
+    def note(d):
+        new = (d < obj_target) & (first_step < 0)
+        first_step[new] = step
+        first_ms[new] = ms
+        curve.append((step, float(d.mean()), float(np.mean(d < obj_target))))
+
     d = depth_l1(vm, objs, ev, dep)
-    curve.append((0, float(d.mean()), float(np.mean(d < 0.01))))
-    reached = d.mean() < target
-    while not reached and step < max_steps:
+    note(d)
+    reached = bool(d.mean() < target)
+    t_steps, t_ms, t_d = (0, 0.0, float(d.mean())) if reached else (None, None, None)
+    while step < max_steps and (not reached or (step < run_to and np.any(first_step < 0))):
         e0.record()
         for _ in range(every):
             vm.sample_rays(R)
@@ -135,11 +173,26 @@ def time_to_target(objs, B, seed, form, hyper=None, target=0.04, max_steps=3000,
         ms += e0.elapsed_time(e1)
         step += every
         d = depth_l1(vm, objs, ev, dep)
-        curve.append((step, float(d.mean()), float(np.mean(d < 0.01))))
-        reached = d.mean() < target
+        note(d)
+        if not reached and d.mean() < target:
+            reached = True
+            t_steps, t_ms, t_d = step, ms, float(d.mean())
+    out = dict(form=form, reached=reached, steps=t_steps if reached else step, train_ms=t_ms if reached else ms,
+               depth_l1_at_stop=t_d if reached else float(d.mean()), final_depth_l1=float(d.mean()),
+               frac_below_1cm=float(np.mean(d < 0.01)), curve=curve, total_steps=step, total_ms=ms)
+    hit = first_step >= 0
+    out["obj_target_m"] = obj_target
+    out["obj_reached_frac"] = float(np.mean(hit))
+    out["obj_median_steps"] = float(np.median(first_step[hit])) if hit.any() else None
+    out["obj_median_ms"] = float(np.median(first_ms[hit])) if hit.any() else None
+    if guided:
+        g = depth_l1_guided(vm, objs, B, seed, ev)
+        out["final_depth_l1_guided"] = float(g.mean())
+        out["frac_below_1cm_guided"] = float(np.mean(g < 0.01))
+        out["final_depth_l1_median"] = float(np.median(d))
+        out["final_depth_l1_guided_median"] = float(np.median(g))
     vm.close()
-    return dict(form=form, reached=bool(reached), steps=step, train_ms=ms, final_depth_l1=float(d.mean()),
-                frac_below_1cm=float(np.mean(d < 0.01)), curve=curve)
+    return out
 
 
 def initial_loss(objs, B, seed, hyper=None):

@@ -8,11 +8,13 @@ Tolerances (FP32 library vs FP64 oracle):
     bias tensor <= 1e-4 (an elementwise bound would be wrong for Adam, whose
     first steps move every weight by about lr * sign(g), so a gradient within
     FP32 noise of zero may legitimately move the other way). Rows of hidden
-    units whose pre-activation came within 1e-5 of zero on some sample (a
-    ReLU kink, where FP32 and FP64 may take different sides) are left out of
-    the weight comparison of the mixed-width stress test; at most half of a
-    layer's rows may be left out. The 20-step small-scene test compares every
-    row.
+    units whose pre-activation came within 5e-6 of zero on some sample (a
+    ReLU kink, where FP32 and FP64 may take different sides) are compared
+    separately in the mixed-width stress test, at 5e-3 relative L2 over
+    those rows (a flipped ReLU' on one sample moves that unit's Adam steps by
+    up to 2 lr per element), and may be at most an eighth of a layer's rows;
+    every other row is held to 1e-4. The 20-step small-scene test compares
+    every row at 1e-4.
 """
 import numpy as np
 import pytest
@@ -28,6 +30,7 @@ pytestmark = pytest.mark.gpu
 
 LOSS_RTOL = 1e-5
 W_RTOL = 1e-4
+KINK_RTOL = 5e-3
 
 
 def _check_samples(vm, scene, rays_per_object, steps):
@@ -112,7 +115,11 @@ def test_train_step_parity_mixed_widths_ragged_tiles():
         assert st == 3
         errs = vh.layer_errors_masked(p.cpu().numpy(), ost[k].params, ost[k].H, skip[k])
         assert max(errs) <= W_RTOL, f"object {k} (H={ost[k].H}): {errs}, kink rows {skip[k]}"
-        assert all(len(r) <= ost[k].H // 2 for r in skip[k].values()), skip[k]
+        # the kink rows themselves, at the looser bound (a flipped ReLU' on one
+        # sample moves that unit's Adam steps by up to 2 lr per element)
+        kerr = vh.layer_errors_rows(p.cpu().numpy(), ost[k].params, ost[k].H, skip[k])
+        assert all(e <= KINK_RTOL for e in kerr.values()), f"object {k}: kink-row errors {kerr}"
+        assert all(len(r) <= ost[k].H // 8 for r in skip[k].values()), skip[k]
 
 
 def test_gradients_and_center_gradient_match_oracle():

@@ -50,7 +50,7 @@ def test_static_entry_point_matches_context_path_twice():
     B = np.ascontiguousarray(np.asarray(sc["B"], np.float32))
     cfg.B = B.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
     cfg.seed = sc["seed"]
-    for k in (1, 3, 0):                       # hidden 32, 128, 16
+    for k in (1, 3, 0, 2):                    # hidden 32, 128, 16, 64
         o = sc["objects"][k]
         one = dict(objects=[o], B=sc["B"], seed=sc["seed"])
         vm = vh.library_context(one, max_rays=2048)
