@@ -307,12 +307,20 @@ vmap_status vmap_set_graph(vmap_ctx* ctx, int on);
 vmap_status vmap_get_launch(vmap_ctx* ctx, int* rays_per_tile, int* grid_mult);
 vmap_status vmap_set_launch(vmap_ctx* ctx, const int* rays_per_tile, const int* grid_mult);
 
-/* Autotuner: for every width class present, time the training tile kernel on
- * the batch rays_per_object (HOST [n_objects]) over `reps` launches for each
- * candidate (rays per tile, grid multiplier) and keep the fastest. Changes no
- * object state; the next step must draw a fresh batch. best_ms: HOST [4] or
- * NULL, the best per-launch milliseconds per class (0 for absent classes).
- * Synchronises. */
+/* Autotuner: choose the launch shape of every width class present by timing
+ * whole training steps (vmap_step: sampling, tile kernels, reduce and Adam,
+ * replayed as a graph when graph mode is on, so the overlapped launches are
+ * what is timed) on the batch rays_per_object (HOST [n_objects]). Candidates
+ * per class: rays per tile (samples per tile = rays x the class's samples per
+ * ray, from the class's tile budget down to one ray) x grid multiplier
+ * (1..2), swept one class at a time with the others held (coordinate
+ * descent, a second pass if the first changed a shape); each candidate is
+ * timed over `reps` steps after two untimed ones. Every object's weights,
+ * moments, step count and status are saved on the device first and restored
+ * at the end, so no object state changes; the next step draws a fresh batch.
+ * best_ms: HOST [4] or NULL, the best step time found (the same value for
+ * every present class, 0 for absent classes). Allocates a temporary copy of
+ * the training state. Synchronises. */
 vmap_status vmap_autotune(vmap_ctx* ctx, const int* rays_per_object, int reps, float* best_ms);
 
 /* ---------------------------------------------------------------------------

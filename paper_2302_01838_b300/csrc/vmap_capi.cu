@@ -329,14 +329,16 @@ cudaError_t launch_tile_c(int c, int grid, cudaStream_t st, const StepParams& sp
     }
 }
 
-// with `after_sample` (the previous kernel in the stream is the sampler, which
-// signals its dependents at its start) the tile kernel is launched with
-// programmatic stream serialization: its set-up and first tile records run on
-// SMs the sampler's last blocks free, and it waits for the sampler before
-// reading the picks and depths
+// With `pdl` the tile kernel is launched with programmatic stream
+// serialization behind the previous kernel in the stream: the sampler
+// (PDL_AFTER_SAMPLE: set-up and first tile records run on SMs the sampler's
+// last blocks free, then it waits for the sampler before reading the picks and
+// depths) or another width class's tile kernel (PDL_AFTER_TILE: its CTAs start
+// on SMs that kernel frees, with no wait at the start, and wait for it before
+// they exit).
+enum { PDL_NONE = 0, PDL_AFTER_SAMPLE = 1, PDL_AFTER_TILE = 2 };
 template <int H, int MODE>
-cudaError_t launch_tile_bf16(int grid, cudaStream_t st, const StepParams& sp, const Bf16Args& ba,
-                             bool after_sample = false) {
+cudaError_t launch_tile_bf16(int grid, cudaStream_t st, const StepParams& sp, Bf16Args ba, int pdl = PDL_NONE) {
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_tile_bf16<H, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -354,7 +356,8 @@ cudaError_t launch_tile_bf16(int grid, cudaStream_t st, const StepParams& sp, co
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = after_sample ? 1 : 0;
+    cfg.numAttrs = pdl != PDL_NONE ? 1 : 0;
+    ba.wait_first = pdl != PDL_AFTER_TILE;
     return cudaLaunchKernelEx(&cfg, k_tile_bf16<H, MODE>, sp, ba);
 }
 
@@ -422,7 +425,7 @@ cudaError_t launch_wide_dw(vmap_ctx* ctx, int loss_only, bool after_fb = false) 
 
 // one width class of the step's tile kernel (FP32 SIMT, or BF16 tensor cores)
 template <int MODE>
-cudaError_t launch_class(vmap_ctx* ctx, int c, bool after_sample = false) {
+cudaError_t launch_class(vmap_ctx* ctx, int c, int pdl = PDL_NONE) {
     TileArgs ta = base_args(ctx);
     ta.tiles = ctx->tiles_d + (long long)c * ctx->tile_cap;
     ta.n_tiles = ctx->counts_d + BC_TILES + c;
@@ -434,11 +437,11 @@ cudaError_t launch_class(vmap_ctx* ctx, int c, bool after_sample = false) {
     }
     if (uses_tc(ctx, c)) {
         constexpr int BM = MODE == MODE_FORWARD ? MODE_FORWARD : MODE_TRAIN;
-        Bf16Args ba{ta, ctx->img_d, ctx->img_off_d, ctx->err_d, ctx->wait_polls};
+        Bf16Args ba{ta, ctx->img_d, ctx->img_off_d, ctx->err_d, ctx->wait_polls, 1};
         switch (c) {
-            case 0: return launch_tile_bf16<16, BM>(grid, ctx->stream, ctx->sp, ba, after_sample);
-            case 1: return launch_tile_bf16<32, BM>(grid, ctx->stream, ctx->sp, ba, after_sample);
-            default: return launch_tile_bf16<64, BM>(grid, ctx->stream, ctx->sp, ba, after_sample);
+            case 0: return launch_tile_bf16<16, BM>(grid, ctx->stream, ctx->sp, ba, pdl);
+            case 1: return launch_tile_bf16<32, BM>(grid, ctx->stream, ctx->sp, ba, pdl);
+            default: return launch_tile_bf16<64, BM>(grid, ctx->stream, ctx->sp, ba, pdl);
         }
     }
     return launch_tile_c<MODE>(c, grid, ctx->stream, ctx->sp, ta);
@@ -511,7 +514,13 @@ vmap_status launch_tiles(vmap_ctx* ctx, int mask) {
             }
         } else {
             const int pi = MODE == MODE_TRAIN ? prof_begin(ctx, PS_TILE + c) : -1;
-            e = launch_class<MODE>(ctx, c, after_sample_c && uses_tc(ctx, c) && pi < 0);
+            // the first class starts behind the sampler, each further one behind
+            // the previous class's tile kernel (no profiling event between)
+            const int pdl = !uses_tc(ctx, c) || pi >= 0 ? PDL_NONE
+                          : after_sample_c           ? PDL_AFTER_SAMPLE
+                          : after_tile               ? PDL_AFTER_TILE
+                                                     : PDL_NONE;
+            e = launch_class<MODE>(ctx, c, pdl);
             prof_end(ctx, pi);
             after_tile = uses_tc(ctx, c) && pi < 0;
         }
@@ -1462,57 +1471,104 @@ vmap_status vmap_set_launch(vmap_ctx* ctx, const int* rays_per_tile, const int* 
 vmap_status vmap_autotune(vmap_ctx* ctx, const int* rays_per_object, int reps, float* best_ms) {
     if (!ctx || !rays_per_object || reps < 1) return fail(ctx, VMAP_ERR_ARG, "bad argument");
     const int mask = class_mask(ctx);
-    const bool graph = ctx->graph_on, prof = ctx->prof_on;
-    drop_graphs(ctx);
-    ctx->graph_on = false;
+    // The candidates are timed on real steps (sampling, tile kernels, reduce,
+    // Adam; graph-replayed when graph mode is on, with the overlapped
+    // launches), so the training state is saved first and put back at the end.
+    const int K = (int)ctx->objs.size();
+    const size_t np = (size_t)ctx->param_used, nw = ctx->bf16 ? 0 : (size_t)ctx->wt_used;
+    const size_t ni = ctx->bf16 ? (size_t)ctx->img_used : 0;
+    const size_t bytes = 3 * np * sizeof(float) + nw * sizeof(float) + ni * sizeof(__nv_bfloat16) + 2 * (size_t)K * sizeof(int);
+    unsigned char* snap = nullptr;
+    CU(cudaStreamSynchronize(ctx->stream));
+    CU(cudaMalloc((void**)&snap, std::max<size_t>(bytes, 16)));
+    const bool prof = ctx->prof_on;
+    prof_flush(ctx);
     ctx->prof_on = false;
-    cudaEvent_t e0, e1;
-    CU(cudaEventCreate(&e0));
-    CU(cudaEventCreate(&e1));
-    vmap_status status = VMAP_OK;
-    for (int c = 0; c < NCLASS && status == VMAP_OK; ++c) {
-        if (best_ms) best_ms[c] = 0.f;
-        if (!(mask & (1 << c))) continue;
-        int Smin = SMAX;
-        for (const ObjDev& o : ctx->objs)
-            if (class_of(o.hidden) == c) Smin = std::min(Smin, o.S);
-        const int rt_hi = std::max(1, std::min(RTMAX, class_mmax(ctx, c) / Smin));
-        float best = 1e30f;
-        int best_rt = ctx->rt[c], best_g = ctx->gmult[c];
-        for (int g = 1; g <= GMULT_MAX && status == VMAP_OK; ++g) {
-            for (int rt = rt_hi; rt >= 1 && status == VMAP_OK; rt = rt > 4 ? rt - 1 : rt / 2) {
-                ctx->rt[c] = rt;
-                ctx->gmult[c] = g;
-                status = sample_impl(ctx, rays_per_object, nullptr, cudaMemcpyDeviceToDevice);
-                if (status) break;
-                // the tile kernel only writes partial slots: timing it changes no state
-                cudaError_t e = launch_class<MODE_TRAIN>(ctx, c);
-                if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
-                for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_class<MODE_TRAIN>(ctx, c);
-                if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
-                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-                if (e != cudaSuccess) {
-                    status = fail(ctx, VMAP_ERR_CUDA, "autotune launch failed: %s", cudaGetErrorString(e));
-                    break;
-                }
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                ms /= reps;
-                if (ms < best) {
-                    best = ms;
-                    best_rt = rt;
-                    best_g = g;
-                }
-                if (rt == 1) break;
+    struct Part { void* p; size_t n; };
+    const Part parts[] = {{ctx->params_d, np * sizeof(float)}, {ctx->m_d, np * sizeof(float)},
+                          {ctx->v_d, np * sizeof(float)},      {ctx->wt_d, nw * sizeof(float)},
+                          {ctx->img_d, ni * sizeof(__nv_bfloat16)}, {ctx->steps_d, K * sizeof(int)},
+                          {ctx->status_d, K * sizeof(int)}};
+    auto copy_state = [&](bool save) -> cudaError_t {
+        size_t off = 0;
+        for (const Part& q : parts) {
+            if (q.n) {
+                cudaError_t e = save ? cudaMemcpyAsync(snap + off, q.p, q.n, cudaMemcpyDeviceToDevice, ctx->stream)
+                                     : cudaMemcpyAsync(q.p, snap + off, q.n, cudaMemcpyDeviceToDevice, ctx->stream);
+                if (e != cudaSuccess) return e;
             }
+            off += q.n;
         }
-        ctx->rt[c] = best_rt;
-        ctx->gmult[c] = best_g;
-        if (best_ms) best_ms[c] = best;
+        return cudaStreamSynchronize(ctx->stream);
+    };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t ce = copy_state(true);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    vmap_status status = ce == cudaSuccess ? VMAP_OK : fail(ctx, VMAP_ERR_CUDA, "autotune set-up: %s", cudaGetErrorString(ce));
+    // one candidate: two untimed steps (graph capture, layout build), then `reps` timed
+    auto time_steps = [&](float& ms) -> vmap_status {
+        drop_graphs(ctx);
+        for (int i = 0; i < 2; ++i)
+            if (vmap_status s = step_impl(ctx, rays_per_object, nullptr, cudaMemcpyDeviceToDevice, nullptr)) return s;
+        CU(cudaEventRecord(e0, ctx->stream));
+        for (int r = 0; r < reps; ++r)
+            if (vmap_status s = step_impl(ctx, rays_per_object, nullptr, cudaMemcpyDeviceToDevice, nullptr)) return s;
+        CU(cudaEventRecord(e1, ctx->stream));
+        CU(cudaEventSynchronize(e1));
+        CU(cudaEventElapsedTime(&ms, e0, e1));
+        ms /= reps;
+        return VMAP_OK;
+    };
+    float best = 1e30f;
+    if (status == VMAP_OK) status = time_steps(best);
+    // coordinate descent over the width classes present: each class's
+    // (rays per tile, grid multiplier) swept with the others held; a second
+    // pass if the first changed anything
+    for (int pass = 0; pass < 2 && status == VMAP_OK; ++pass) {
+        bool changed = false;
+        for (int c = NCLASS - 1; c >= 0 && status == VMAP_OK; --c) {
+            if (!(mask & (1 << c))) continue;
+            int Smin = SMAX;
+            for (const ObjDev& o : ctx->objs)
+                if (class_of(o.hidden) == c) Smin = std::min(Smin, o.S);
+            const int rt_hi = std::max(1, std::min(RTMAX, class_mmax(ctx, c) / Smin));
+            int best_rt = ctx->rt[c], best_g = ctx->gmult[c];
+            for (int g = 1; g <= GMULT_MAX && status == VMAP_OK; ++g) {
+                for (int rt = rt_hi; rt >= 1 && status == VMAP_OK; rt = rt > 4 ? rt - 1 : rt / 2) {
+                    if (rt == best_rt && g == best_g) {
+                        if (rt == 1) break;
+                        continue;   // the current shape: already timed
+                    }
+                    ctx->rt[c] = rt;
+                    ctx->gmult[c] = g;
+                    float ms = 0.f;
+                    status = time_steps(ms);
+                    if (status) break;
+                    if (ms < best) {
+                        best = ms;
+                        best_rt = rt;
+                        best_g = g;
+                        changed = true;
+                    }
+                    if (rt == 1) break;
+                }
+            }
+            ctx->rt[c] = best_rt;
+            ctx->gmult[c] = best_g;
+        }
+        if (!changed) break;
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    ctx->graph_on = graph;
+    if (best_ms)
+        for (int c = 0; c < NCLASS; ++c) best_ms[c] = (mask & (1 << c)) ? best : 0.f;
+    drop_graphs(ctx);
+    ce = copy_state(false);
+    if (status == VMAP_OK && ce != cudaSuccess)
+        status = fail(ctx, VMAP_ERR_CUDA, "autotune restore: %s", cudaGetErrorString(ce));
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(snap);
+    if (ctx->bf16) ctx->shadow_stale = true;
     ctx->prof_on = prof;
     ctx->batch_ready = false;
     return status;

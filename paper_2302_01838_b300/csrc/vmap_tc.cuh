@@ -52,6 +52,25 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
         "l"(a), "l"(b), "r"(idesc), "r"((int)acc));
 }
 
+// The same MMA, executed by all 32 lanes of a converged warp: every lane forms
+// the operands (so they are warp-uniform values), the lane elect.sync picks
+// (the lowest active lane, the same lane at every call of a converged warp)
+// issues.
+__device__ __forceinline__ void mma_bf16_w(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, bool acc) {
+    asm volatile(
+        "{\n.reg .pred p, e;\nelect.sync _|e, 0xffffffff;\nsetp.ne.b32 p, %4, 0;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"((int)acc));
+}
+// mma_commit by the elected lane of a converged warp (the lane that issued
+// the warp's MMAs with mma_bf16_w)
+__device__ __forceinline__ void mma_commit_w(uint64_t* mbar) {
+    asm volatile(
+        "{\n.reg .pred e;\nelect.sync _|e, 0xffffffff;\n"
+        "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}" ::"r"(smem_u32(mbar))
+        : "memory");
+}
+
 // arrive on mbar once every MMA issued so far by this thread has completed
 __device__ __forceinline__ void mma_commit(uint64_t* mbar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))

@@ -191,6 +191,11 @@ struct Bf16Args {
     const long long* img_off;   // per object: element offset of its image
     int* err;                   // set to 1 when a bounded wait gives up
     long long polls;            // polls before an MMA or weight-copy wait gives up
+    // 1: wait for the preceding grid at the start (launched behind the sampler,
+    // or without programmatic serialization); 0: launched behind another tile
+    // kernel, whose start already waited for the sampler: no wait at the start,
+    // the wait comes before the CTA exits (so completions stay in stream order)
+    int wait_first;
 };
 
 template <int H, int MODE>
@@ -247,10 +252,13 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
     }
     if (warp == 0) tmem_alloc(tslot, C::NCOLS);
     if constexpr (FUSED) {
-        // the ones column of Hs (the bias lane of S2) and the zero columns after it
+        // the ones column of Hs (the bias lane of S2) and the zero columns after
+        // it; the dY columns of ZY (the render rewrites the first 8 of each row)
         for (int r = tid; r < TM; r += blockDim.x) {
             float v[8] = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             st_bf16x8(Hst, cm_off(r, C::ONES_HS, C::HSC), v);
+            *reinterpret_cast<uint4*>(ZYt + cm_off(r, H, C::ZYC)) = make_uint4(0u, 0u, 0u, 0u);
+            *reinterpret_cast<uint4*>(ZYt + cm_off(r, H + 8, C::ZYC)) = make_uint4(0u, 0u, 0u, 0u);
         }
     } else {
         for (int i = tid; i < 4 * TM; i += blockDim.x) {
@@ -338,41 +346,69 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
         tc_fence_after();
         if constexpr (FUSED) {
             if (GRAD) {
-                // S1 = X^T ZY: lane = X column (encoding 0..95, h4 96..), column = ZY column
-                // (dZ1 0..H-1, dY H..H+15); a warp loads 8 columns at a time, every
-                // lane keeps what belongs to its row
-#pragma unroll 1
-                for (int c8 = hf; c8 < C::ZYC / 8; c8 += 2) {
-                    float v[8];
-                    tmem_ld8(tl_lane + C::C_S1 + 8 * c8, v);
+                // Each warp loads (8 columns at a time, alternating with the other
+                // warp of its lane quadrant, one wait) only the columns its lanes own.
+                // S1 = X^T ZY: lane = X column (encoding 0..95 with the ones lane 93,
+                // h4 from 96), column = ZY column (dZ1 0..H-1, dY H..H+15).
+                {
+                    float v[3][8];
+                    const int ndz = q < 3 ? H / 16 : 0;          // dZ1 chunks of this thread
+                    const bool dyc = q >= 2 && hf == 0;          // the dY chunk (lane 93, h4 lanes)
+#pragma unroll
+                    for (int j = 0; j < 2; ++j)
+                        if (j < ndz) tmem_ld8(tl_lane + C::C_S1 + 8 * (hf + 2 * j), v[j]);
+                    if (dyc) tmem_ld8(tl_lane + C::C_S1 + H, v[2]);
                     tmem_ld_wait();
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const int col = 8 * c8 + j;
-                        if (col < H) {
-                            if (row < DIN) gp[w_off(H, 0) + col * DIN + row] = v[j];    // dW1[n][in]
-                            else if (row == DIN) gp[b_off(H, 0) + col] = v[j];          // b1
-                        } else if (col - H < NOUT) {
-                            const int o = col - H;
-                            if (row == DIN) gp[b_off(H, 4) + o] = v[j];                 // b5
+                    for (int j = 0; j < 2; ++j)
+                        if (j < ndz) {
+#pragma unroll
+                            for (int u = 0; u < 8; ++u) {
+                                const int col = 8 * (hf + 2 * j) + u;
+                                if (row < DIN) gp[w_off(H, 0) + col * DIN + row] = v[j][u];    // dW1[n][in]
+                                else if (row == DIN) gp[b_off(H, 0) + col] = v[j][u];          // b1
+                            }
+                        }
+                    if (dyc) {
+#pragma unroll
+                        for (int o = 0; o < NOUT; ++o) {
+                            if (row == DIN) gp[b_off(H, 4) + o] = v[2][o];                   // b5
                             else if (row >= DINP && row < DINP + H)
-                                gp[w_off(H, 4) + o * H + (row - DINP)] = v[j];                // dW5[o][in]
+                                gp[w_off(H, 4) + o * H + (row - DINP)] = v[2][o];          // dW5[o][in]
                         }
                     }
                 }
-                // S2 = Hs^T Z: lane = Hs column (h1 | h2 | h3 | ones), column = Z column
-                // (dZ2 | dZ3 | dZ4); layer l's block is lanes and columns l*H .. l*H + H - 1
+                // S2 = Hs^T Z: lane = Hs column (h1 | h2 | h3 | ones lane 3H), column = Z
+                // column (dZ2 | dZ3 | dZ4); layer l's block is lanes and columns
+                // l*H .. l*H + H - 1, the ones lane holds b2 | b3 | b4
+                {
+                    const int r0 = 32 * q, r1 = r0 + 32;
+                    const bool bias_q = C::ONES_HS >= r0 && C::ONES_HS < r1;
+                    const int wr1 = min(r1, C::ONES_HS);
+                    const int lo = bias_q ? 0 : (r0 < C::ONES_HS ? (r0 / H) * H : 0);
+                    const int hi = bias_q ? C::ONES_HS : (r0 < C::ONES_HS ? ((wr1 - 1) / H + 1) * H : 0);
 #pragma unroll 1
-                for (int c8 = hf; c8 < C::ZC / 8; c8 += 2) {
-                    float v[8];
-                    tmem_ld8(tl_lane + C::C_S2 + 8 * c8, v);
-                    tmem_ld_wait();
+                    for (int g = 0; g < 2; ++g) {   // up to 6 chunks per thread, 3 per wait
+                        float v[3][8];
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const int col = 8 * c8 + j, lc = col / H;
-                        if (row == C::ONES_HS) gp[b_off(H, lc + 1) + col % H] = v[j];   // b2..b4
-                        else if (row / H == lc && row < C::ONES_HS)
-                            gp[w_off(H, lc + 1) + (col % H) * H + (row % H)] = v[j];    // dW2..4[n][in]
+                        for (int j = 0; j < 3; ++j) {
+                            const int c8 = lo / 8 + hf + 2 * (3 * g + j);
+                            if (8 * c8 < hi) tmem_ld8(tl_lane + C::C_S2 + 8 * c8, v[j]);
+                        }
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) {
+                            const int c8 = lo / 8 + hf + 2 * (3 * g + j);
+                            if (8 * c8 < hi) {
+#pragma unroll
+                                for (int u = 0; u < 8; ++u) {
+                                    const int col = 8 * c8 + u, lc = col / H;
+                                    if (row == C::ONES_HS) gp[b_off(H, lc + 1) + col % H] = v[j][u];   // b2..b4
+                                    else if (row / H == lc && row < C::ONES_HS)
+                                        gp[w_off(H, lc + 1) + (col % H) * H + (row % H)] = v[j][u];    // dW2..4[n][in]
+                                }
+                            }
+                        }
                     }
                 }
             }
@@ -461,11 +497,14 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
     }
     // Launched behind the sampler (programmatic dependent launch), the kernel
     // has done its set-up so far; the sampler's picks and depths are complete
-    // past this wait. Dependents are released only after it, so a width-128
-    // kernel launched behind this one (which reads the sampler's output too)
-    // starts after the sampler's completion; every CTA of this grid is
-    // resident once each has passed this point.
-    pdl_wait();
+    // past this wait. Dependents are released only after it, so a kernel
+    // launched behind this one (the next width class's, or the width-128
+    // kernel, which read the sampler's output too) starts after the sampler's
+    // completion; every CTA of this grid is resident once each has passed this
+    // point. Launched behind another width class's tile kernel, whose CTAs all
+    // passed that wait before this grid could start, the sampler is complete
+    // already.
+    if (ba.wait_first) pdl_wait();
     pdl_launch_dependents();
 
 #pragma unroll 1
@@ -523,9 +562,9 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
             }
             dwpend = false;
         };
-        if (dwpend) wait_dw();
         // ---- points and encoding (BF16; two threads per sample, each forms the
         // sample's normalised point itself) ----------------------------------------
+        if (dwpend) wait_dw();
         for (int f = tid; f < 2 * TM; f += blockDim.x) {
             const int m = f % TM, half = f / TM;
             float x0 = 0.f, x1 = 0.f, x2 = 0.f;
@@ -554,14 +593,14 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
             wpend = false;
         }
         // layer 1: [128 x 96] x W1^T -> C_FWD
-        if (tid == 0) {
+        if (warp == 0) {
             int cc, c0;
             unsigned char* a = fwd_a(0, cc, c0);
 #pragma unroll
             for (int kc = 0; kc < DINP / 16; ++kc)
-                mma_bf16(tmem + C::C_FWD, desc_kmajor(a, cc, c0 + 16 * kc), desc_kmajor(W1, DINP, 16 * kc),
+                mma_bf16_w(tmem + C::C_FWD, desc_kmajor(a, cc, c0 + 16 * kc), desc_kmajor(W1, DINP, 16 * kc),
                          idesc_bf16(TM, H, 0, 0), kc > 0);
-            mma_commit(mbar);
+            mma_commit_w(mbar);
         }
         constexpr int NC = H / 2;
         // the next tile of this range: its picks now, its rays and depths (into the
@@ -606,21 +645,21 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
             }
             sync_for_mma();
             if (abort) break;
-            if (tid == 0) {
+            if (warp == 0) {
                 int cc, cb;
                 unsigned char* a = fwd_a(l + 1, cc, cb);
                 if (l < 3) {
 #pragma unroll
                     for (int kc = 0; kc < H / 16; ++kc)
-                        mma_bf16(tmem + C::C_FWD, desc_kmajor(a, cc, cb + 16 * kc), desc_kmajor(Whp(l), H, 16 * kc),
+                        mma_bf16_w(tmem + C::C_FWD, desc_kmajor(a, cc, cb + 16 * kc), desc_kmajor(Whp(l), H, 16 * kc),
                                  idesc_bf16(TM, H, 0, 0), kc > 0);
                 } else {
 #pragma unroll
                     for (int kc = 0; kc < H / 16; ++kc)
-                        mma_bf16(tmem + C::C_FWD, desc_kmajor(a, cc, cb + 16 * kc), desc_kmajor(W5, H, 16 * kc),
+                        mma_bf16_w(tmem + C::C_FWD, desc_kmajor(a, cc, cb + 16 * kc), desc_kmajor(W5, H, 16 * kc),
                                  idesc_bf16(TM, 16, 0, 0), kc > 0);
                 }
-                mma_commit(mbar);
+                mma_commit_w(mbar);
             }
             wait_mma();
             if (abort) break;
@@ -644,16 +683,25 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
         const float invR = th.invR;
         for (int r = warp; r < nr; r += NTHREADS / 32) {
             float* d = rays + r * RAYF;
-            render_ray_warp<GRAD, TM, true>(sp, yb, tsm, d, r, S, invR);
+            // fused: each sample's dL/dy goes straight to its row of the dY columns of ZY
+            if constexpr (FUSED) render_ray_warp<GRAD, TM, true>(sp, yb, tsm, d, r, S, invR, GRAD ? ZYt : nullptr,
+                                                                 C::ZYC, H);
+            else render_ray_warp<GRAD, TM, true>(sp, yb, tsm, d, r, S, invR);
             // the ray's loss terms join its slot's run sums (lane 0 wrote them)
             if (lane == 0) {
                 lossacc[3 * r] += d[13]; lossacc[3 * r + 1] += d[14]; lossacc[3 * r + 2] += d[15];
             }
         }
-        for (int m = M + tid; m < TM; m += blockDim.x) {
-            yb[m] = 0.f; yb[TM + m] = 0.f; yb[2 * TM + m] = 0.f; yb[3 * TM + m] = 0.f;
+        if constexpr (FUSED) {
+            if (GRAD)   // rows past the tile's samples: zero dL/dy
+                for (int m = M + tid; m < TM; m += blockDim.x)
+                    *reinterpret_cast<uint4*>(ZYt + cm_off(m, H, C::ZYC)) = make_uint4(0u, 0u, 0u, 0u);
+        } else {
+            for (int m = M + tid; m < TM; m += blockDim.x) {
+                yb[m] = 0.f; yb[TM + m] = 0.f; yb[2 * TM + m] = 0.f; yb[3 * TM + m] = 0.f;
+            }
         }
-        __syncthreads();
+        if (!GRAD) __syncthreads();
         if (!GRAD) {
             __syncthreads();
             if (last) {
@@ -663,16 +711,15 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
             __syncthreads();
             continue;
         }
-        // dY -> BF16 [128][16] (columns 4..15 zero): the dY columns of ZY (fused)
-        {
-            unsigned char* dyt = FUSED ? ZYt : DYt;
-            const int dcc = FUSED ? C::ZYC : 16, dc0 = FUSED ? H : 0;
+        // split: dY -> BF16 [128][16] (columns 4..15 zero)
+        if constexpr (!FUSED) {
+            __syncthreads();
             for (int m = tid; m < TM * 2; m += blockDim.x) {
                 const int r = m % TM, half = m / TM;
                 float v[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) v[j] = (half == 0 && j < NOUT) ? yb[j * TM + r] : 0.f;
-                st_bf16x8(dyt, cm_off(r, dc0 + half * 8, dcc), v);
+                st_bf16x8(DYt, cm_off(r, half * 8, 16), v);
             }
         }
         sync_for_mma();
@@ -709,39 +756,39 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
         auto issue_dx = [&](const unsigned char* z, int zcc, int z0, const unsigned char* w) {
 #pragma unroll
             for (int kc = 0; kc < H / 16; ++kc)
-                mma_bf16(tmem + C::C_DX, desc_kmajor(z, zcc, z0 + 16 * kc), desc_mnmajor(w, H, 16 * kc),
+                mma_bf16_w(tmem + C::C_DX, desc_kmajor(z, zcc, z0 + 16 * kc), desc_mnmajor(w, H, 16 * kc),
                          idesc_bf16(TM, H, 0, 1), kc > 0);
-            mma_commit(mbar);
+            mma_commit_w(mbar);
         };
         // dW^T [fan-in lanes][n] += a^T z over the tile's samples
         auto issue_dw = [&](int col, const unsigned char* a, int acc_, const unsigned char* z, int zcc, int n) {
 #pragma unroll
             for (int kc = 0; kc < TM / 16; ++kc)
-                mma_bf16(tmem + col, desc_mnmajor(a, acc_, 16 * kc), desc_mnmajor(z, zcc, 16 * kc),
+                mma_bf16_w(tmem + col, desc_mnmajor(a, acc_, 16 * kc), desc_mnmajor(z, zcc, 16 * kc),
                          idesc_bf16(TM, n, 1, 1), !first || kc > 0);
         };
         if constexpr (FUSED) {
             // layer 5: dY W5
-            if (tid == 0) {
-                mma_bf16(tmem + C::C_DX, desc_kmajor(ZYt, C::ZYC, H), desc_mnmajor(W5, H, 0), idesc_bf16(TM, H, 0, 1),
+            if (warp == 0) {
+                mma_bf16_w(tmem + C::C_DX, desc_kmajor(ZYt, C::ZYC, H), desc_mnmajor(W5, H, 0), idesc_bf16(TM, H, 0, 1),
                          false);
-                mma_commit(mbar);
+                mma_commit_w(mbar);
             }
             wait_mma();
             dx_epi(Xt, C::XC, DINP, Zt, C::ZC, 2 * H, false);           // dZ4 = . * [h4 > 0]
             sync_for_mma();
             if (abort) break;
-            if (tid == 0) issue_dx(Zt, C::ZC, 2 * H, Whp(2));           // dZ4 W4
+            if (warp == 0) issue_dx(Zt, C::ZC, 2 * H, Whp(2));           // dZ4 W4
             wait_mma();
             dx_epi(Hst, C::HSC, 2 * H, Zt, C::ZC, H, false);            // dZ3 = . * [h3 > 0]
             sync_for_mma();
             if (abort) break;
-            if (tid == 0) issue_dx(Zt, C::ZC, H, Whp(1));               // dZ3 W3
+            if (warp == 0) issue_dx(Zt, C::ZC, H, Whp(1));               // dZ3 W3
             wait_mma();
             dx_epi(Hst, C::HSC, H, Zt, C::ZC, 0, false);                // dZ2 = . * [h2 > 0]
             sync_for_mma();
             if (abort) break;
-            if (tid == 0) {
+            if (warp == 0) {
                 issue_dx(Zt, C::ZC, 0, Whp(0));                         // dZ2 W2
                 issue_dw(C::C_S2, Hst, C::HSC, Zt, C::ZC, C::ZC);       // S2 += Hs^T [dZ2 | dZ3 | dZ4]
             }
@@ -749,9 +796,9 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
             dx_epi(Hst, C::HSC, 0, ZYt, C::ZYC, 0, true);               // dZ1 = . * [h1 > 0]
             sync_for_mma();
             if (abort) break;
-            if (tid == 0) {
+            if (warp == 0) {
                 issue_dw(C::C_S1, Xt, C::XC, ZYt, C::ZYC, C::ZYC);      // S1 += [enc | h4]^T [dZ1 | dY]
-                mma_commit(mbar2);                                      // (also covers S2's MMAs)
+                mma_commit_w(mbar2);                                      // (also covers S2's MMAs)
             }
         } else {
             // dZ_l = acc * [h_l > 0] (h_l in HA[l - 1]) -> dst with zcc columns
@@ -762,16 +809,16 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
             // issues the previous layer's weight-gradient MMAs behind it; in the last
             // round thread 0 feeds dW2 and thread 128 feeds dW1 (each accumulator
             // always from the same thread, in order).
-            if (tid == 0) {
-                mma_bf16(tmem + C::C_DX, desc_kmajor(DYt, 16, 0), desc_mnmajor(W5, H, 0), idesc_bf16(TM, H, 0, 1),
+            if (warp == 0) {
+                mma_bf16_w(tmem + C::C_DX, desc_kmajor(DYt, 16, 0), desc_mnmajor(W5, H, 0), idesc_bf16(TM, H, 0, 1),
                          false);
-                mma_commit(mbar);
+                mma_commit_w(mbar);
             }
             wait_mma();
             dx_epi(HAp(3), CH, 0, DZp(0), H, 0, false);                  // dZ4
             sync_for_mma();
             if (abort) break;
-            if (tid == 0) {
+            if (warp == 0) {
                 issue_dx(DZp(0), H, 0, Whp(2));                          // dZ4 W4
                 issue_dw(C::C_DW5, HAp(3), CH, DYt, 16, 16);             // dW5^T += h4^T dY
             }
@@ -779,7 +826,7 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
             dx_epi(HAp(2), CH, 0, DZp(1), H, 0, true);                   // dZ3
             sync_for_mma();
             if (abort) break;
-            if (tid == 0) {
+            if (warp == 0) {
                 issue_dx(DZp(1), H, 0, Whp(1));                          // dZ3 W3
                 issue_dw(C::C_DW1 + 3 * H, HAp(2), CH, DZp(0), H, H);     // dW4^T += h3^T dZ4
             }
@@ -787,7 +834,7 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
             dx_epi(HAp(1), CH, 0, HAp(3), CH, 0, true);                  // dZ2
             sync_for_mma();
             if (abort) break;
-            if (tid == 0) {
+            if (warp == 0) {
                 issue_dx(HAp(3), CH, 0, Whp(0));                         // dZ2 W2
                 issue_dw(C::C_DW1 + 2 * H, HAp(1), CH, DZp(1), H, H);     // dW3^T += h2^T dZ3
             }
@@ -795,12 +842,12 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
             dx_epi(HAp(0), CH, 0, DZp(0), H, 0, true);                   // dZ1
             sync_for_mma();
             if (abort) break;
-            if (tid == 0) {
+            if (warp == 0) {
                 issue_dw(C::C_DW1 + H, HAp(0), CH, HAp(3), CH, H);        // dW2^T += h1^T dZ2
-                mma_commit(mbar);
-            } else if (tid == 128) {
+                mma_commit_w(mbar);
+            } else if (warp == 4) {
                 issue_dw(C::C_DW1, G0, DINP, DZp(0), H, H);              // dW1^T += enc^T dZ1
-                mma_commit(mbar2);
+                mma_commit_w(mbar2);
             }
         }
         dwpend = true;
@@ -826,6 +873,9 @@ __global__ void __launch_bounds__(NTHREADS, Bf16Cfg<H>::CTAS) k_tile_bf16(StepPa
     }
     if (wpend) mbar_wait(wbar, wphase, DRAIN_POLLS);
     cp_async_wait_all();   // prefetches issued before an abort land before the CTA exits
+    // behind another tile kernel: complete only after it (what follows in the
+    // stream waits for this grid alone and must see both)
+    if (!ba.wait_first) pdl_wait();
     tc_fence_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, C::NCOLS);

@@ -18,6 +18,7 @@
 // hidden layers 2-4 (it is recomputed for the layer-1 weight gradient), which
 // lets two CTAs share an SM at H = 32.
 #pragma once
+#include <cuda_bf16.h>
 #include "vmap_common.cuh"
 
 namespace vmapk {
@@ -291,9 +292,13 @@ __device__ __forceinline__ float warp_sum(float v) {
 // S_i = o_i g_i + (1 - o_i) S_{i+1} is a suffix scan of affine maps
 // x -> (1 - o_i) x + o_i g_i (no division by 1 - o_i anywhere). With ACT the
 // four outputs in yb already went through the sigmoid.
+// With dyt (GRAD only), dL/dy of sample m goes, as 8 BF16 values (the 4
+// outputs' gradients, then 4 zeros), to row m at column dc0 of that
+// core-matrix tile with dcc columns, instead of back into yb.
 template <bool GRAD, int LD, bool ACT = false>
 __device__ __forceinline__ void render_ray_warp(const StepParams& sp, float* yb, const float* tsm,
-                                                float* d, int r, int S, float invR) {
+                                                float* d, int r, int S, float invR,
+                                                unsigned char* dyt = nullptr, int dcc = 0, int dc0 = 0) {
     const int i = threadIdx.x & 31;
     const bool v = i < S;
     const int m = r * S + i;
@@ -350,10 +355,24 @@ __device__ __forceinline__ void render_ray_warp(const StepParams& sp, float* yb,
     if (i == 31) Sn = 0.f;
     if (v) {
         const float dLdo = P * (gi - Sn);
-        yb[m] = dLdo * o * (1.f - o);
-        yb[LD + m] = T * b0 * c0 * (1.f - c0);
-        yb[2 * LD + m] = T * b1 * c1 * (1.f - c1);
-        yb[3 * LD + m] = T * b2 * c2 * (1.f - c2);
+        const float g0 = dLdo * o * (1.f - o);
+        const float g1 = T * b0 * c0 * (1.f - c0);
+        const float g2 = T * b1 * c1 * (1.f - c1);
+        const float g3 = T * b2 * c2 * (1.f - c2);
+        if (dyt) {
+            const __nv_bfloat162 p01 = __floats2bfloat162_rn(g0, g1), p23 = __floats2bfloat162_rn(g2, g3);
+            uint4 u;
+            u.x = *reinterpret_cast<const uint32_t*>(&p01);
+            u.y = *reinterpret_cast<const uint32_t*>(&p23);
+            u.z = 0u;
+            u.w = 0u;
+            *reinterpret_cast<uint4*>(dyt + (((m >> 3) * (dcc >> 3) + (dc0 >> 3)) * 128 + (m & 7) * 16)) = u;
+        } else {
+            yb[m] = g0;
+            yb[LD + m] = g1;
+            yb[2 * LD + m] = g2;
+            yb[3 * LD + m] = g3;
+        }
     }
 }
 

@@ -269,12 +269,12 @@ __global__ void __launch_bounds__(WIDE_THREADS, 1) k_wide_fb(StepParams sp, Wide
         }
 
         // ---- forward -----------------------------------------------------------
-        if (tid == 0) {
+        if (warp == 0) {
 #pragma unroll
             for (int kc = 0; kc < DINP / 16; ++kc)
-                mma_bf16(tmem, desc_kmajor(G0, DINP, 16 * kc), desc_kmajor(W1, DINP, 16 * kc),
+                mma_bf16_w(tmem, desc_kmajor(G0, DINP, 16 * kc), desc_kmajor(W1, DINP, 16 * kc),
                          idesc_bf16(TM, WH, 0, 0), kc > 0);
-            mma_commit(mbar);
+            mma_commit_w(mbar);
         }
         // the next tile of this range: its picks now, its rays and depths during the backward
         const bool has_next = GRAD && tl + 1 < t1;
@@ -300,19 +300,19 @@ __global__ void __launch_bounds__(WIDE_THREADS, 1) k_wide_fb(StepParams sp, Wide
             sync_for_mma();
             if (abort) break;
             if (GRAD) record(at + WideAct::h(l), hb, TM * WH * 2);
-            if (tid == 0) {
+            if (warp == 0) {
                 if (l < 3) {
 #pragma unroll
                     for (int kc = 0; kc < WH / 16; ++kc)
-                        mma_bf16(tmem, desc_kmajor(hb, WH, 16 * kc), desc_kmajor(Whp(l), WH, 16 * kc),
+                        mma_bf16_w(tmem, desc_kmajor(hb, WH, 16 * kc), desc_kmajor(Whp(l), WH, 16 * kc),
                                  idesc_bf16(TM, WH, 0, 0), kc > 0);
                 } else {
 #pragma unroll
                     for (int kc = 0; kc < WH / 16; ++kc)
-                        mma_bf16(tmem, desc_kmajor(hb, WH, 16 * kc), desc_kmajor(W5, WH, 16 * kc),
+                        mma_bf16_w(tmem, desc_kmajor(hb, WH, 16 * kc), desc_kmajor(W5, WH, 16 * kc),
                                  idesc_bf16(TM, 16, 0, 0), kc > 0);
                 }
-                mma_commit(mbar);
+                mma_commit_w(mbar);
             }
             if (GRAD) {
                 // the ReLU mask of h_{l+1} (needed by the backward), from the BF16
@@ -401,9 +401,9 @@ __global__ void __launch_bounds__(WIDE_THREADS, 1) k_wide_fb(StepParams sp, Wide
         }
 
         // ---- backward: input gradients ------------------------------------------
-        if (tid == 0) {
-            mma_bf16(tmem, desc_kmajor(DYt, 16, 0), desc_mnmajor(W5, WH, 0), idesc_bf16(TM, WH, 0, 1), false);
-            mma_commit(mbar);
+        if (warp == 0) {
+            mma_bf16_w(tmem, desc_kmajor(DYt, 16, 0), desc_mnmajor(W5, WH, 0), idesc_bf16(TM, WH, 0, 1), false);
+            mma_commit_w(mbar);
         }
 #pragma unroll 1
         for (int l = 3; l >= 0; --l) {
@@ -424,12 +424,12 @@ __global__ void __launch_bounds__(WIDE_THREADS, 1) k_wide_fb(StepParams sp, Wide
             if (abort) break;
             record(at + WideAct::dz(l), zb, TM * WH * 2);
             if (l == 0) break;
-            if (tid == 0) {
+            if (warp == 0) {
 #pragma unroll
                 for (int kc = 0; kc < WH / 16; ++kc)
-                    mma_bf16(tmem, desc_kmajor(zb, WH, 16 * kc), desc_mnmajor(Whp(l - 1), WH, 16 * kc),
+                    mma_bf16_w(tmem, desc_kmajor(zb, WH, 16 * kc), desc_mnmajor(Whp(l - 1), WH, 16 * kc),
                              idesc_bf16(TM, WH, 0, 1), kc > 0);
-                mma_commit(mbar);
+                mma_commit_w(mbar);
             }
         }
         if (abort) break;
@@ -576,13 +576,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_wide_dw(WideArgs wa) {
         }
         consumed = i + 1;
         unsigned char* st = sm + s * C::STAGE;
-        if (tid == 0) {
+        if (warp == 0) {
             tc_fence_after();
 #pragma unroll
             for (int kc = 0; kc < TM / 16; ++kc)
-                mma_bf16(tmem, desc_mnmajor(st, jb.a_cc, 16 * kc), desc_mnmajor(st + 32768, jb.b_cc, 16 * kc),
+                mma_bf16_w(tmem, desc_mnmajor(st, jb.a_cc, 16 * kc), desc_mnmajor(st + 32768, jb.b_cc, 16 * kc),
                          idesc_bf16(TM, jb.n, 1, 1), !(first && kc == 0));
-            mma_commit(empty + s);
+            mma_commit_w(empty + s);
         }
         if (b_active) {
 #pragma unroll

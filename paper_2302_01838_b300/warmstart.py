@@ -37,10 +37,10 @@ def _context(objs, B, seed, precision, graph=False, autotune=False):
     for k, o in enumerate(objs):
         vm.add_object(o["pool"], hidden=32, center=o["center"], scale=float(o["scale"]),
                       n_surface=o["n_surface"], n_strat=o["n_strat"], init_params=o["init"], stream_id=k)
-    if autotune:
-        vm.autotune([o["rays"] for o in objs], reps=2)
     if graph:
         vm.set_graph(True)
+    if autotune:   # times whole steps in the mode they will run in
+        vm.autotune([o["rays"] for o in objs], reps=2)
     return vm
 
 
@@ -186,6 +186,15 @@ def time_to_target(objs, B, seed, form, hyper=None, target=0.04, max_steps=3000,
     out["obj_median_steps"] = float(np.median(first_step[hit])) if hit.any() else None
     out["obj_median_ms"] = float(np.median(first_ms[hit])) if hit.any() else None
     if guided:
+        # the same render on rays of the training views (fit, not generalisation)
+        rng = np.random.default_rng(seed + 7)
+        tv = []
+        for o in objs:
+            on = o["pool"][o["pool"][:, 10] > 0]
+            tv.append(torch.from_numpy(on[rng.integers(0, on.shape[0], 256)].copy()).cuda())
+        dt = depth_l1(vm, objs, tv, [torch.empty(256, device="cuda") for _ in objs])
+        out["final_depth_l1_train_views"] = float(dt.mean())
+        out["final_depth_l1_train_views_median"] = float(np.median(dt))
         g = depth_l1_guided(vm, objs, B, seed, ev)
         out["final_depth_l1_guided"] = float(g.mean())
         out["frac_below_1cm_guided"] = float(np.mean(g < 0.01))

@@ -472,8 +472,13 @@ def test_autotuner_and_launch_shapes_keep_parity():
             L = _train(vm, R, 1)[0].cpu().numpy()
             assert np.all(np.abs(L - Lo) <= LOSS_RTOL * np.abs(Lo)), (shape, gm)
     vm = vh.library_context(sc)
-    best = vm.autotune(R, reps=2)
+    before = [tuple(t.cpu().numpy().copy() if torch.is_tensor(t) else t for t in vm.get_object_state(k))
+              for k in range(len(R))]
+    best = vm.autotune(R, reps=2)   # times whole training steps, then restores every object
     assert all(b > 0 for b in best)
+    for k in range(len(R)):
+        after = vm.get_object_state(k)
+        assert all(np.array_equal(a.cpu().numpy() if torch.is_tensor(a) else a, b) for a, b in zip(after, before[k]))
     rt, gm = vm.get_launch()
     assert all(1 <= x <= 32 for x in rt) and all(1 <= x <= 2 for x in gm)
     L = _train(vm, R, 1)[0].cpu().numpy()
