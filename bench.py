@@ -7,12 +7,14 @@ ray, every object present (the steady state after the last incremental
 insertion). One step = ray picking + depth-guided sampling + encoding + MLP
 forward + rendering + losses + backward + Adam for all 51 objects.
 
-Default path: BF16 tensor-core GEMMs with FP32 accumulation, master weights,
-moments, rendering and losses, the step replayed as CUDA graphs, launch
-shapes autotuned. The same line reports the plain FP32 path on the same
-workload, a profiled kernel-by-kernel pass (per-kernel time and the roofline
-of the dominant kernel), and the time to a held-out depth-L1 target of
-plain FP32 vs BF16 + batched vs BF16 + batched + warm start.
+Headline: the FP32 path (the paper's precision: FP32 SIMT kernels), the
+step replayed as a CUDA graph, launch shapes autotuned. Beside it, on the
+same workload: the BF16 tensor-core path (tcgen05 GEMMs, FP32 accumulation,
+master weights, moments, rendering and losses); each with a profiled
+kernel-by-kernel pass (per-kernel time and the roofline of the dominant
+kernel). Also: the precision-200 and 1,000-object workloads, and the time to
+a held-out depth-L1 target of plain FP32 vs BF16 + batched vs BF16 + batched
++ warm start.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -43,12 +45,14 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=20)
-    ap.add_argument("--precision", choices=["fp32", "bf16"], default="bf16",
-                    help="bf16: tcgen05 BF16 GEMMs, FP32 accumulation (default); fp32: plain FP32 SIMT path")
+    ap.add_argument("--precision", choices=["fp32", "bf16"], default="fp32",
+                    help="fp32: the FP32 path, the paper's precision (default headline); bf16: tcgen05 BF16 "
+                         "GEMMs with FP32 accumulation (reported beside it either way)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch kernel by kernel instead of graph replay")
     ap.add_argument("--prof-steps", type=int, default=200, help="steps of the profiled kernel-by-kernel pass")
-    ap.add_argument("--fp32-steps", type=int, default=1, help="0: skip the FP32 comparison")
+    ap.add_argument("--fp32-steps", type=int, default=1,
+                    help="0: skip the line of the other precision (BF16 beside an FP32 headline, or FP32 beside BF16)")
     ap.add_argument("--no-ttd", action="store_true", help="skip the time-to-depth-L1 comparison")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -557,11 +561,15 @@ def run_ours(args):
     e2e_s = sharding.max_over_ranks(e2e_s)
     vm.close()
 
-    # ---- the plain FP32 path on the same workload (precision-matched to the paper) --
-    fp32 = None
-    if args.precision == "bf16" and args.fp32_steps > 0 and world == 1:
-        fp32 = measure_workload(sc, "fp32", args.steps, args.warmup, flush, args, peaks, props, clocks=True)
-        fp32["note"] = "room50 on the FP32 SIMT kernels (the paper's precision), same windows"
+    # ---- the same workload at the other precision, side by side ------------------
+    other = "bf16" if args.precision == "fp32" else "fp32"
+    side = None
+    if args.fp32_steps > 0 and world == 1:
+        side = measure_workload(sc, other, args.steps, args.warmup, flush, args, peaks, props, clocks=True)
+        side["note"] = ("room50 on the BF16 tensor-core kernels (tcgen05, FP32 accumulation, master weights, "
+                        "moments, rendering and losses): the precision extension, same windows"
+                        if other == "bf16" else
+                        "room50 on the FP32 SIMT kernels (the paper's precision), same windows")
 
     # ---- the other named workloads, BF16 ------------------------------------------
     workloads = {}
@@ -573,7 +581,11 @@ def run_ours(args):
                                                  peaks, props, admit=8)
         workloads["many1000"]["config"] = ("1,000 objects, hidden {16,32,64}, rays log-uniform 16-1,024, "
                                            "samples per ray {16,22,32}, BF16, one persistent launch per width "
-                                           "class, graph-replayed; 8 objects admitted after the first windows")
+                                           "class (chained: each starts on the SMs the previous one frees), "
+                                           "graph-replayed; 8 objects admitted after the first windows")
+        workloads["many1000_fp32"] = measure_workload(scenes.scene_many(), "fp32", args.steps, args.warmup, flush,
+                                                      args, peaks, props)
+        workloads["many1000_fp32"]["config"] = "the same 1,000 objects on the FP32 SIMT kernels, graph-replayed"
 
     if rank == 0:
         value = world * sps * args.steps / (ms_max * 1e-3)
@@ -599,8 +611,8 @@ def run_ours(args):
                     "api": "vmap_train_step_host (pinned host rays in, host losses out, synchronous)"},
             "clocks": clk,
         }
-        if fp32:
-            out["fp32"] = fp32
+        if side:
+            out[other] = side
         if workloads:
             out["workloads"] = workloads
         if world == 1 and not args.no_ttd:

@@ -79,7 +79,7 @@ cudaError_t prepare_tile() {
 
 template <int H>
 cudaError_t run_tile(cudaStream_t st, const StepParams& sp, const TileArgs& ta) {
-    k_tile_fp32<H, MODE_TRAIN><<<NA_GRID, NTHREADS, TileSmem<H>::BYTES, st>>>(sp, ta);
+    k_tile_fp32<H, MODE_TRAIN><<<NA_GRID, TileCfg<H>::THREADS, TileSmem<H>::BYTES, st>>>(sp, ta);
     return cudaGetLastError();
 }
 

@@ -25,11 +25,16 @@ namespace vmapk {
 
 enum TileMode { MODE_TRAIN = 0, MODE_FORWARD = 1, MODE_GRAD_CENTER = 2, MODE_EVAL = 3, MODE_QUERY = 4 };
 
+// MMAX: samples per tile; CTAS: CTAs per SM (shared memory); THREADS: CTA
+// size. Width 64 (one CTA per SM, 112-sample tiles) runs 16 warps, which
+// hide more shared-memory latency (0.666 vs 0.743 ms per step, 50 objects);
+// width 128 keeps 8: its 48-sample tiles have too few 4x4 register tiles per
+// layer for 512 threads (0.947 vs 0.896 ms per launch).
 template <int H> struct TileCfg;
-template <> struct TileCfg<16>  { static constexpr int MMAX = 120; static constexpr bool GSEP = true;  static constexpr int CTAS = 2; };
-template <> struct TileCfg<32>  { static constexpr int MMAX = 136; static constexpr bool GSEP = false; static constexpr int CTAS = 2; };
-template <> struct TileCfg<64>  { static constexpr int MMAX = 112; static constexpr bool GSEP = false; static constexpr int CTAS = 1; };
-template <> struct TileCfg<128> { static constexpr int MMAX = 48;  static constexpr bool GSEP = false; static constexpr int CTAS = 1; };
+template <> struct TileCfg<16>  { static constexpr int MMAX = 120; static constexpr bool GSEP = true;  static constexpr int CTAS = 2; static constexpr int THREADS = 256; };
+template <> struct TileCfg<32>  { static constexpr int MMAX = 136; static constexpr bool GSEP = false; static constexpr int CTAS = 2; static constexpr int THREADS = 256; };
+template <> struct TileCfg<64>  { static constexpr int MMAX = 112; static constexpr bool GSEP = false; static constexpr int CTAS = 1; static constexpr int THREADS = 512; };
+template <> struct TileCfg<128> { static constexpr int MMAX = 48;  static constexpr bool GSEP = false; static constexpr int CTAS = 1; static constexpr int THREADS = 256; };
 
 constexpr int RED_FLOATS = 4096;   // split-reduction scratch
 constexpr int RAYF = 16;           // floats of per-ray scratch
@@ -124,12 +129,12 @@ __device__ __forceinline__ void acc_store(float* p, float v, bool first) { *p = 
 // The sample range is split SPLIT ways (interleaved quads) to fill the CTA;
 // split partials are combined in a fixed order through smem.
 // ---------------------------------------------------------------------------
-template <int N, int KP>
+template <int N, int KP, int NT = NTHREADS>
 __device__ __forceinline__ void gemm_dw(const float* __restrict__ Z, const float* __restrict__ A,
                                         int ld, int Mpad, float* red, float* __restrict__ g,
                                         int Kreal, float* __restrict__ gb, bool first) {
     constexpr int NQ = N / 4, KQ = KP / 4, T = NQ * KQ;
-    constexpr int S0 = NTHREADS / T > 0 ? NTHREADS / T : 1;
+    constexpr int S0 = NT / T > 0 ? NT / T : 1;
     constexpr int S1 = RED_FLOATS / (N * KP) > 0 ? RED_FLOATS / (N * KP) : 1;
     constexpr int SPLIT = S0 < S1 ? S0 : S1;   // SPLIT == 1 never touches red
     static_assert(SPLIT >= 1 && (SPLIT == 1 || SPLIT * N * KP <= RED_FLOATS), "split scratch");
@@ -377,7 +382,7 @@ __device__ __forceinline__ void render_ray_warp(const StepParams& sp, float* yb,
 }
 
 template <int H, int MODE>
-__global__ void __launch_bounds__(NTHREADS, TileCfg<H>::CTAS) k_tile_fp32(StepParams sp, TileArgs ta) {
+__global__ void __launch_bounds__(TileCfg<H>::THREADS, TileCfg<H>::CTAS) k_tile_fp32(StepParams sp, TileArgs ta) {
     using SM = TileSmem<H>;
     constexpr int LD = SM::LD;
     constexpr bool TRAINISH = MODE == MODE_TRAIN || MODE == MODE_FORWARD || MODE == MODE_GRAD_CENTER;
@@ -593,7 +598,8 @@ __global__ void __launch_bounds__(NTHREADS, TileCfg<H>::CTAS) k_tile_fp32(StepPa
 
         // ---- backward -------------------------------------------------------
         // layer 5: dW5 = dY^T h4, dZ4 = (dY W5) * [h4 > 0]
-        gemm_dw<NOUT, H>(yb, act + 3 * H * LD, LD, Mpad, red, gp + w_off(H, 4), H, gp + b_off(H, 4), first);
+        gemm_dw<NOUT, H, TileCfg<H>::THREADS>(yb, act + 3 * H * LD, LD, Mpad, red, gp + w_off(H, 4), H,
+                                             gp + b_off(H, 4), first);
         stage(ws, P + w_off(H, 4), NOUT * H);     // W5 [4][H] == B[k=out][n=in]
         __syncthreads();
         gemm_fwd<H, NOUT, 2>(yb, LD, ws, nullptr, act + 3 * H * LD, LD, Mpad);
@@ -603,7 +609,7 @@ __global__ void __launch_bounds__(NTHREADS, TileCfg<H>::CTAS) k_tile_fp32(StepPa
             // dW_{l+1} = dZ_{l+1}^T h_l ; dZ_l = (dZ_{l+1} W_{l+1}) * [h_l > 0]
             float* hz = act + l * H * LD;
             float* ha = act + (l - 1) * H * LD;
-            gemm_dw<H, H>(hz, ha, LD, Mpad, red, gp + w_off(H, l), H, gp + b_off(H, l), first);
+            gemm_dw<H, H, TileCfg<H>::THREADS>(hz, ha, LD, Mpad, red, gp + w_off(H, l), H, gp + b_off(H, l), first);
             stage(ws, P + w_off(H, l), H * H);
             __syncthreads();
             gemm_fwd<H, H, 2>(hz, LD, ws, nullptr, ha, LD, Mpad);
@@ -630,7 +636,7 @@ __global__ void __launch_bounds__(NTHREADS, TileCfg<H>::CTAS) k_tile_fp32(StepPa
             __syncthreads();
         }
         // layer 1: dW1 = dZ1^T gamma
-        gemm_dw<H, DINP>(act, g, LD, Mpad, red, gp + w_off(H, 0), DIN, gp + b_off(H, 0), first);
+        gemm_dw<H, DINP, TileCfg<H>::THREADS>(act, g, LD, Mpad, red, gp + w_off(H, 0), DIN, gp + b_off(H, 0), first);
         if (MODE == MODE_GRAD_CENTER) {
             // encoding backward, one thread per sample:
             //   dgamma_j = sum_n dZ1[n] W1[n][j]
