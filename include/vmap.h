@@ -189,6 +189,31 @@ vmap_status vmap_backward(vmap_ctx* ctx, const float* grad_loss, float* grad_par
  * changes. FP32 contexts only. */
 vmap_status vmap_ray_gradients(vmap_ctx* ctx, float* grad_rays);
 
+/* One iteration of camera-pose refinement against object `obj` with the
+ * map held fixed, entirely on the device (the paper refines camera poses
+ * through the map, section 4 "Tracking"; the gradients are those of
+ * vmap_ray_gradients): the camera at position p with rotation R
+ * (world from camera) casts rays o = p, d = R d_c; their samples are drawn
+ * as vmap_sample_rays_given draws them; one tile pass gives the object's
+ * loss on them and the per-ray (dL/do, dL/dd); one kernel forms
+ * dL/dp = sum_rays dL/do and dL/dw = sum_rays d x dL/dd (for the rotation
+ * update R <- exp([w]x) R; fixed summation order) and takes one Adam step
+ * (the context's beta1, beta2; epsilon 1e-12) with learning rates lr_t for
+ * p and lr_r for w. Nothing synchronises.
+ *   dc:        DEVICE [n][3] camera-frame ray directions ((u + 1/2 - cx)/f, (v + 1/2 - cy)/f, 1).
+ *   meas:      DEVICE [n][5] measured depth, rgb and mask per ray.
+ *   pose:      DEVICE [12] p[3], R[9] row-major; updated in place.
+ *   adam:      DEVICE [13] first moments [6], second moments [6], step count; zero it
+ *              before the first iteration.
+ *   rays_work: DEVICE [n][12], grad_work: DEVICE [n][6]: scratch the caller owns.
+ *   loss:      DEVICE [n_objects]: this iteration's loss of `obj` (before the update);
+ *              NaN for the other objects.
+ * FP32 contexts only (VMAP_ERR_ARG otherwise); n <= max_rays_total
+ * (VMAP_ERR_CAPACITY). The context's current batch becomes these rays. */
+vmap_status vmap_pose_step(vmap_ctx* ctx, int obj, const float* dc, const float* meas, int n,
+                           float* pose, float* adam, float lr_t, float lr_r,
+                           float* rays_work, float* grad_work, float* loss);
+
 /* Occupancy (and colour) of n arbitrary world points of one object (section
  * 3.4: an object is queried inside its bound). pts DEVICE [n][3];
  * occ DEVICE [n]; rgb DEVICE [n][3] or NULL. n = 0 is a no-op. */

@@ -193,6 +193,14 @@ class VMap:
         self._check(self.lib.vmap_query_occupancy(self.h, int(obj), _ptr(pts), pts.shape[0],
                                                   _ptr(occ), _ptr(rgb)))
 
+    def pose_step(self, obj, dc, meas, pose, adam, lr_t, lr_r, rays_work, grad_work, loss):
+        """One device iteration of camera-pose refinement (vmap_pose_step); every
+        argument tensor is CUDA float32: dc [n, 3], meas [n, 5], pose [12], adam [13],
+        rays_work [n, 12], grad_work [n, 6], loss [n_objects]."""
+        self._check(self.lib.vmap_pose_step(self.h, int(obj), _ptr(dc), _ptr(meas), int(dc.shape[0]), _ptr(pose),
+                                            _ptr(adam), float(lr_t), float(lr_r), _ptr(rays_work), _ptr(grad_work),
+                                            _ptr(loss)))
+
     def ray_gradients(self, out):
         """(dL/do, dL/dd) of every ray of the current batch into out [n_rays, 6] (CUDA)."""
         self._check(self.lib.vmap_ray_gradients(self.h, _ptr(out)))

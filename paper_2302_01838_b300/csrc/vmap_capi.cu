@@ -18,6 +18,7 @@
 #include "vmap_mesh.cuh"
 #include "vmap_common.cuh"
 #include "vmap_optim.cuh"
+#include "vmap_pose.cuh"
 #include "vmap_sample.cuh"
 #include "vmap_scene.cuh"
 #include "vmap_tile_bf16.cuh"
@@ -1080,6 +1081,33 @@ vmap_status vmap_ray_gradients(vmap_ctx* ctx, float* grad_rays) {
     vmap_status s = launch_tiles<MODE_GRAD_CENTER>(ctx, class_mask(ctx));
     ctx->ray_grad_out = nullptr;
     return s;
+}
+
+vmap_status vmap_pose_step(vmap_ctx* ctx, int obj, const float* dc, const float* meas, int n, float* pose,
+                           float* adam, float lr_t, float lr_r, float* rays_work, float* grad_work, float* loss) {
+    if (vmap_status s = check_obj(ctx, obj)) return s;
+    if (!dc || !meas || !pose || !adam || !rays_work || !grad_work || !loss || n < 1)
+        return fail(ctx, VMAP_ERR_ARG, "bad argument");
+    if (ctx->bf16) return fail(ctx, VMAP_ERR_ARG, "pose refinement needs an FP32 context");
+    if (n > ctx->cfg.max_rays_total) return fail(ctx, VMAP_ERR_CAPACITY, "%d rays exceed max_rays_total", n);
+    // the camera's rays from the current pose, their samples
+    k_pose_rays<<<(n + 255) / 256, 256, 0, ctx->stream>>>(pose, dc, meas, n, rays_work);
+    CHECK_LAUNCH("k_pose_rays");
+    std::vector<int> req(ctx->objs.size(), 0);
+    req[obj] = n;
+    if (vmap_status s = sample_impl(ctx, req.data(), rays_work, cudaMemcpyDeviceToDevice)) return s;
+    // one pass: per-ray gradients and the loss sums of the same samples
+    if (vmap_status s = fill_nan(ctx, loss, ctx->objs.size())) return s;
+    ctx->ray_grad_out = grad_work;
+    vmap_status s = launch_tiles<MODE_GRAD_CENTER>(ctx, class_mask(ctx));
+    ctx->ray_grad_out = nullptr;
+    if (s) return s;
+    if (vmap_status s2 = launch_reduce(ctx, RED_LOSS, nullptr, nullptr, loss, nullptr)) return s2;
+    // pose gradient and one Adam step on the device
+    k_pose_update<<<1, POSE_THREADS, 0, ctx->stream>>>(pose, adam, grad_work, rays_work, n, lr_t, lr_r,
+                                                        ctx->cfg.beta1, ctx->cfg.beta2, 1e-12f);
+    CHECK_LAUNCH("k_pose_update");
+    return VMAP_OK;
 }
 
 vmap_status vmap_query_occupancy(vmap_ctx* ctx, int obj, const float* pts, long long n, float* occ, float* rgb) {

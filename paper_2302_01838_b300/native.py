@@ -77,6 +77,7 @@ SIGNATURES = {
     "vmap_step": (_I, [_P, _IP, _P]),
     "vmap_set_graph": (_I, [_P, _I]),
     "vmap_set_wait_limit": (_I, [_P, _LL]),
+    "vmap_pose_step": (_I, [_P, _I, _P, _P, _I, _P, _P, ctypes.c_float, ctypes.c_float, _P, _P, _P]),
     "vmap_get_launch": (_I, [_P, _IP, _IP]),
     "vmap_set_launch": (_I, [_P, _IP, _IP]),
     "vmap_autotune": (_I, [_P, _IP, _I, ctypes.POINTER(ctypes.c_float)]),

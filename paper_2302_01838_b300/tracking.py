@@ -1,12 +1,14 @@
 """Camera-pose refinement against a trained object (the map held fixed):
 the per-ray gradients of the object's loss with respect to ray origin and
-direction (vmap_ray_gradients, the encoding backward) give the pose
-gradient, which Adam follows. A camera at position p with rotation R maps
-camera-frame directions d_c to d = R d_c, so dL/dp = sum_rays dL/do and,
-for a rotation update exp([w]x) R, dL/dw = sum_rays d x dL/dd.
+direction (the encoding backward) give the pose gradient, which Adam
+follows. A camera at position p with rotation R maps camera-frame directions
+d_c to d = R d_c, so dL/dp = sum_rays dL/do and, for a rotation update
+exp([w]x) R, dL/dw = sum_rays d x dL/dd.
 
-Library calls only (vmap_sample_rays_given, vmap_ray_gradients,
-vmap_forward); FP32 contexts."""
+Each iteration is one library call (vmap_pose_step: rays from the pose,
+samples, loss and per-ray gradients in one pass, pose gradient and Adam on
+the device); the host reads the pose and the loss curve once at the end.
+FP32 contexts."""
 import numpy as np
 import torch
 
@@ -35,27 +37,17 @@ def refine_pose(vm, obj, n_objects, dc, meas, p0, R0, iters=150, lr_t=2e-3, lr_r
     rays matches their measurements.
       dc:   camera-frame ray directions [n, 3] ((u + 1/2 - cx)/f, (v + 1/2 - cy)/f, 1)
       meas: [n, 5] measured depth, rgb and mask per ray
-    Returns (p, R, losses)."""
-    p, R = np.asarray(p0, np.float64).copy(), np.asarray(R0, np.float64).copy()
+    Returns (p, R, losses): the loss of each iteration is taken before its update."""
     n = dc.shape[0]
-    R_req = [0] * n_objects
-    R_req[obj] = n
-    g = torch.empty(n, 6, device="cuda")
-    loss = torch.empty(n_objects, device="cuda")
-    m = np.zeros(6)
-    v = np.zeros(6)
-    losses = []
-    for it in range(1, iters + 1):
-        rec, d = _records(p, R, dc, meas)
-        vm.sample_rays_given(rec, R_req)
-        vm.forward(loss)
-        losses.append(float(loss[obj]))
-        vm.ray_gradients(g)
-        gg = g.double().cpu().numpy()
-        grad = np.concatenate([gg[:, :3].sum(0), np.cross(d, gg[:, 3:]).sum(0)])
-        m = 0.9 * m + 0.1 * grad
-        v = 0.999 * v + 0.001 * grad * grad
-        step = (m / (1 - 0.9 ** it)) / (np.sqrt(v / (1 - 0.999 ** it)) + 1e-12)
-        p = p - lr_t * step[:3]
-        R = rodrigues(-lr_r * step[3:]) @ R
-    return p, R, losses
+    dcd = torch.from_numpy(np.ascontiguousarray(dc, np.float32)).cuda()
+    measd = torch.from_numpy(np.ascontiguousarray(meas, np.float32)).cuda()
+    pose = torch.from_numpy(np.concatenate([np.asarray(p0, np.float64).ravel(),
+                                            np.asarray(R0, np.float64).ravel()]).astype(np.float32)).cuda()
+    adam = torch.zeros(13, device="cuda")
+    rays_work = torch.empty(n, 12, device="cuda")
+    grad_work = torch.empty(n, 6, device="cuda")
+    losses = torch.empty(iters, n_objects, device="cuda")
+    for it in range(iters):
+        vm.pose_step(obj, dcd, measd, pose, adam, lr_t, lr_r, rays_work, grad_work, losses[it])
+    pose = pose.double().cpu().numpy()
+    return pose[:3], pose[3:].reshape(3, 3), losses[:, obj].double().cpu().numpy().tolist()

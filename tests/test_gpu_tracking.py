@@ -93,3 +93,65 @@ def test_pose_gradient_and_refinement():
           f"(true pose {true_loss:.4f})")
     assert losses[-1] <= true_loss and losses[-1] < 0.8 * losses[0]
     assert np.linalg.norm(p - eye) < 0.03 and rot_err(Rf) < 1.0
+
+
+def test_device_pose_step_matches_its_definition():
+    """vmap_pose_step against the same iteration spelled out from library
+    outputs: rays from the pose, the per-ray gradients of the same batch
+    (vmap_ray_gradients), dL/dp = sum dL/do, dL/dw = sum d x dL/dd, one Adam
+    step (float64 here), R <- exp([w]x) R; and the loss it reports equals
+    vmap_forward on the same batch."""
+    rng = np.random.default_rng(91)
+    o = scenes.make_object(rng, (2, 2), 0.1, 0.25, 0.25, H=32, per_view=256)
+    o["init"] = scenes.init_weights(rng, 32)
+    o["n_surface"], o["n_strat"], o["rays"] = 10, 12, 64
+    sc = dict(objects=[o], B=scenes.make_B(92), seed=91)
+    vm = vh.library_context(sc, max_rays=1024)
+    center = np.asarray(o["center"], np.float64)
+    eye, Rwc = scenes.random_view(rng, center, 2.0)
+    u, v = np.meshgrid(np.arange(0, scenes.W_IMG, 8), np.arange(0, scenes.H_IMG, 8))
+    u, v = u.ravel().astype(np.float64), v.ravel().astype(np.float64)
+    dc = np.stack([(u + 0.5 - scenes.CX) / scenes.FOCAL, (v + 0.5 - scenes.CY) / scenes.FOCAL, np.ones_like(u)], 1)
+    orig, d = scenes.camera_rays(Rwc, eye, u, v)
+    t_hit, rgb = scenes.cast(o["prims"], center, orig, d)
+    sel = np.nonzero(np.isfinite(t_hit))[0][:300]
+    meas = np.zeros((sel.size, 5))
+    meas[:, 0], meas[:, 1:4], meas[:, 4] = t_hit[sel], rgb[sel], 1.0
+    dc = dc[sel]
+    n = sel.size
+    p0 = eye + np.array([0.01, -0.02, 0.015])
+    R0 = tracking.rodrigues(np.array([0.01, 0.02, -0.015])) @ Rwc
+    dcd = torch.from_numpy(dc.astype(np.float32)).cuda()
+    measd = torch.from_numpy(meas.astype(np.float32)).cuda()
+    pose = torch.from_numpy(np.concatenate([p0, R0.ravel()]).astype(np.float32)).cuda()
+    pose_before = pose.double().cpu().numpy()
+    adam = torch.zeros(13, device="cuda")
+    rays = torch.empty(n, 12, device="cuda")
+    gw = torch.empty(n, 6, device="cuda")
+    loss = torch.empty(1, device="cuda")
+    lr_t, lr_r = 2e-3, 4e-3
+    vm.pose_step(0, dcd, measd, pose, adam, lr_t, lr_r, rays, gw, loss)
+    # the same batch (same rays, same draws: the step count is unchanged)
+    g = torch.empty(n, 6, device="cuda")
+    vm.ray_gradients(g)
+    lf = torch.empty(1, device="cuda")
+    vm.forward(lf)
+    assert float(loss[0]) == float(lf[0])
+    g = g.double().cpu().numpy()
+    rec = rays.double().cpu().numpy()
+    assert np.allclose(rec[:, 0:3], pose_before[:3]) and np.allclose(rec[:, 6:11], meas.astype(np.float32))
+    assert np.allclose(rec[:, 3:6], dc.astype(np.float32) @ pose_before[3:].reshape(3, 3).T, atol=1e-6)
+    grad = np.concatenate([g[:, :3].sum(0), np.cross(rec[:, 3:6], g[:, 3:]).sum(0)])
+    a = adam.double().cpu().numpy()
+    # the pose gradient (FP32 sums on the device, FP64 here) through Adam's first moments
+    assert np.linalg.norm(a[:6] - 0.1 * grad) <= 1e-4 * np.linalg.norm(0.1 * grad), (a[:6], 0.1 * grad)
+    assert np.linalg.norm(a[6:12] - 0.001 * grad * grad) <= 1e-4 * np.linalg.norm(0.001 * grad * grad)
+    assert a[12] == 1.0
+    # the update from the device's moments (the first Adam step is about lr * sign(g) per
+    # component, so a component near zero must not decide the comparison)
+    step = (a[:6] / 0.1) / (np.sqrt(a[6:12] / 0.001) + 1e-12)
+    p_exp = pose_before[:3] - lr_t * step[:3]
+    R_exp = tracking.rodrigues(-lr_r * step[3:]) @ pose_before[3:].reshape(3, 3)
+    got = pose.double().cpu().numpy()
+    assert np.allclose(got[:3], p_exp, atol=1e-6), (got[:3], p_exp)
+    assert np.allclose(got[3:].reshape(3, 3), R_exp, atol=1e-6), (got[3:], R_exp)
