@@ -28,13 +28,13 @@ enum TileMode { MODE_TRAIN = 0, MODE_FORWARD = 1, MODE_GRAD_CENTER = 2, MODE_EVA
 // MMAX: samples per tile; CTAS: CTAs per SM (shared memory); THREADS: CTA
 // size. Width 64 (one CTA per SM, 112-sample tiles) runs 16 warps, which
 // hide more shared-memory latency (0.666 vs 0.743 ms per step, 50 objects);
-// width 128 keeps 8: its 48-sample tiles have too few 4x4 register tiles per
-// layer for 512 threads (0.947 vs 0.896 ms per launch).
+// width 128 runs 12: a 48-sample tile has 12 x 32 = 384 4x4 register tiles
+// per hidden layer, one per thread (0.433 vs 0.461 ms per launch with 8).
 template <int H> struct TileCfg;
 template <> struct TileCfg<16>  { static constexpr int MMAX = 120; static constexpr bool GSEP = true;  static constexpr int CTAS = 2; static constexpr int THREADS = 256; };
 template <> struct TileCfg<32>  { static constexpr int MMAX = 136; static constexpr bool GSEP = false; static constexpr int CTAS = 2; static constexpr int THREADS = 256; };
 template <> struct TileCfg<64>  { static constexpr int MMAX = 112; static constexpr bool GSEP = false; static constexpr int CTAS = 1; static constexpr int THREADS = 512; };
-template <> struct TileCfg<128> { static constexpr int MMAX = 48;  static constexpr bool GSEP = false; static constexpr int CTAS = 1; static constexpr int THREADS = 256; };
+template <> struct TileCfg<128> { static constexpr int MMAX = 48;  static constexpr bool GSEP = false; static constexpr int CTAS = 1; static constexpr int THREADS = 384; };
 
 constexpr int RED_FLOATS = 4096;   // split-reduction scratch
 constexpr int RAYF = 16;           // floats of per-ray scratch
@@ -62,8 +62,9 @@ template <int H> struct TileSmem {
 // out[n][m] = epi( sum_k A[k][m] * Bm[k][n] ),  m < Mpad, n < N.
 // A: [K][lda] in smem, Bm: [K][N] dense in smem.
 // EPI 0: + bias, ReLU;  EPI 1: + bias;  EPI 2: * (out[n][m] > 0), in place.
-// A warp covers 8 sample quads x 4 output quads: its A loads touch 128
-// consecutive bytes and its B loads 64, one wavefront each.
+// A warp covers 4 sample quads x 8 output quads: its A loads touch 64
+// consecutive bytes and its B loads 128, one wavefront each; sample quads are
+// grouped by four, so a tile wastes at most three quads of padding per group.
 // ---------------------------------------------------------------------------
 template <int N, int K, int EPI>
 __device__ __forceinline__ void gemm_fwd(const float* __restrict__ A, int lda,
@@ -72,10 +73,10 @@ __device__ __forceinline__ void gemm_fwd(const float* __restrict__ A, int lda,
                                          int Mpad) {
     constexpr int NQ = N / 4;
     const int MQ = Mpad >> 2;
-    const int items = ((MQ + 7) >> 3) * 8 * NQ;
+    const int items = ((MQ + 3) >> 2) * 4 * NQ;
     for (int f = threadIdx.x; f < items; f += blockDim.x) {
-        const int mq = (f / (8 * NQ)) * 8 + (f & 7);
-        const int nq = (f >> 3) % NQ;
+        const int mq = (f / (4 * NQ)) * 4 + (f & 3);
+        const int nq = (f >> 2) % NQ;
         if (mq >= MQ) continue;
         float acc[4][4];
 #pragma unroll
@@ -124,8 +125,10 @@ __device__ __forceinline__ void acc_store(float* p, float v, bool first) { *p = 
 // dW[n][k] (+)= sum_m Z[n][m] * A[k][m]   (reduction over the tile's samples)
 // and db[n] (+)= sum_m Z[n][m], into global g (canonical [n][Kreal]) and gb;
 // `first` stores, otherwise the tile's sums are added to what the run holds.
-// A thread owns rows n = nq + NQ i and k = kq + KQ j (i, j < 4): the eight
-// lanes that differ in nq read eight consecutive rows (no bank conflicts).
+// A thread owns rows n = nq + NQ i and k = kq + KQ j (i, j < 4). Lanes differ
+// in kq: each group of eight reads eight consecutive A rows (no bank
+// conflicts), the Z row is a broadcast, and the run slot's row n is read and
+// written by the warp as consecutive floats (coalesced).
 // The sample range is split SPLIT ways (interleaved quads) to fill the CTA;
 // split partials are combined in a fixed order through smem.
 // ---------------------------------------------------------------------------
@@ -141,7 +144,7 @@ __device__ __forceinline__ void gemm_dw(const float* __restrict__ Z, const float
     const int MQ = Mpad >> 2;
     for (int f = threadIdx.x; f < T * SPLIT; f += blockDim.x) {
         const int s = f / T, r = f % T;
-        const int nq = r % NQ, kq = r / NQ;
+        const int kq = r % KQ, nq = r / KQ;
         float acc[4][4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
@@ -230,10 +233,21 @@ __device__ __forceinline__ void gemm_dw(const float* __restrict__ Z, const float
     }
 }
 
-// copy n floats global -> smem (both 16-byte aligned, n multiple of 4)
-__device__ __forceinline__ void stage(float* dst, const float* __restrict__ src, int n) {
+// copy n floats global -> smem (both 16-byte aligned, n multiple of 4) with
+// asynchronous 16-byte copies: every copy of the thread is in flight at once
+// and no register holds the data. stage_issue only starts them (work that
+// does not touch dst may run meanwhile); stage_wait waits for this thread's
+// copies, and the barrier after it publishes them to the CTA.
+__device__ __forceinline__ void stage_issue(float* dst, const float* __restrict__ src, int n) {
+    const unsigned base = (unsigned)__cvta_generic_to_shared(dst);
     for (int i = threadIdx.x * 4; i < n; i += blockDim.x * 4)
-        *reinterpret_cast<float4*>(dst + i) = *reinterpret_cast<const float4*>(src + i);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(base + 4u * i), "l"(src + i) : "memory");
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void stage_wait() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void stage(float* dst, const float* __restrict__ src, int n) {
+    stage_issue(dst, src, n);
+    stage_wait();
 }
 
 // W1 [H][93] (canonical) -> smem [H][96] zero padded, for the encoding backward
@@ -506,9 +520,10 @@ __global__ void __launch_bounds__(TileCfg<H>::THREADS, TileCfg<H>::CTAS) k_tile_
             g[1 * LD + m] = x1;
             g[2 * LD + m] = x2;
         }
+        stage_issue(ws, WT + wt_layer_off(H, 0), DINP * H);   // W1^T [96][H], during the encoding
         __syncthreads();
         encode<LD>(sp, g, Mpad);
-        stage(ws, WT + wt_layer_off(H, 0), DINP * H);   // W1^T [96][H]
+        stage_wait();
         __syncthreads();
 
         // ---- forward --------------------------------------------------------
@@ -598,9 +613,10 @@ __global__ void __launch_bounds__(TileCfg<H>::THREADS, TileCfg<H>::CTAS) k_tile_
 
         // ---- backward -------------------------------------------------------
         // layer 5: dW5 = dY^T h4, dZ4 = (dY W5) * [h4 > 0]
+        stage_issue(ws, P + w_off(H, 4), NOUT * H);     // W5 [4][H] == B[k=out][n=in]
         gemm_dw<NOUT, H, TileCfg<H>::THREADS>(yb, act + 3 * H * LD, LD, Mpad, red, gp + w_off(H, 4), H,
                                              gp + b_off(H, 4), first);
-        stage(ws, P + w_off(H, 4), NOUT * H);     // W5 [4][H] == B[k=out][n=in]
+        stage_wait();
         __syncthreads();
         gemm_fwd<H, NOUT, 2>(yb, LD, ws, nullptr, act + 3 * H * LD, LD, Mpad);
         __syncthreads();
@@ -609,8 +625,9 @@ __global__ void __launch_bounds__(TileCfg<H>::THREADS, TileCfg<H>::CTAS) k_tile_
             // dW_{l+1} = dZ_{l+1}^T h_l ; dZ_l = (dZ_{l+1} W_{l+1}) * [h_l > 0]
             float* hz = act + l * H * LD;
             float* ha = act + (l - 1) * H * LD;
+            stage_issue(ws, P + w_off(H, l), H * H);
             gemm_dw<H, H, TileCfg<H>::THREADS>(hz, ha, LD, Mpad, red, gp + w_off(H, l), H, gp + b_off(H, l), first);
-            stage(ws, P + w_off(H, l), H * H);
+            stage_wait();
             __syncthreads();
             gemm_fwd<H, H, 2>(hz, LD, ws, nullptr, ha, LD, Mpad);
             __syncthreads();
