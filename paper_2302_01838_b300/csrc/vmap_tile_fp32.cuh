@@ -78,11 +78,16 @@ __device__ __forceinline__ void gemm_fwd(const float* __restrict__ A, int lda,
         const int mq = (f / (4 * NQ)) * 4 + (f & 3);
         const int nq = (f >> 2) % NQ;
         if (mq >= MQ) continue;
-        float acc[4][4];
+        float acc[4][4], bb[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+        if (EPI != 2) {
+            // the bias, loaded before the k loop (its latency hides there)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bb[j] = bias[nq * 4 + j];
+        }
         const float* a = A + mq * 4;
         const float* b = Bm + nq * 4;
 #pragma unroll 8
@@ -108,8 +113,7 @@ __device__ __forceinline__ void gemm_fwd(const float* __restrict__ A, int lda,
                 v.z = prev.z > 0.f ? acc[2][j] : 0.f;
                 v.w = prev.w > 0.f ? acc[3][j] : 0.f;
             } else {
-                const float bb = bias[n];
-                v.x = acc[0][j] + bb; v.y = acc[1][j] + bb; v.z = acc[2][j] + bb; v.w = acc[3][j] + bb;
+                v.x = acc[0][j] + bb[j]; v.y = acc[1][j] + bb[j]; v.z = acc[2][j] + bb[j]; v.w = acc[3][j] + bb[j];
                 if (EPI == 0) {
                     v.x = fmaxf(v.x, 0.f); v.y = fmaxf(v.y, 0.f); v.z = fmaxf(v.z, 0.f); v.w = fmaxf(v.w, 0.f);
                 }
@@ -130,7 +134,9 @@ __device__ __forceinline__ void acc_store(float* p, float v, bool first) { *p = 
 // conflicts), the Z row is a broadcast, and the run slot's row n is read and
 // written by the warp as consecutive floats (coalesced).
 // The sample range is split SPLIT ways (interleaved quads) to fill the CTA;
-// split partials are combined in a fixed order through smem.
+// split partials are combined in a fixed order through smem. Without a split
+// the accumulators start from the run's old values (loaded before the sample
+// loop, which hides their latency). NT is the CTA size.
 // ---------------------------------------------------------------------------
 template <int N, int KP, int NT = NTHREADS>
 __device__ __forceinline__ void gemm_dw(const float* __restrict__ Z, const float* __restrict__ A,
@@ -141,15 +147,33 @@ __device__ __forceinline__ void gemm_dw(const float* __restrict__ Z, const float
     constexpr int S1 = RED_FLOATS / (N * KP) > 0 ? RED_FLOATS / (N * KP) : 1;
     constexpr int SPLIT = S0 < S1 ? S0 : S1;   // SPLIT == 1 never touches red
     static_assert(SPLIT >= 1 && (SPLIT == 1 || SPLIT * N * KP <= RED_FLOATS), "split scratch");
+    constexpr int NB = (N * 8 + NT - 1) / NT;   // bias-gradient items per thread
     const int MQ = Mpad >> 2;
+    // the bias slot's old values, loaded first (in flight during the GEMM)
+    float bold[NB];
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+        const int f = threadIdx.x + u * NT;
+        bold[u] = (!first && f < N * 8 && (f & 7) == 0) ? gb[f >> 3] : 0.f;
+    }
     for (int f = threadIdx.x; f < T * SPLIT; f += blockDim.x) {
         const int s = f / T, r = f % T;
         const int kq = r % KQ, nq = r / KQ;
         float acc[4][4];
+        if (SPLIT == 1 && !first) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+                for (int j = 0; j < 4; ++j) {
+                    const int k = kq + KQ * j;
+                    acc[i][j] = k < Kreal ? g[(nq + NQ * i) * Kreal + k] : 0.f;
+                }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+        }
         for (int q = s; q < MQ; q += SPLIT) {
             float4 z[4], a[4];
 #pragma unroll
@@ -169,16 +193,6 @@ __device__ __forceinline__ void gemm_dw(const float* __restrict__ Z, const float
                 }
         }
         if (SPLIT == 1) {
-            // read what the run holds first (16 independent loads in flight), then add and store
-            if (!first) {
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const int k = kq + KQ * j;
-                        if (k < Kreal) acc[i][j] += g[(nq + NQ * i) * Kreal + k];
-                    }
-            }
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -194,7 +208,10 @@ __device__ __forceinline__ void gemm_dw(const float* __restrict__ Z, const float
         }
     }
     // bias gradient: 8 lanes per output row, combined by a fixed xor tree
-    for (int f = threadIdx.x; f < N * 8; f += blockDim.x) {
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+        const int f = threadIdx.x + u * NT;
+        if (f >= N * 8) break;   // uniform per warp: N * 8 is a multiple of 32
         const int n = f >> 3, l = f & 7;
         float v = 0.f;
         for (int q = l; q < MQ; q += 8) {
@@ -204,7 +221,7 @@ __device__ __forceinline__ void gemm_dw(const float* __restrict__ Z, const float
         v += __shfl_xor_sync(0xffffffffu, v, 4);
         v += __shfl_xor_sync(0xffffffffu, v, 2);
         v += __shfl_xor_sync(0xffffffffu, v, 1);
-        if (l == 0) acc_store(gb + n, v, first);
+        if (l == 0) gb[n] = first ? v : bold[u] + v;
     }
     if (SPLIT > 1) {
         __syncthreads();
@@ -259,18 +276,60 @@ __device__ __forceinline__ void stage_w1_rows(float* dst, const float* __restric
     }
 }
 
+// sin p and cos p. For |p| <= 2^17 (the encoding's arguments stay far below:
+// |B x~| is a few thousand at most): Cody & Waite's additive range reduction,
+// p = k pi/2 + r with pi/2 split in two floats (c1 = pi/2 rounded, c2 the
+// rest; the fused multiply-adds take k c1 exactly, and the dropped tail
+// |k| 1.8e-15 stays below 3e-10), |r| <= pi/4 (+1 ulp); then the Taylor
+// series of sin to r^9 and cos to r^10 (truncation below 2e-9), and the
+// quadrant k mod 4 picks and signs them. Its result agrees with sincosf to a
+// few ulp; a dependent chain of about 20 operations instead of the library
+// routine's longer one. Larger |p| goes to sincosf.
+__device__ __forceinline__ void sincos_enc(float p, float* sp_, float* cp_) {
+    if (fabsf(p) > 131072.f) {
+        sincosf(p, sp_, cp_);
+        return;
+    }
+    const float k = rintf(p * 0.636619746685028076171875f);        // 2/pi
+    float r = fmaf(-k, 1.57079637050628662109375f, p);            // c1
+    r = fmaf(-k, -4.37113882867379300296306610107421875e-8f, r);  // c2
+    const float r2 = r * r;
+    float ps = fmaf(r2, 2.7557319223985893e-6f, -1.9841269841269841e-4f);   // 1/9!, -1/7!
+    ps = fmaf(r2, ps, 8.3333333333333333e-3f);                               // 1/5!
+    ps = fmaf(r2, ps, -1.6666666666666667e-1f);                              // -1/3!
+    const float sn = fmaf(r * r2, ps, r);
+    float pc = fmaf(r2, -2.7557319223985891e-7f, 2.4801587301587302e-5f);    // -1/10!, 1/8!
+    pc = fmaf(r2, pc, -1.3888888888888889e-3f);                              // -1/6!
+    pc = fmaf(r2, pc, 4.1666666666666667e-2f);                               // 1/4!
+    pc = fmaf(r2, pc, -0.5f);                                                // -1/2!
+    const float cs = fmaf(r2, pc, 1.f);
+    const int q = (int)k & 3;
+    const float s0 = (q & 1) ? cs : sn, c0 = (q & 1) ? sn : cs;
+    *sp_ = (q & 2) ? -s0 : s0;
+    *cp_ = ((q + 1) & 2) ? -c0 : c0;
+}
+
 // Gaussian encoding of the tile's points: rows 0..2 of g hold x~ on entry;
 // rows 3..47 get sin(B x~), rows 48..92 cos(B x~), rows 93..95 zero.
+// Item f = j Mpad + m is stepped by the CTA size without a division per item.
 template <int LD>
 __device__ __forceinline__ void encode(const StepParams& sp, float* g, int Mpad) {
-    for (int f = threadIdx.x; f < NF * Mpad; f += blockDim.x) {
-        const int j = f / Mpad, m = f - j * Mpad;
+    if (Mpad <= 0) return;
+    const int dq = blockDim.x / Mpad, dr = blockDim.x - dq * Mpad;
+    int j = threadIdx.x / Mpad, m = threadIdx.x - j * Mpad;
+    for (; j < NF;) {
         const float p = fmaf(sp.B[3 * j + 2], g[2 * LD + m],
                              fmaf(sp.B[3 * j + 1], g[1 * LD + m], sp.B[3 * j] * g[0 * LD + m]));
         float s, c;
-        sincosf(p, &s, &c);
+        sincos_enc(p, &s, &c);
         g[(3 + j) * LD + m] = s;
         g[(3 + NF + j) * LD + m] = c;
+        j += dq;
+        m += dr;
+        if (m >= Mpad) {
+            m -= Mpad;
+            ++j;
+        }
     }
     for (int i = threadIdx.x; i < 3 * Mpad; i += blockDim.x) g[(DIN + i / Mpad) * LD + (i % Mpad)] = 0.f;
 }
