@@ -2,7 +2,10 @@
 // counts, lay out this step's batch (ray and sample offsets), cut every
 // object's rays into tiles per width class, assign tiles to the persistent
 // CTAs, number the gradient runs and their partial slots, and list the
-// reduce work. Everything the step's other kernels need is read back from
+// reduce work. A class whose tiles fit its dynamic slot capacity is
+// scheduled dynamically: its CTAs take tiles from a counter, and every tile
+// is a run with its own slot (the slot depends on the tile, not on the CTA
+// that processes it, so the sums stay reproducible). Everything the step's other kernels need is read back from
 // device memory, so the launch sequence never changes when objects are
 // admitted, stopped or resized (the step can be captured in a CUDA graph
 // once and replayed).
@@ -20,7 +23,7 @@ __host__ __device__ inline int hidden_of(int c) { return 16 << c; }
 
 // counts written by k_build (device int array)
 enum BuildCount { BC_TILES = 0 /* + class */, BC_NB = 4, BC_RAYS = 5, BC_SAMPLES_LO = 6, BC_SAMPLES_HI = 7,
-                  BC_ITEMS = 8, BC_N = 16 };
+                  BC_ITEMS = 8, BC_DYN = 9 /* + class: scheduled dynamically */, BC_N = 16 };
 
 struct BuildArgs {
     const ObjDev* objs;
@@ -33,6 +36,7 @@ struct BuildArgs {
     int mmax[NCLASS];          // samples per tile, at most, per class
     int rtmax;                 // rays per tile, at most
     int grid[NCLASS];          // persistent grid per class
+    int dyn_cap[NCLASS];       // most tiles a class may have to be scheduled dynamically; 0: never
     TileDev* tiles;            // [NCLASS][tile_cap]
     int* flags;                // [NCLASS][tile_cap] scratch
     int tile_cap;
@@ -182,9 +186,12 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_build(BuildArgs a) {
         TileDev* tl = a.tiles + (long long)q * a.tile_cap;
         int* fl = a.flags + (long long)q * a.tile_cap;
         const long long stride = param_count(hidden_of(q)) + NEXTRA;
-        for (int t = threadIdx.x; t < n; t += BUILD_THREADS) fl[t] = (t == 0 || tl[t].obj != tl[t - 1].obj) ? 1 : 0;
+        const bool dyn = a.dyn_cap[q] > 0 && n <= a.dyn_cap[q];
+        if (threadIdx.x == 0) a.counts[BC_DYN + q] = dyn ? 1 : 0;
+        for (int t = threadIdx.x; t < n; t += BUILD_THREADS)
+            fl[t] = (dyn || t == 0 || tl[t].obj != tl[t - 1].obj) ? 1 : 0;
         __syncthreads();
-        for (int cta = threadIdx.x; cta < G; cta += BUILD_THREADS) {
+        for (int cta = threadIdx.x; !dyn && cta < G; cta += BUILD_THREADS) {
             const long long s = (long long)cta * n / G;
             if (s < n) fl[s] = 1;
         }

@@ -54,6 +54,7 @@ int ctas_of(int c) {
 }
 bool valid_hidden(int H) { return H == 16 || H == 32 || H == 64 || H == 128; }
 constexpr int GMULT_MAX = 2;   // persistent grid: n_sm * CTAS * gmult CTAs per class
+constexpr long long DYN_SLOT_BYTES = 256LL << 20;   // per class, for dynamically scheduled FP32 classes
 
 struct ProfPair {
     int slot;
@@ -98,6 +99,8 @@ struct vmap_ctx {
     int2* items_d = nullptr;
     int* counts_d = nullptr;
     int* sig_d = nullptr;           // inputs of the last batch build ([0] = -1: rebuild)
+    int* dyn_d = nullptr;           // [NCLASS][2] tile counters of dynamically scheduled classes
+    int dyn_cap[NCLASS] = {0, 0, 0, 0};   // tiles a class may have to be scheduled dynamically
     int* done_d = nullptr;          // per object: reduce warps that have finished (reset by the last)
     long long build_key = -1;       // launch shape the last build ran with
     // host-side inputs of the last batch build: when none changed, the builder
@@ -308,11 +311,12 @@ TileArgs base_args(vmap_ctx* ctx) {
 
 enum { PDL_NONE = 0, PDL_AFTER_SAMPLE = 1, PDL_AFTER_TILE = 2 };
 
-// FP32 tile kernel, launched in stream order (chaining the FP32 width classes
-// by programmatic dependent launch, as the BF16 ones are, measured 10% slower
-// on the room workload although no kernel's own time changed)
+// FP32 tile kernel. With PDL_AFTER_TILE it is launched with programmatic
+// stream serialization behind another width class's FP32 tile kernel: its CTAs
+// start on the SMs that kernel leaves (the classes touch disjoint objects and
+// slots) and it completes only after that kernel.
 template <int H, int MODE>
-cudaError_t launch_tile(int grid, cudaStream_t st, const StepParams& sp, const TileArgs& ta) {
+cudaError_t launch_tile(int grid, cudaStream_t st, const StepParams& sp, const TileArgs& ta, int pdl = PDL_NONE) {
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_tile_fp32<H, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -321,17 +325,27 @@ cudaError_t launch_tile(int grid, cudaStream_t st, const StepParams& sp, const T
         attr_set = true;
     }
     if (grid <= 0) return cudaSuccess;
-    k_tile_fp32<H, MODE><<<grid, TileCfg<H>::THREADS, TileSmem<H>::BYTES, st>>>(sp, ta);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(TileCfg<H>::THREADS);
+    cfg.dynamicSmemBytes = TileSmem<H>::BYTES;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl == PDL_AFTER_TILE ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k_tile_fp32<H, MODE>, sp, ta);
 }
 
 template <int MODE>
-cudaError_t launch_tile_c(int c, int grid, cudaStream_t st, const StepParams& sp, const TileArgs& ta) {
+cudaError_t launch_tile_c(int c, int grid, cudaStream_t st, const StepParams& sp, const TileArgs& ta,
+                          int pdl = PDL_NONE) {
     switch (c) {
-        case 0: return launch_tile<16, MODE>(grid, st, sp, ta);
-        case 1: return launch_tile<32, MODE>(grid, st, sp, ta);
-        case 2: return launch_tile<64, MODE>(grid, st, sp, ta);
-        default: return launch_tile<128, MODE>(grid, st, sp, ta);
+        case 0: return launch_tile<16, MODE>(grid, st, sp, ta, pdl);
+        case 1: return launch_tile<32, MODE>(grid, st, sp, ta, pdl);
+        case 2: return launch_tile<64, MODE>(grid, st, sp, ta, pdl);
+        default: return launch_tile<128, MODE>(grid, st, sp, ta, pdl);
     }
 }
 
@@ -449,7 +463,11 @@ cudaError_t launch_class(vmap_ctx* ctx, int c, int pdl = PDL_NONE) {
             default: return launch_tile_bf16<64, BM>(grid, ctx->stream, ctx->sp, ba, pdl);
         }
     }
-    return launch_tile_c<MODE>(c, grid, ctx->stream, ctx->sp, ta);
+    if (ctx->dyn_cap[c] > 0) {
+        ta.dyn = ctx->dyn_d + 2 * c;
+        ta.dyn_on = ctx->counts_d + BC_DYN + c;
+    }
+    return launch_tile_c<MODE>(c, grid, ctx->stream, ctx->sp, ta, pdl);
 }
 
 int class_mmax(vmap_ctx* ctx, int c) { return uses_tc(ctx, c) || uses_wide(ctx, c) ? TM : mmax_of(c); }
@@ -467,6 +485,7 @@ vmap_status launch_build_sample(vmap_ctx* ctx, int given, bool build = true) {
         a.rt[c] = ctx->rt[c];
         a.mmax[c] = class_mmax(ctx, c);
         a.grid[c] = grid_of(ctx, c);
+        a.dyn_cap[c] = ctx->dyn_cap[c];
         a.part_base[c] = ctx->part_base[c];
     }
     a.rtmax = RTMAX;
@@ -496,12 +515,18 @@ vmap_status launch_build_sample(vmap_ctx* ctx, int given, bool build = true) {
     return VMAP_OK;
 }
 
+// FP32 classes run widest first: the hidden-128 kernel's long tiles start at
+// once, and the narrower classes (scheduled dynamically when their slots
+// allow) start on the SMs it leaves and fill them as they free up.
 template <int MODE>
 vmap_status launch_tiles(vmap_ctx* ctx, int mask) {
     bool after_tile = false;   // the last launch in the stream is a BF16 tile kernel
+    bool after_fp32 = false;   // ... an FP32 tile kernel
     bool after_sample = ctx->after_sample;   // ... the sampler
     ctx->after_sample = false;
-    for (int c = 0; c < NCLASS; ++c) {
+    static const int order_tc[NCLASS] = {0, 1, 2, 3}, order_fp32[NCLASS] = {3, 0, 1, 2};
+    for (int ci = 0; ci < NCLASS; ++ci) {
+        const int c = ctx->bf16 ? order_tc[ci] : order_fp32[ci];
         if (!(mask & (1 << c))) continue;
         cudaError_t e;
         const bool after_sample_c = after_sample;   // only the first launch follows the sampler
@@ -521,13 +546,13 @@ vmap_status launch_tiles(vmap_ctx* ctx, int mask) {
             const int pi = MODE == MODE_TRAIN ? prof_begin(ctx, PS_TILE + c) : -1;
             // the first class starts behind the sampler, each further one behind
             // the previous class's tile kernel (no profiling event between)
-            const int pdl = !uses_tc(ctx, c) || pi >= 0 ? PDL_NONE
-                          : after_sample_c           ? PDL_AFTER_SAMPLE
-                          : after_tile               ? PDL_AFTER_TILE
-                                                     : PDL_NONE;
+            int pdl = PDL_NONE;
+            if (pi < 0 && uses_tc(ctx, c)) pdl = after_sample_c ? PDL_AFTER_SAMPLE : after_tile ? PDL_AFTER_TILE : PDL_NONE;
+            if (pi < 0 && !uses_tc(ctx, c) && after_fp32) pdl = PDL_AFTER_TILE;
             e = launch_class<MODE>(ctx, c, pdl);
             prof_end(ctx, pi);
             after_tile = uses_tc(ctx, c) && pi < 0;
+            after_fp32 = !uses_tc(ctx, c) && pi < 0;
         }
         if (e != cudaSuccess)
             return fail(ctx, VMAP_ERR_CUDA, "tile kernel (H=%d) failed: %s", hidden_of(c), cudaGetErrorString(e));
@@ -543,7 +568,7 @@ vmap_status launch_reduce(vmap_ctx* ctx, int mode, const float* grad_loss, float
                           float* dcenter_out, bool train = false) {
     const int pi = prof_begin(ctx, PS_REDUCE);
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(ctx->n_sm * 3));
+    cfg.gridDim = dim3((unsigned)(ctx->n_sm * REDUCE_BLOCKS_PER_SM));
     cfg.blockDim = dim3(REDUCE_THREADS);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = ctx->stream;
@@ -828,17 +853,25 @@ vmap_status vmap_init_objects(vmap_ctx** out, const vmap_config* cfg, void* cuda
     ctx->tile_cap = cfg->max_rays_total + 16;
     ALLOC(ctx->tiles_d, sizeof(TileDev) * (size_t)ctx->tile_cap * NCLASS);
     ALLOC(ctx->flags_d, sizeof(int) * (size_t)ctx->tile_cap * NCLASS);
-    // run slots per class: at most one per CTA plus one per object
+    // run slots per class: at most one per CTA plus one per object; the FP32
+    // hidden 16-64 classes may also take one per tile (dynamic scheduling) up
+    // to DYN_SLOT_BYTES of slots, and are scheduled statically when a step has
+    // more tiles than that
     long long part = 0;
     for (int c = 0; c < NCLASS; ++c) {
         ctx->part_base[c] = part;
-        const long long slots = (long long)ctx->n_sm * ctas_of(c) * GMULT_MAX + K;
-        part += slots * (param_count(hidden_of(c)) + NEXTRA);
+        const long long stride = param_count(hidden_of(c)) + NEXTRA;
+        ctx->dyn_cap[c] = 0;
+        if (!ctx->bf16 && c < 3)
+            ctx->dyn_cap[c] = (int)std::min<long long>(ctx->tile_cap, DYN_SLOT_BYTES / (stride * (long long)sizeof(float)));
+        const long long slots = std::max<long long>((long long)ctx->n_sm * ctas_of(c) * GMULT_MAX + K, ctx->dyn_cap[c]);
+        part += slots * stride;
     }
     ALLOC(ctx->part_d, sizeof(float) * part);
     ALLOC(ctx->items_d, sizeof(int2) * (size_t)K * ((param_count(128) + REDUCE_CHUNK - 1) / REDUCE_CHUNK));
     ALLOC(ctx->counts_d, sizeof(int) * BC_N);
     ALLOC(ctx->sig_d, sizeof(int) * (2 + (size_t)K));
+    ALLOC(ctx->dyn_d, sizeof(int) * 2 * NCLASS);
     ALLOC(ctx->done_d, sizeof(int) * K);
     ALLOC(ctx->given_d, sizeof(float) * REC * (size_t)cfg->max_rays_total);
     ALLOC(ctx->loss_d, sizeof(float) * K);
@@ -859,6 +892,7 @@ vmap_status vmap_init_objects(vmap_ctx** out, const vmap_config* cfg, void* cuda
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->n_obj_d, 0, sizeof(int), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->counts_d, 0, sizeof(int) * BC_N, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->sig_d, 0xFF, sizeof(int) * (2 + (size_t)K), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->dyn_d, 0, sizeof(int) * 2 * NCLASS, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->done_d, 0, sizeof(int) * K, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->err_d, 0, sizeof(int), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->img_off_d, 0xFF, sizeof(long long) * K, ctx->stream);
@@ -879,7 +913,7 @@ vmap_status vmap_destroy(vmap_ctx* ctx) {
                     ctx->params_d, ctx->wt_d,     ctx->m_d,      ctx->v_d,     ctx->pool_d,   ctx->pick_d,
                     ctx->t_d,      ctx->bobj_d,   ctx->bray_d,   ctx->tiles_d, ctx->flags_d,  ctx->part_d,
                     ctx->items_d,  ctx->counts_d, ctx->given_d,  ctx->loss_d,  ctx->err_d,  ctx->img_off_d,
-                    ctx->img_d,    ctx->act_d,    ctx->act_pp_d, ctx->tile_loss_d, ctx->sig_d,  ctx->done_d,
+                    ctx->img_d,    ctx->act_d,    ctx->act_pp_d, ctx->tile_loss_d, ctx->sig_d,  ctx->done_d, ctx->dyn_d,
                     ctx->scene_d,  ctx->ray_bj_d, ctx->loss_pp_d};
     for (void* p : ptrs)
         if (p) cudaFree(p);

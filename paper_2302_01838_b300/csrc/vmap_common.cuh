@@ -78,6 +78,14 @@ __host__ __device__ constexpr long long wt_layer_off(int H, int l) {
     return l == 0 ? 0 : (long long)DINP * H + (long long)(l - 1) * H * H;
 }
 
+// programmatic dependent launch: let the next kernel of the stream (when it was
+// launched with programmatic stream serialization) start; without such a
+// dependent this has no effect
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+// wait until the grids this one depends on have completed and their writes are
+// visible (returns at once for a grid launched without programmatic dependences)
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 products.
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll

@@ -95,11 +95,13 @@ __device__ __forceinline__ long long wt_index(int H, long long p) {
 // warp of an object to finish (every other one has read the step count)
 // advances the object's step count unless it is frozen, and resets its counter.
 constexpr int REDUCE_THREADS = 256;
+constexpr int REDUCE_SLOT_LOADS = 4;    // slot loads in flight per lane
+constexpr int REDUCE_BLOCKS_PER_SM = 3; // the grid
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 __device__ __forceinline__ float& at4(float4& v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
 
-__global__ void __launch_bounds__(REDUCE_THREADS, 3) k_reduce(StepParams sp, const ObjDev* __restrict__ objs,
+__global__ void __launch_bounds__(REDUCE_THREADS, REDUCE_BLOCKS_PER_SM) k_reduce(StepParams sp, const ObjDev* __restrict__ objs,
                                                            const ObjBatch* __restrict__ obs,
                                                            const int2* __restrict__ items,
                                                            const int* __restrict__ counts,
@@ -181,12 +183,12 @@ __global__ void __launch_bounds__(REDUCE_THREADS, 3) k_reduce(StepParams sp, con
         }
         if (act) {
             const float* src = part + bt.part_off + p;
-            for (int t = 0; t < nr; t += 4) {   // four (predicated) slot loads in flight, added in slot order
-                float4 v[4];
+            for (int t = 0; t < nr; t += REDUCE_SLOT_LOADS) {   // (predicated) slot loads in flight, added in slot order
+                float4 v[REDUCE_SLOT_LOADS];
 #pragma unroll
-                for (int w = 0; w < 4; ++w) v[w] = t + w < nr ? ld4(src + (long long)(t + w) * stride) : g;
+                for (int w = 0; w < REDUCE_SLOT_LOADS; ++w) v[w] = t + w < nr ? ld4(src + (long long)(t + w) * stride) : g;
 #pragma unroll
-                for (int w = 0; w < 4; ++w)
+                for (int w = 0; w < REDUCE_SLOT_LOADS; ++w)
                     if (t + w < nr) {
                         g.x += v[w].x; g.y += v[w].y; g.z += v[w].z; g.w += v[w].w;
                     }

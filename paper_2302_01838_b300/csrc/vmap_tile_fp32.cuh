@@ -9,7 +9,10 @@
 // each tile's weight gradient into the run's slot of the partial buffer (the
 // first tile stores, the next ones add), so an object has at most
 // (CTAs covering it + 1) slots and the reduce/Adam kernel adds them in a
-// fixed order: results are bitwise reproducible.
+// fixed order: results are bitwise reproducible. When the builder schedules
+// the class dynamically, the CTAs take tiles from a counter instead, and each
+// tile stores into its own slot: the CTAs that start early (on SMs another
+// width class's kernel has left) take more tiles, and the sums stay the same.
 //
 // Activations live in shared memory, feature-major [feature][sample], row
 // stride LD = Mpad + 4 (LD = 4 mod 8: eight consecutive rows read at one
@@ -356,6 +359,8 @@ struct TileArgs {
     const float* qpts;        // MODE_QUERY: points [n][3]
     float* qocc;              // MODE_QUERY: occupancy [n]
     float* qrgb;              // MODE_QUERY: colour [n][3] or NULL
+    int* dyn;                 // [2]: next tile, CTAs done (dynamic scheduling), or NULL
+    const int* dyn_on;        // builder: non-zero when this step schedules the class dynamically
 };
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -470,17 +475,31 @@ __global__ void __launch_bounds__(TileCfg<H>::THREADS, TileCfg<H>::CTAS) k_tile_
     float* rays = smem + SM::RAYS;
     const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
 
+    __shared__ long long s_tile;
     long long t0, t1;
+    bool dyn = false;
     if (TRAINISH) {
         const long long n = *ta.n_tiles;
-        t0 = (long long)blockIdx.x * n / gridDim.x;
-        t1 = (long long)(blockIdx.x + 1) * n / gridDim.x;
+        dyn = ta.dyn != nullptr && *ta.dyn_on != 0;
+        t0 = dyn ? 0 : (long long)blockIdx.x * n / gridDim.x;
+        t1 = dyn ? n : (long long)(blockIdx.x + 1) * n / gridDim.x;
     } else {
         t0 = blockIdx.x;
         t1 = t0 + 1;
     }
+    // a width class launched behind this one may start on the SMs it leaves
+    pdl_launch_dependents();
 #pragma unroll 1
-    for (long long tl = t0; tl < t1; ++tl) {
+    for (long long it = t0;; ++it) {
+        long long tl = it;
+        if (dyn) {
+            // every thread read the previous tile index before the barrier that
+            // ended the previous tile
+            if (threadIdx.x == 0) s_tile = atomicAdd(ta.dyn, 1);
+            __syncthreads();
+            tl = s_tile;
+        }
+        if (tl >= t1) break;
         // ---- the tile -----------------------------------------------------
         int k, nr, S;
         long long sbase = 0, part = 0, ray_first;
@@ -499,7 +518,7 @@ __global__ void __launch_bounds__(TileCfg<H>::THREADS, TileCfg<H>::CTAS) k_tile_
             part = td.part;
             S = ta.objs[k].S;
             sbase = ta.obs[k].sample_off + (long long)(td.ray0 - ta.obs[k].ray_off) * S;
-            first = tl == t0 || ta.tiles[tl - 1].obj != k;
+            first = dyn || tl == t0 || ta.tiles[tl - 1].obj != k;
         }
         const ObjDev& ob = ta.objs[k];
         const int M = nr * S;
@@ -777,6 +796,14 @@ __global__ void __launch_bounds__(TileCfg<H>::THREADS, TileCfg<H>::CTAS) k_tile_
         }
         __syncthreads();
     }
+    if (dyn && threadIdx.x == 0 && atomicAdd(ta.dyn + 1, 1) == (int)gridDim.x - 1) {
+        // every CTA has taken its last tile: reset the counter for the next launch
+        ta.dyn[0] = 0;
+        ta.dyn[1] = 0;
+    }
+    // launched behind another width class's tile kernel (programmatic stream
+    // serialization, no wait at the start): complete only after it
+    pdl_wait();
 }
 
 }  // namespace vmapk
