@@ -93,7 +93,7 @@ __device__ __forceinline__ void gemm_fwd(const float* __restrict__ A, int lda,
         }
         const float* a = A + mq * 4;
         const float* b = Bm + nq * 4;
-#pragma unroll 8
+#pragma unroll 16
         for (int k = 0; k < K; ++k) {
             const float4 av = *reinterpret_cast<const float4*>(a + k * lda);
             const float4 bv = *reinterpret_cast<const float4*>(b + k * N);
@@ -177,6 +177,7 @@ __device__ __forceinline__ void gemm_dw(const float* __restrict__ Z, const float
 #pragma unroll
                 for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
         }
+#pragma unroll 2
         for (int q = s; q < MQ; q += SPLIT) {
             float4 z[4], a[4];
 #pragma unroll
