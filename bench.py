@@ -90,7 +90,7 @@ def flops_per_sample(H, part="all"):
     forward F = 93H + 3H^2 + 4H MACs, weight gradient F MACs, input gradient
     3H^2 + 4H MACs (layer 1 skipped); 2 flops per MAC. part = "fb" (forward
     and input gradients) or "dw" (weight gradients) splits the sum the way
-    the width-128 path splits its two kernels."""
+    the width-128 paths (tensor-core and FP32) split their two kernels."""
     F = 93 * H + 3 * H * H + 4 * H
     fb, dw = 2 * (F + 3 * H * H + 4 * H), 2 * F
     return {"all": fb + dw, "fb": fb, "dw": dw}[part]
@@ -99,7 +99,8 @@ def flops_per_sample(H, part="all"):
 def kernel_flops(name, objs):
     """Algorithmic flops of one launch of a tile kernel on the workload."""
     H = int(name.split("<")[1].rstrip(">"))
-    part = "fb" if name.startswith("k_wide_fb") else "dw" if name.startswith("k_wide_dw") else "all"
+    part = ("fb" if name.startswith(("k_wide_fb", "k_w32_fb")) else
+            "dw" if name.startswith(("k_wide_dw", "k_w32_dw")) else "all")
     return sum(o["rays"] * (o["n_surface"] + o["n_strat"]) * flops_per_sample(H, part) for o in objs if o["H"] == H)
 
 
@@ -354,7 +355,7 @@ def roofline_of(prof, objs, precision, peaks, props, prof_steps):
     """Roofline of the dominant tile kernel: algorithmic flops per launch /
     its mean CUDA-event duration, against the measured BF16 burst peak
     (tensor-core kernels) or the FP32 FFMA peak (FP32 SIMT kernels)."""
-    tiles = {k: v for k, v in prof.items() if k.startswith(("k_tile", "k_wide"))}
+    tiles = {k: v for k, v in prof.items() if k.startswith(("k_tile", "k_wide", "k_w32"))}
     dom = max(tiles, key=lambda k: tiles[k][1])
     flops = kernel_flops(dom, objs)
     n_l, dom_ms = tiles[dom]

@@ -23,6 +23,7 @@
 #include "vmap_scene.cuh"
 #include "vmap_tile_bf16.cuh"
 #include "vmap_tile_fp32.cuh"
+#include "vmap_tile_w32.cuh"
 #include "vmap_tile_wide.cuh"
 
 using namespace vmapk;
@@ -139,7 +140,7 @@ struct vmap_ctx {
     unsigned char* act_d = nullptr;
     unsigned char** act_pp_d = nullptr;
     long long act_cap = 0;          // tiles
-    float* tile_loss_d = nullptr;   // [tile_cap][4]
+    float* tile_loss_d = nullptr;   // [tile_cap][8] per-tile loss sums (the BF16 pair uses 4 of them)
     // scene rendering: per (object, ray) records, grown on demand
     float* scene_d = nullptr;
     long long scene_cap = 0;        // floats
@@ -286,13 +287,16 @@ int class_mask(vmap_ctx* ctx) {
 
 bool uses_tc(vmap_ctx* ctx, int c) { return ctx->bf16 && c < 3; }
 bool uses_wide(vmap_ctx* ctx, int c) { return ctx->bf16 && c == 3; }
+// the FP32 width-128 pair (k_w32_fb, k_w32_dw)
+bool uses_w32(vmap_ctx* ctx, int c) { return !ctx->bf16 && c == 3; }
 
-// tile ranges of the width-128 weight-gradient kernel (WJOBS CTAs each; one wave of CTAs at gmult 1)
-int wide_ranges(vmap_ctx* ctx) { return std::max(1, ctx->n_sm / WJOBS) * ctx->gmult[3]; }
+// tile ranges of the width-128 weight-gradient kernel (WJOBS or W32JOBS CTAs
+// each; one wave of CTAs at gmult 1)
+int wide_ranges(vmap_ctx* ctx) { return std::max(1, ctx->n_sm / (ctx->bf16 ? WJOBS : W32JOBS)) * ctx->gmult[3]; }
 
 // CTA ranges that own a run slot (the builder's partition of the class's tiles)
 int grid_of(vmap_ctx* ctx, int c) {
-    return uses_wide(ctx, c) ? wide_ranges(ctx) : ctx->n_sm * ctas_of(c) * ctx->gmult[c];
+    return uses_wide(ctx, c) || uses_w32(ctx, c) ? wide_ranges(ctx) : ctx->n_sm * ctas_of(c) * ctx->gmult[c];
 }
 
 TileArgs base_args(vmap_ctx* ctx) {
@@ -442,6 +446,57 @@ cudaError_t launch_wide_dw(vmap_ctx* ctx, int loss_only, bool after_fb = false) 
     return cudaLaunchKernelEx(&cfg, k_wide_dw, wa);
 }
 
+W32Args w32_args(vmap_ctx* ctx) {
+    TileArgs ta = base_args(ctx);
+    ta.tiles = ctx->tiles_d + 3LL * ctx->tile_cap;
+    ta.n_tiles = ctx->counts_d + BC_TILES + 3;
+    ta.dyn = ctx->dyn_d + 2 * 3;
+    return W32Args{ta, reinterpret_cast<float* const*>(ctx->act_pp_d), ctx->tile_loss_d, 0};
+}
+
+// FP32 width-128 forward/input-gradient kernel: one CTA per SM taking tiles
+// from the class's counter; launched in stream order (it starts the step's
+// FP32 tile kernels), the narrower classes chained behind it
+template <int MODE>
+cudaError_t launch_w32_fb(vmap_ctx* ctx) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_w32_fb<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)W32FbCfg::BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    k_w32_fb<MODE><<<ctx->n_sm, W32_THREADS, W32FbCfg::BYTES, ctx->stream>>>(ctx->sp, w32_args(ctx));
+    return cudaGetLastError();
+}
+
+// FP32 width-128 weight-gradient kernel, after the step's other FP32 tile
+// kernels; with `pdl` launched with programmatic stream serialization (its
+// CTAs wait for the previous kernel, and through it for k_w32_fb, before
+// reading the records)
+cudaError_t launch_w32_dw(vmap_ctx* ctx, int loss_only, bool pdl) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_w32_dw, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)W32DwCfg::BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    W32Args wa = w32_args(ctx);
+    wa.loss_only = loss_only;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(W32JOBS * wide_ranges(ctx)));
+    cfg.blockDim = dim3(W32_THREADS);
+    cfg.dynamicSmemBytes = W32DwCfg::BYTES;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k_w32_dw, wa);
+}
+
 // one width class of the step's tile kernel (FP32 SIMT, or BF16 tensor cores)
 template <int MODE>
 cudaError_t launch_class(vmap_ctx* ctx, int c, int pdl = PDL_NONE) {
@@ -470,7 +525,9 @@ cudaError_t launch_class(vmap_ctx* ctx, int c, int pdl = PDL_NONE) {
     return launch_tile_c<MODE>(c, grid, ctx->stream, ctx->sp, ta, pdl);
 }
 
-int class_mmax(vmap_ctx* ctx, int c) { return uses_tc(ctx, c) || uses_wide(ctx, c) ? TM : mmax_of(c); }
+int class_mmax(vmap_ctx* ctx, int c) {
+    return uses_tc(ctx, c) || uses_wide(ctx, c) ? TM : uses_w32(ctx, c) ? W32M : mmax_of(c);
+}
 
 // ---- the step's launches ------------------------------------------------------
 vmap_status launch_build_sample(vmap_ctx* ctx, int given, bool build = true) {
@@ -524,6 +581,7 @@ vmap_status launch_tiles(vmap_ctx* ctx, int mask) {
     bool after_fp32 = false;   // ... an FP32 tile kernel
     bool after_sample = ctx->after_sample;   // ... the sampler
     ctx->after_sample = false;
+    bool w32_dw = false;       // the FP32 width-128 weight-gradient kernel is due
     static const int order_tc[NCLASS] = {0, 1, 2, 3}, order_fp32[NCLASS] = {3, 0, 1, 2};
     for (int ci = 0; ci < NCLASS; ++ci) {
         const int c = ctx->bf16 ? order_tc[ci] : order_fp32[ci];
@@ -531,7 +589,15 @@ vmap_status launch_tiles(vmap_ctx* ctx, int mask) {
         cudaError_t e;
         const bool after_sample_c = after_sample;   // only the first launch follows the sampler
         after_sample = false;
-        if (uses_wide(ctx, c)) {
+        if (uses_w32(ctx, c)) {
+            // forward and input gradients first; the weight gradients after the
+            // narrower classes, which fill the SMs its CTAs leave
+            const int pi = MODE == MODE_TRAIN ? prof_begin(ctx, PS_TILE + c) : -1;
+            e = launch_w32_fb<MODE>(ctx);
+            prof_end(ctx, pi);
+            w32_dw = true;
+            after_fp32 = pi < 0;
+        } else if (uses_wide(ctx, c)) {
             constexpr int BM = MODE == MODE_FORWARD ? MODE_FORWARD : MODE_TRAIN;
             int pi = MODE == MODE_TRAIN ? prof_begin(ctx, PS_TILE + c) : -1;
             e = launch_wide_fb<BM>(ctx, after_tile && pi < 0);
@@ -556,6 +622,12 @@ vmap_status launch_tiles(vmap_ctx* ctx, int mask) {
         }
         if (e != cudaSuccess)
             return fail(ctx, VMAP_ERR_CUDA, "tile kernel (H=%d) failed: %s", hidden_of(c), cudaGetErrorString(e));
+    }
+    if (w32_dw) {
+        const int pi = MODE == MODE_TRAIN ? prof_begin(ctx, PS_WIDE_DW) : -1;
+        const cudaError_t e = launch_w32_dw(ctx, MODE == MODE_FORWARD, after_fp32 && pi < 0);
+        prof_end(ctx, pi);
+        if (e != cudaSuccess) return fail(ctx, VMAP_ERR_CUDA, "k_w32_dw failed: %s", cudaGetErrorString(e));
     }
     return VMAP_OK;
 }
@@ -654,7 +726,8 @@ vmap_status grow_act(vmap_ctx* ctx, long long need) {
     if (ctx->act_d) CU(cudaFree(ctx->act_d));
     ctx->act_d = nullptr;
     ctx->act_cap = 0;
-    CU(cudaMalloc((void**)&ctx->act_d, (size_t)cap * WideAct::BYTES));
+    const size_t per_tile = ctx->bf16 ? (size_t)WideAct::BYTES : (size_t)W32Act::FLOATS * sizeof(float);
+    CU(cudaMalloc((void**)&ctx->act_d, (size_t)cap * per_tile));
     ctx->act_cap = cap;
     // pageable source: staged before the call returns
     CU(cudaMemcpyAsync(ctx->act_pp_d, &ctx->act_d, sizeof(unsigned char*), cudaMemcpyHostToDevice, ctx->stream));
@@ -689,7 +762,7 @@ vmap_status sample_plan(vmap_ctx* ctx, const int* rays_per_object, const float* 
         return fail(ctx, VMAP_ERR_CAPACITY, "%lld rays exceed max_rays_total %d", rays, ctx->cfg.max_rays_total);
     for (int c = 0; c < NCLASS; ++c)
         if (tiles[c] > ctx->tile_cap) return fail(ctx, VMAP_ERR_CAPACITY, "too many tiles");
-    if (uses_wide(ctx, 3) && tiles[3] > ctx->act_cap)
+    if ((uses_wide(ctx, 3) || uses_w32(ctx, 3)) && tiles[3] > ctx->act_cap)
         if (vmap_status s = grow_act(ctx, tiles[3])) return s;
     // the builder skips unchanged layouts; a new launch shape invalidates its record
     long long key = 0;
@@ -882,9 +955,10 @@ vmap_status vmap_init_objects(vmap_ctx** out, const vmap_config* cfg, void* cuda
         // img_count(H) - param_count(H) = 11 H - 4 <= 1408, plus 64-element alignment per object
         ctx->img_cap = ctx->param_cap + 1536LL * K;
         ALLOC(ctx->img_d, sizeof(__nv_bfloat16) * ctx->img_cap);
-        ALLOC(ctx->act_pp_d, sizeof(unsigned char*));
-        ALLOC(ctx->tile_loss_d, sizeof(float) * 4 * (size_t)ctx->tile_cap);
     }
+    // width-128 records (grown on demand) and per-tile loss sums, both paths
+    ALLOC(ctx->act_pp_d, sizeof(unsigned char*));
+    ALLOC(ctx->tile_loss_d, sizeof(float) * 8 * (size_t)ctx->tile_cap);
 #undef ALLOC
     e = cudaMemsetAsync(ctx->steps_d, 0, sizeof(int) * K, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->status_d, 0, sizeof(int) * K, ctx->stream);
@@ -1456,8 +1530,12 @@ vmap_status vmap_profile_read(vmap_ctx* ctx, int slot, const char** name, long l
     if (!ctx) return VMAP_ERR_ARG;
     if (slot < 0 || slot >= PS_N) return VMAP_ERR_ARG;
     prof_flush(ctx);
-    if (name) *name = (slot >= PS_TILE && slot < PS_TILE + NCLASS && ctx->bf16) ? kProfNamesBf16[slot - PS_TILE]
-                                                                               : kProfNames[slot];
+    if (name) {
+        *name = (slot >= PS_TILE && slot < PS_TILE + NCLASS && ctx->bf16) ? kProfNamesBf16[slot - PS_TILE]
+                                                                         : kProfNames[slot];
+        if (!ctx->bf16 && slot == PS_TILE + 3) *name = "k_w32_fb<128>";
+        if (!ctx->bf16 && slot == PS_WIDE_DW) *name = "k_w32_dw<128>";
+    }
     if (launches) *launches = ctx->prof_n[slot];
     if (total_ms) *total_ms = ctx->prof_ms[slot];
     return VMAP_OK;
