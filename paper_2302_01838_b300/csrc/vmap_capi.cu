@@ -101,6 +101,7 @@ struct vmap_ctx {
     int* counts_d = nullptr;
     int* sig_d = nullptr;           // inputs of the last batch build ([0] = -1: rebuild)
     int* dyn_d = nullptr;           // [NCLASS][2] tile counters of dynamically scheduled classes
+    float* enc_d[NCLASS] = {nullptr, nullptr, nullptr, nullptr};   // FP32 per-CTA encoding copies
     int dyn_cap[NCLASS] = {0, 0, 0, 0};   // tiles a class may have to be scheduled dynamically
     int* done_d = nullptr;          // per object: reduce warps that have finished (reset by the last)
     long long build_key = -1;       // launch shape the last build ran with
@@ -522,6 +523,7 @@ cudaError_t launch_class(vmap_ctx* ctx, int c, int pdl = PDL_NONE) {
         ta.dyn = ctx->dyn_d + 2 * c;
         ta.dyn_on = ctx->counts_d + BC_DYN + c;
     }
+    ta.enc_scratch = ctx->enc_d[c];
     return launch_tile_c<MODE>(c, grid, ctx->stream, ctx->sp, ta, pdl);
 }
 
@@ -945,6 +947,13 @@ vmap_status vmap_init_objects(vmap_ctx** out, const vmap_config* cfg, void* cuda
     ALLOC(ctx->counts_d, sizeof(int) * BC_N);
     ALLOC(ctx->sig_d, sizeof(int) * (2 + (size_t)K));
     ALLOC(ctx->dyn_d, sizeof(int) * 2 * NCLASS);
+    if (!ctx->bf16) {
+        // the FP32 tile kernel's encoding copies (hidden 32 and 64: the encoding shares the
+        // hidden rows), one block per CTA of the largest grid
+        const long long enc_floats[NCLASS] = {0, (long long)DINP * TileSmem<32>::LD, (long long)DINP * TileSmem<64>::LD, 0};
+        for (int c = 1; c < 3; ++c)
+            ALLOC(ctx->enc_d[c], sizeof(float) * (size_t)enc_floats[c] * ctx->n_sm * ctas_of(c) * GMULT_MAX);
+    }
     ALLOC(ctx->done_d, sizeof(int) * K);
     ALLOC(ctx->given_d, sizeof(float) * REC * (size_t)cfg->max_rays_total);
     ALLOC(ctx->loss_d, sizeof(float) * K);
@@ -990,6 +999,8 @@ vmap_status vmap_destroy(vmap_ctx* ctx) {
                     ctx->img_d,    ctx->act_d,    ctx->act_pp_d, ctx->tile_loss_d, ctx->sig_d,  ctx->done_d, ctx->dyn_d,
                     ctx->scene_d,  ctx->ray_bj_d, ctx->loss_pp_d};
     for (void* p : ptrs)
+        if (p) cudaFree(p);
+    for (float* p : ctx->enc_d)
         if (p) cudaFree(p);
     for (auto& p : ctx->pending) {
         cudaEventDestroy(p.a);

@@ -362,6 +362,9 @@ struct TileArgs {
     float* qrgb;              // MODE_QUERY: colour [n][3] or NULL
     int* dyn;                 // [2]: next tile, CTAs done (dynamic scheduling), or NULL
     const int* dyn_on;        // builder: non-zero when this step schedules the class dynamically
+    float* enc_scratch;       // [grid][DINP * LD] (widths whose encoding shares the hidden rows): the
+                              // encoding is saved there for the layer-1 weight gradient, or NULL
+                              // (recomputed)
 };
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -604,6 +607,12 @@ __global__ void __launch_bounds__(TileCfg<H>::THREADS, TileCfg<H>::CTAS) k_tile_
         encode<LD>(sp, g, Mpad);
         stage_wait();
         __syncthreads();
+        // hidden layers 2-4 overwrite the encoding: keep a copy for the layer-1 weight gradient
+        float* const enc_save = (!SM::GSEP && GRAD && ta.enc_scratch)
+                                    ? ta.enc_scratch + (long long)blockIdx.x * (DINP * LD) : nullptr;
+        if (enc_save)
+            for (int i = threadIdx.x * 4; i < DINP * LD; i += blockDim.x * 4)
+                *reinterpret_cast<float4*>(enc_save + i) = *reinterpret_cast<const float4*>(g + i);
 
         // ---- forward --------------------------------------------------------
         gemm_fwd<H, DINP, 0>(g, LD, ws, P + b_off(H, 0), act, LD, Mpad);
@@ -711,7 +720,12 @@ __global__ void __launch_bounds__(TileCfg<H>::THREADS, TileCfg<H>::CTAS) k_tile_
             gemm_fwd<H, H, 2>(hz, LD, ws, nullptr, ha, LD, Mpad);
             __syncthreads();
         }
-        if (!SM::GSEP) {
+        if (enc_save) {
+            // the encoding was overwritten by hidden layers 2-4: copy it back (this
+            // CTA's own stores, ordered before by the barriers since)
+            stage(g, enc_save, DINP * LD);
+            __syncthreads();
+        } else if (!SM::GSEP) {
             // the encoding was overwritten by hidden layers 2-4: recompute it
             for (int m = threadIdx.x; m < Mpad; m += blockDim.x) {
                 float x0 = 0.f, x1 = 0.f, x2 = 0.f;
