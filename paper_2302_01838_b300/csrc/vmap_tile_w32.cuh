@@ -11,22 +11,24 @@
 //   k_w32_fb  per tile of <= 128 samples (whole rays of one object): encoding,
 //             the five forward GEMMs, rendering and losses (Eq. 3-5), and the
 //             input-gradient GEMMs dZ_l = (dZ_{l+1} W_{l+1}) * [h_l > 0]. Only
-//             two activation buffers live in shared memory; each GEMM operand
-//             the weight gradients need (encoding, h1..h4, dY, dZ1..dZ4) is
-//             written to a record buffer, FP32, sample-major ([128 samples]
-//             [features]) from the registers that formed it, and the ReLU masks
-//             of h1..h4 stay in registers (a thread's backward block is the
-//             same 8x8 block of samples and features as its forward one).
-//             Tiles come from a counter.
-//   k_w32_dw  weight gradients dW_l = sum over samples of dZ_l^T h_{l-1}: CTA
-//             (range r, job j) streams job j's operands of every tile in range
-//             r through three stages of asynchronous copies, in 32-sample
-//             chunks (contiguous in the sample-major records), and accumulates
-//             8x8 blocks of dW_l in registers, the samples being the GEMM's
-//             reduction axis as in k_w32_fb's own GEMMs; bias gradients are
-//             column sums of dZ_l in the same order. At the end of each object
-//             run the CTA stores its layer's part of the run slot, which the
-//             reduce kernel sums in slot order.
+//             two activation buffers live in shared memory; the GEMM operands
+//             the weight gradients of layers 1-4 need (encoding, h1..h3,
+//             dZ1..dZ4) are written to a record buffer, FP32, sample-major
+//             ([128 samples][features]) from the registers that formed them;
+//             the output layer's weight and bias gradients and the bias
+//             gradients of layers 1-4 are summed over the tile on chip. The
+//             ReLU masks of h1..h4 stay in registers (a thread's backward block
+//             is the same 8x8 block of samples and features as its forward
+//             one). Tiles come from a counter.
+//   k_w32_dw  weight gradients dW_l = sum over samples of dZ_l^T h_{l-1},
+//             l = 1..4: CTA (range r, job j) streams job j's two operands of
+//             every tile in range r through three stages of asynchronous
+//             copies, in 64-sample chunks (contiguous in the sample-major
+//             records), and accumulates 8x8 blocks of dW_l in registers, the
+//             samples being the GEMM's reduction axis as in k_w32_fb's own
+//             GEMMs. At the end of each object run the CTA stores its layer's
+//             part of the run slot (adding the run's per-tile sums in tile
+//             order), which the reduce kernel sums in slot order.
 #pragma once
 #include "vmap_common.cuh"
 #include "vmap_tile_fp32.cuh"
@@ -36,7 +38,7 @@ namespace vmapk {
 constexpr int W32H = 128;          // hidden width of this path
 constexpr int W32M = 128;          // samples per tile
 constexpr int W32_THREADS = 256;   // 16 x 16 threads, an 8x8 block each
-constexpr int W32JOBS = 4;         // weight-gradient jobs: (W1, W5), W2, W3, W4
+constexpr int W32JOBS = 4;         // weight-gradient jobs: W1, W2, W3, W4
 constexpr int W32LD = W32M + 4;    // activation row stride in shared memory (floats)
 
 // per-tile record (floats): sample-major operand blocks [W32M samples][width],
@@ -45,12 +47,12 @@ constexpr int W32LD = W32M + 4;    // activation row stride in shared memory (fl
 struct W32Act {
     static constexpr int BLK = W32M * W32H;
     static constexpr int G0 = 0;                        // encoding [128][128] (features 96..127 zero)
-    static constexpr int HL = G0 + BLK;                 // h1..h4 [128][128] each
-    static constexpr int DZ = HL + 4 * BLK;             // dZ1..dZ4 [128][128] each
+    static constexpr int HL = G0 + BLK;                 // h1..h3 [128][128] each
+    static constexpr int DZ = HL + 3 * BLK;             // dZ1..dZ4 [128][128] each
     static constexpr int DB = DZ + 4 * BLK;             // sum over samples of dZ1..dZ4 [4][128]
     static constexpr int DW5 = DB + 4 * W32H;           // sum over samples of dY[o] h4[k] [4][128]
     static constexpr int DB5 = DW5 + NOUT * W32H;       // sum over samples of dY [4] (+ 4 unused)
-    static constexpr long long FLOATS = DB5 + 8;        // 148,488 (593,952 bytes)
+    static constexpr long long FLOATS = DB5 + 8;        // 132,104 (528,416 bytes)
     __host__ __device__ static constexpr int h(int l) { return HL + l * BLK; }    // h_{l+1}
     __host__ __device__ static constexpr int dz(int l) { return DZ + l * BLK; }   // dZ_{l+1}
 };

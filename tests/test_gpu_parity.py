@@ -93,7 +93,17 @@ def test_train_step_parity_small_scene_20_steps():
 def test_train_step_parity_mixed_widths_ragged_tiles():
     """H in {16, 32, 64, 128}, S in {16, 22, 32}, rays spanning several tiles,
     a ragged last tile and a single-ray object; 3 steps."""
-    sc = vh.mixed_scene(seed=12)
+    _train_parity(vh.mixed_scene(seed=12), 3)
+
+
+def test_train_step_parity_hidden128_ranges_span_objects():
+    """55 hidden-128 tiles of 27 objects over 37 weight-gradient ranges (at
+    148 SMs): the ten ranges that hold the last tile of one object and the
+    first of the next flush two runs; 2 steps."""
+    _train_parity(vh.wide_scene(seed=21), 2)
+
+
+def _train_parity(sc, steps):
     vm = vh.library_context(sc)
     cfg = vh.oracle_config(sc)
     ost = vh.oracle_states(sc)
@@ -101,7 +111,7 @@ def test_train_step_parity_mixed_widths_ragged_tiles():
     R = [o["rays"] for o in sc["objects"]]
     loss = torch.empty(K, device="cuda")
     skip = [dict() for _ in range(K)]
-    for step in range(3):
+    for step in range(steps):
         vm.sample_rays(R)
         vm.train_step(loss)
         for k in range(K):
@@ -112,18 +122,19 @@ def test_train_step_parity_mixed_widths_ragged_tiles():
         assert np.all(rel <= LOSS_RTOL), f"step {step}: {rel}"
     for k in range(K):
         p, _, _, st = vm.get_object_state(k)
-        assert st == 3
+        assert st == steps
         errs = vh.layer_errors_masked(p.cpu().numpy(), ost[k].params, ost[k].H, skip[k])
         assert max(errs) <= W_RTOL, f"object {k} (H={ost[k].H}): {errs}, kink rows {skip[k]}"
         # the kink rows themselves, at the looser bound (a flipped ReLU' on one
         # sample moves that unit's Adam steps by up to 2 lr per element)
         kerr = vh.layer_errors_rows(p.cpu().numpy(), ost[k].params, ost[k].H, skip[k])
         assert all(e <= KINK_RTOL for e in kerr.values()), f"object {k}: kink-row errors {kerr}"
-        assert all(len(r) <= ost[k].H // 8 for r in skip[k].values()), skip[k]
+        assert all(len(r) <= ost[k].H // 8 for r in skip[k].values()), f"object {k}: {skip[k]}"
 
 
-def test_gradients_and_center_gradient_match_oracle():
-    sc = vh.mixed_scene(seed=13)
+@pytest.mark.parametrize("scene", ["mixed", "wide"])
+def test_gradients_and_center_gradient_match_oracle(scene):
+    sc = vh.mixed_scene(seed=13) if scene == "mixed" else vh.wide_scene(seed=22)
     vm = vh.library_context(sc)
     cfg = vh.oracle_config(sc)
     K = len(sc["objects"])

@@ -67,6 +67,27 @@ def mixed_scene(seed=7):
     return dict(objects=objs, B=scenes.make_B(seed + 1000), seed=seed)
 
 
+def wide_scene(seed=21):
+    """27 hidden-128 objects of 1 to 14 rays, cycling through the three
+    samples-per-ray classes (55 tiles of at most 128 samples), spread over the
+    37 weight-gradient ranges of the width-128 kernels at 148 SMs, ten of
+    which hold tiles of two objects; plus one hidden-32 object. Small objects
+    keep the number of ReLU-kink rows (kink_rows) per object small."""
+    rng = np.random.default_rng(seed)
+    classes = [(15, 17), (10, 12), (7, 9)]
+    rays = [9, 12, 3, 10, 7, 1, 11, 8, 14, 5, 10, 6, 12, 9, 4, 11, 7, 13, 8, 10, 2, 12, 9, 11, 6, 10, 8]
+    spec = [(128, classes[i % 3], r) for i, r in enumerate(rays)]
+    spec.insert(4, (32, (10, 12), 40))
+    objs = []
+    for H, (ns, nc), R in spec:
+        o = scenes.make_object(rng, (1, 3), 0.1, 0.3, 0.2, H=H, per_view=200)
+        o["init"] = scenes.init_weights(rng, H)
+        o["n_surface"], o["n_strat"] = ns, nc
+        o["rays"] = R
+        objs.append(o)
+    return dict(objects=objs, B=scenes.make_B(seed + 1000), seed=seed)
+
+
 def kink_rows(cfg, ob, R, tau=5e-6):
     """Hidden units whose ReLU pre-activation comes within tau of 0 on some
     sample of this step's batch (oracle values). Their ReLU' may differ
