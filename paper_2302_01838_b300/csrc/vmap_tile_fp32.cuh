@@ -53,7 +53,11 @@ template <int H> struct TileSmem {
     static constexpr int G = GSEP ? 4 * H * LD : H * LD;               // [96][LD] encoding
     static constexpr int Y = GSEP ? (4 * H + DINP) * LD : 4 * H * LD;  // [4][LD] outputs / grads
     static constexpr int W = Y + 4 * LD;                               // weight staging
-    static constexpr int RED = W + WS;
+    // a second weight buffer (widths up to 64, where it fits beside the
+    // activations): each forward layer's weights are copied during the GEMM before it
+    static constexpr bool WDB = H <= 64;
+    static constexpr int W2 = W + WS;                                  // [H][H] second buffer
+    static constexpr int RED = W2 + (WDB ? H * H : 0);
     static constexpr int PS = RED + RED_FLOATS;                        // [LD] per-sample scratch
     static constexpr int TS = PS + LD;                                 // [LD] sample depths t
     static constexpr int RAYS = TS + LD;                               // [RTMAX][RAYF]
@@ -288,12 +292,10 @@ __device__ __forceinline__ void stage_w1_rows(float* dst, const float* __restric
 // series of sin to r^9 and cos to r^10 (truncation below 2e-9), and the
 // quadrant k mod 4 picks and signs them. Its result agrees with sincosf to a
 // few ulp; a dependent chain of about 20 operations instead of the library
-// routine's longer one. Larger |p| goes to sincosf.
-__device__ __forceinline__ void sincos_enc(float p, float* sp_, float* cp_) {
-    if (fabsf(p) > 131072.f) {
-        sincosf(p, sp_, cp_);
-        return;
-    }
+// routine's longer one. sincos_fast holds for |p| <= SINCOS_FAST_MAX only;
+// sincos_enc sends larger |p| to sincosf.
+constexpr float SINCOS_FAST_MAX = 131072.f;
+__device__ __forceinline__ void sincos_fast(float p, float* sp_, float* cp_) {
     const float k = rintf(p * 0.636619746685028076171875f);        // 2/pi
     float r = fmaf(-k, 1.57079637050628662109375f, p);            // c1
     r = fmaf(-k, -4.37113882867379300296306610107421875e-8f, r);  // c2
@@ -312,28 +314,56 @@ __device__ __forceinline__ void sincos_enc(float p, float* sp_, float* cp_) {
     *sp_ = (q & 2) ? -s0 : s0;
     *cp_ = ((q + 1) & 2) ? -c0 : c0;
 }
+__device__ __forceinline__ void sincos_enc(float p, float* sp_, float* cp_) {
+    if (fabsf(p) > SINCOS_FAST_MAX) sincosf(p, sp_, cp_);
+    else sincos_fast(p, sp_, cp_);
+}
 
 // Gaussian encoding of the tile's points: rows 0..2 of g hold x~ on entry;
 // rows 3..47 get sin(B x~), rows 48..92 cos(B x~), rows 93..95 zero.
 // Item f = j Mpad + m is stepped by the CTA size without a division per item.
+// A thread takes ENC_ITEMS items per pass: their loads first, then their
+// sincos chains side by side, then their stores (the stores may alias the
+// next pass's loads as far as the compiler knows, so within a pass is where
+// the chains can overlap). Items past the last one compute a dummy and store
+// nothing.
+constexpr int ENC_ITEMS = 4;
 template <int LD>
 __device__ __forceinline__ void encode(const StepParams& sp, float* g, int Mpad) {
     if (Mpad <= 0) return;
     const int dq = blockDim.x / Mpad, dr = blockDim.x - dq * Mpad;
     int j = threadIdx.x / Mpad, m = threadIdx.x - j * Mpad;
-    for (; j < NF;) {
-        const float p = fmaf(sp.B[3 * j + 2], g[2 * LD + m],
-                             fmaf(sp.B[3 * j + 1], g[1 * LD + m], sp.B[3 * j] * g[0 * LD + m]));
-        float s, c;
-        sincos_enc(p, &s, &c);
-        g[(3 + j) * LD + m] = s;
-        g[(3 + NF + j) * LD + m] = c;
-        j += dq;
-        m += dr;
-        if (m >= Mpad) {
-            m -= Mpad;
-            ++j;
+    while (j < NF) {
+        int jj[ENC_ITEMS], mm[ENC_ITEMS];
+#pragma unroll
+        for (int u = 0; u < ENC_ITEMS; ++u) {
+            jj[u] = j;
+            mm[u] = m;
+            j += dq;
+            m += dr;
+            if (m >= Mpad) {
+                m -= Mpad;
+                ++j;
+            }
         }
+        float p[ENC_ITEMS], sn[ENC_ITEMS], cs[ENC_ITEMS];
+#pragma unroll
+        for (int u = 0; u < ENC_ITEMS; ++u) {
+            const int jc = min(jj[u], NF - 1);
+            p[u] = fmaf(sp.B[3 * jc + 2], g[2 * LD + mm[u]],
+                        fmaf(sp.B[3 * jc + 1], g[1 * LD + mm[u]], sp.B[3 * jc] * g[0 * LD + mm[u]]));
+        }
+#pragma unroll
+        for (int u = 0; u < ENC_ITEMS; ++u) sincos_fast(p[u], &sn[u], &cs[u]);
+#pragma unroll
+        for (int u = 0; u < ENC_ITEMS; ++u)
+            if (fabsf(p[u]) > SINCOS_FAST_MAX) sincosf(p[u], &sn[u], &cs[u]);
+#pragma unroll
+        for (int u = 0; u < ENC_ITEMS; ++u)
+            if (jj[u] < NF) {
+                g[(3 + jj[u]) * LD + mm[u]] = sn[u];
+                g[(3 + NF + jj[u]) * LD + mm[u]] = cs[u];
+            }
     }
     for (int i = threadIdx.x; i < 3 * Mpad; i += blockDim.x) g[(DIN + i / Mpad) * LD + (i % Mpad)] = 0.f;
 }
@@ -474,6 +504,7 @@ __global__ void __launch_bounds__(TileCfg<H>::THREADS, TileCfg<H>::CTAS) k_tile_
     float* g = smem + SM::G;
     float* yb = smem + SM::Y;
     float* ws = smem + SM::W;
+    float* ws2 = smem + SM::W2;
     float* red = smem + SM::RED;
     float* tsm = smem + SM::TS;
     float* rays = smem + SM::RAYS;
@@ -603,6 +634,7 @@ __global__ void __launch_bounds__(TileCfg<H>::THREADS, TileCfg<H>::CTAS) k_tile_
             g[2 * LD + m] = x2;
         }
         stage_issue(ws, WT + wt_layer_off(H, 0), DINP * H);   // W1^T [96][H], during the encoding
+        if (SM::WDB) stage_issue(ws2, WT + wt_layer_off(H, 1), H * H);   // W2^T
         __syncthreads();
         encode<LD>(sp, g, Mpad);
         stage_wait();
@@ -617,15 +649,32 @@ __global__ void __launch_bounds__(TileCfg<H>::THREADS, TileCfg<H>::CTAS) k_tile_
         // ---- forward --------------------------------------------------------
         gemm_fwd<H, DINP, 0>(g, LD, ws, P + b_off(H, 0), act, LD, Mpad);
         __syncthreads();
+        if (SM::WDB) {
+            // layer l reads W_{l+1}^T from ws2 (l odd) or ws (l even); the layer
+            // after it's weights go to the other buffer, which the previous GEMM
+            // read (free since the barrier after it), and arrive during this GEMM
 #pragma unroll 1
-        for (int l = 1; l < 4; ++l) {
-            stage(ws, WT + wt_layer_off(H, l), H * H);
-            __syncthreads();
-            gemm_fwd<H, H, 0>(act + (l - 1) * H * LD, LD, ws, P + b_off(H, l), act + l * H * LD, LD, Mpad);
+            for (int l = 1; l < 4; ++l) {
+                float* const wcur = (l & 1) ? ws2 : ws;
+                float* const wnext = (l & 1) ? ws : ws2;
+                if (l < 3) stage_issue(wnext, WT + wt_layer_off(H, l + 1), H * H);
+                else stage_issue(wnext, WT + wt_layer_off(H, 4), H * NOUT);
+                gemm_fwd<H, H, 0>(act + (l - 1) * H * LD, LD, wcur, P + b_off(H, l), act + l * H * LD, LD, Mpad);
+                stage_wait();
+                __syncthreads();
+            }
+        } else {
+#pragma unroll 1
+            for (int l = 1; l < 4; ++l) {
+                stage(ws, WT + wt_layer_off(H, l), H * H);
+                __syncthreads();
+                gemm_fwd<H, H, 0>(act + (l - 1) * H * LD, LD, ws, P + b_off(H, l), act + l * H * LD, LD, Mpad);
+                __syncthreads();
+            }
+            stage(ws, WT + wt_layer_off(H, 4), H * NOUT);
             __syncthreads();
         }
-        stage(ws, WT + wt_layer_off(H, 4), H * NOUT);
-        __syncthreads();
+        // W5^T [H][4] is in ws either way
         gemm_fwd<NOUT, H, 1>(act + 3 * H * LD, LD, ws, P + b_off(H, 4), yb, LD, Mpad);
         __syncthreads();
         if (MODE == MODE_QUERY) {
