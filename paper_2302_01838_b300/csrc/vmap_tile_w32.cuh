@@ -78,10 +78,13 @@ __device__ __forceinline__ int w32_n(int tn, int j) { return (j < 4 ? 0 : 60) + 
 
 // acc[i][j] (+)= sum_k A[k][m_i] B[k][n_j] (m_i = w32_m(tm, i), n_j =
 // w32_n(tn, j)); A: [K][LA], B: [K][LB]. The next k's operands load while
-// this k's 64 FMAs run. ZERO: start from zero, else add to acc.
-template <int K, int LA = W32LD, int LB = W32H, bool ZERO = true>
+// this k's 64 FMAs run. ZERO: start from zero, else add to acc. kc < K
+// stops after the first kc rows of k (RUNTIME_K only; rows of A and B up to
+// kc are read).
+template <int K, int LA = W32LD, int LB = W32H, bool ZERO = true, bool RUNTIME_K = false>
 __device__ __forceinline__ void w32_mm(const float* __restrict__ A, const float* __restrict__ B, int tm, int tn,
-                                       float (&acc)[8][8]) {
+                                       float (&acc)[8][8], int kc = K) {
+    if (!RUNTIME_K) kc = K;
     if (ZERO) {
 #pragma unroll
         for (int i = 0; i < 8; ++i)
@@ -93,8 +96,8 @@ __device__ __forceinline__ void w32_mm(const float* __restrict__ A, const float*
     float4 a0 = *reinterpret_cast<const float4*>(a), a1 = *reinterpret_cast<const float4*>(a + 64);
     float4 b0 = *reinterpret_cast<const float4*>(b), b1 = *reinterpret_cast<const float4*>(b + 64);
 #pragma unroll 4
-    for (int k = 0; k < K; ++k) {
-        const int kn = k + 1 < K ? k + 1 : k;
+    for (int k = 0; k < kc; ++k) {
+        const int kn = k + 1 < kc ? k + 1 : k;
         const float4 na0 = *reinterpret_cast<const float4*>(a + kn * LA);
         const float4 na1 = *reinterpret_cast<const float4*>(a + kn * LA + 64);
         const float4 nb0 = *reinterpret_cast<const float4*>(b + kn * LB);
@@ -443,6 +446,7 @@ __global__ void __launch_bounds__(W32_THREADS, 1) k_w32_fb(StepParams sp, W32Arg
 // shared memory of k_w32_dw (floats): NST stages of 64-sample chunks, a
 // chunk being two contiguous sample-major blocks (dZ_l and the layer's input)
 constexpr int W32CH = 64;
+constexpr int W32DW_ROWS = 1024;   // tiles of a range whose valid rows are tabled
 struct W32DwCfg {
     static constexpr int BLK = W32CH * W32H;
     static constexpr int STAGE = 2 * BLK;          // A = dZ_l [64][128], B = input [64][128]
@@ -492,6 +496,20 @@ __global__ void __launch_bounds__(W32_THREADS, 1) k_w32_dw(W32Args wa) {
     }
     if (n <= 0) return;
     const float* act = *wa.act;
+    // valid samples of the range's first W32DW_ROWS tiles (later tiles count as
+    // full): chunks copy and contract only those rows (the padded rows' dZ is
+    // zero, so leaving them out changes no sum)
+    __shared__ int s_rows[W32DW_ROWS];
+    for (int i = tid; i < n && i < W32DW_ROWS; i += W32_THREADS) {
+        const TileDev td = ta.tiles[t0 + i];
+        s_rows[i] = min(W32M, td.nr * ta.objs[td.obj].S);
+    }
+    __syncthreads();
+    auto chunk_rows = [&](int c) {
+        const int i = c / (W32M / W32CH);
+        const int r = (i < W32DW_ROWS ? s_rows[i] : W32M) - (c % (W32M / W32CH)) * W32CH;
+        return r < 0 ? 0 : (r > W32CH ? W32CH : r);
+    };
     // job j: dW_{j+1} from dZ_{j+1} and the layer's input (job 0: the encoding);
     // job 0 also gathers the output layer's per-tile sums
     const int L = j;
@@ -502,6 +520,7 @@ __global__ void __launch_bounds__(W32_THREADS, 1) k_w32_dw(W32Args wa) {
     auto issue = [&](int c) {
         const float* rec = act + (t0 + c / CPT) * W32Act::FLOATS;
         const int m0 = (c % CPT) * W32CH;
+        const int rows = chunk_rows(c);
         const float* srca = rec + a_off + m0 * W32H;
         const float* srcb = rec + b_off_rec + m0 * W32H;
         const unsigned base = (unsigned)__cvta_generic_to_shared(smem + (c % C::NST) * C::STAGE);
@@ -509,6 +528,7 @@ __global__ void __launch_bounds__(W32_THREADS, 1) k_w32_dw(W32Args wa) {
         for (int it = 0; it < PIECES; ++it) {
             const int p = tid + it * W32_THREADS;            // 16-byte piece of the stage
             const int q = p & (C::BLK / 4 - 1);              // ... within its block
+            if (q / (W32H / 4) >= rows) continue;            // its row is padding
             const float* src = (p < C::BLK / 4 ? srca : srcb) + 4 * q;
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(base + 16u * p), "l"(src) : "memory");
         }
@@ -531,7 +551,7 @@ __global__ void __launch_bounds__(W32_THREADS, 1) k_w32_dw(W32Args wa) {
         if (c + 2 < nch) issue(c + 2);
         const float* st = smem + (c % C::NST) * C::STAGE;
         // dW[n][k] += sum over the chunk's samples m of dZ[m][n] x[m][k]
-        w32_mm<W32CH, W32H, W32H, false>(st, st + C::BLK, ta_, tb, acc);
+        w32_mm<W32CH, W32H, W32H, false, true>(st, st + C::BLK, ta_, tb, acc, chunk_rows(c));
         __syncthreads();   // every thread is done with stage c % NST before it is refilled
         // ---- run end: store this job's part of the run slot ------------------
         if (c % CPT != CPT - 1) continue;
