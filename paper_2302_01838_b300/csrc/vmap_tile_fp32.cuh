@@ -70,8 +70,13 @@ template <int H> struct TileSmem {
 // A: [K][lda] in smem, Bm: [K][N] dense in smem.
 // EPI 0: + bias, ReLU;  EPI 1: + bias;  EPI 2: * (out[n][m] > 0), in place.
 // A warp covers 4 sample quads x 8 output quads: its A loads touch 64
-// consecutive bytes and its B loads 128, one wavefront each; sample quads are
-// grouped by four, so a tile wastes at most three quads of padding per group.
+// consecutive bytes and its B loads 128. A warp's 16-byte shared load takes
+// as many wavefronts as the most distinct vectors any group of four
+// consecutive lanes reads, and two at least (measured with ncu's wavefront
+// counters); so each four-lane group takes 2 sample quads x 2 output quads:
+// two wavefronts per load for A and B (lanes along the sample quads would
+// cost four for A). Sample quads are grouped by four, so a tile wastes at
+// most three quads of padding per group.
 // ---------------------------------------------------------------------------
 template <int N, int K, int EPI>
 __device__ __forceinline__ void gemm_fwd(const float* __restrict__ A, int lda,
@@ -82,8 +87,18 @@ __device__ __forceinline__ void gemm_fwd(const float* __restrict__ A, int lda,
     const int MQ = Mpad >> 2;
     const int items = ((MQ + 3) >> 2) * 4 * NQ;
     for (int f = threadIdx.x; f < items; f += blockDim.x) {
-        const int mq = (f / (4 * NQ)) * 4 + (f & 3);
-        const int nq = (f >> 2) % NQ;
+        int mq, nq;
+        if (NQ % 2 == 0) {
+            // each group of four lanes takes 2 sample quads x 2 output quads (a
+            // 16-byte shared load costs as many wavefronts as the most distinct
+            // vectors any four-lane group reads, two at least)
+            const int e = f % (4 * NQ), g = e >> 2, t = e & 3;
+            mq = (f / (4 * NQ)) * 4 + 2 * (g & 1) + (t & 1);
+            nq = 2 * (g >> 1) + (t >> 1);
+        } else {
+            mq = (f / (4 * NQ)) * 4 + (f & 3);
+            nq = (f >> 2) % NQ;
+        }
         if (mq >= MQ) continue;
         float acc[4][4], bb[4];
 #pragma unroll
@@ -136,10 +151,10 @@ __device__ __forceinline__ void acc_store(float* p, float v, bool first) { *p = 
 // dW[n][k] (+)= sum_m Z[n][m] * A[k][m]   (reduction over the tile's samples)
 // and db[n] (+)= sum_m Z[n][m], into global g (canonical [n][Kreal]) and gb;
 // `first` stores, otherwise the tile's sums are added to what the run holds.
-// A thread owns rows n = nq + NQ i and k = kq + KQ j (i, j < 4). Lanes differ
-// in kq: each group of eight reads eight consecutive A rows (no bank
-// conflicts), the Z row is a broadcast, and the run slot's row n is read and
-// written by the warp as consecutive floats (coalesced).
+// A thread owns rows n = nq + NQ i and k = kq + KQ j (i, j < 4). A warp covers
+// 8 k-groups x 4 n-groups, each group of four lanes 2 x 2 (two wavefronts per
+// 16-byte load, as in gemm_fwd; eight consecutive A rows fall on distinct
+// banks), and the run slot's rows are read and written as 32-byte pieces.
 // The sample range is split SPLIT ways (interleaved quads) to fill the CTA;
 // split partials are combined in a fixed order through smem. Without a split
 // the accumulators start from the run's old values (loaded before the sample
@@ -165,7 +180,18 @@ __device__ __forceinline__ void gemm_dw(const float* __restrict__ Z, const float
     }
     for (int f = threadIdx.x; f < T * SPLIT; f += blockDim.x) {
         const int s = f / T, r = f % T;
-        const int kq = r % KQ, nq = r / KQ;
+        int kq, nq;
+        if (KQ % 8 == 0 && NQ % 4 == 0) {
+            // a warp: 8 k-groups x 4 n-groups, each group of four lanes 2 k x 2 n
+            // (two wavefronts per 16-byte load; see gemm_fwd), the warp's eight
+            // A rows on distinct banks
+            const int rw = r >> 5, lane = r & 31, g = lane >> 2, t = lane & 3;
+            kq = (rw % (KQ / 8)) * 8 + 2 * (g & 3) + (t & 1);
+            nq = (rw / (KQ / 8)) * 4 + 2 * (g >> 2) + (t >> 1);
+        } else {
+            kq = r % KQ;
+            nq = r / KQ;
+        }
         float acc[4][4];
         if (SPLIT == 1 && !first) {
 #pragma unroll
