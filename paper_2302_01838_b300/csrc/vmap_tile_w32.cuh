@@ -76,6 +76,18 @@ struct W32FbCfg {
 __device__ __forceinline__ int w32_m(int tm, int i) { return (i < 4 ? 0 : 60) + tm * 4 + i; }
 __device__ __forceinline__ int w32_n(int tn, int j) { return (j < 4 ? 0 : 60) + tn * 4 + j; }
 
+// A thread's register-tile coordinates (16 x 16 over the CTA's 256 threads).
+// A warp's 16-byte shared load costs as many wavefronts as the most distinct
+// vectors any group of four consecutive lanes reads (two at least), so each
+// four-lane group takes 2 tm x 2 tn (two wavefronts for every operand load;
+// lanes along tn would cost four for B); a warp covers 4 tm x 8 tn.
+static_assert(W32_THREADS == 256, "w32_lane_map covers 16 x 16 threads");
+__device__ __forceinline__ void w32_lane_map(int tid, int& tm, int& tn) {
+    const int w = tid >> 5, g = (tid >> 2) & 7, t = tid & 3;
+    tm = (w >> 1) * 4 + 2 * (g & 1) + (t & 1);
+    tn = (w & 1) * 8 + 2 * (g >> 1) + (t >> 1);
+}
+
 // acc[i][j] (+)= sum_k A[k][m_i] B[k][n_j] (m_i = w32_m(tm, i), n_j =
 // w32_n(tn, j)); A: [K][LA], B: [K][LB]. The next k's operands load while
 // this k's 64 FMAs run. ZERO: start from zero, else add to acc. kc < K
@@ -113,8 +125,8 @@ __device__ __forceinline__ void w32_mm(const float* __restrict__ A, const float*
 }
 
 // store a thread's block to out[n][m] (feature-major) and, when rec is not
-// NULL, to the sample-major record rec[m][n] (a half warp writes 256
-// consecutive bytes of a sample's row): with bias, ReLU and the mask bits of
+// NULL, to the sample-major record rec[m][n] (a warp writes 128 consecutive
+// bytes of each of four samples' rows): with bias, ReLU and the mask bits of
 // the result (bit 8 i + j: h[n_j][m_i] > 0); or, with `mask`, the block
 // times those bits
 template <bool FWD>
@@ -195,9 +207,9 @@ __global__ void __launch_bounds__(W32_THREADS, 1) k_w32_fb(StepParams sp, W32Arg
     float* rays = smem + C::RAYS;
     __shared__ long long s_tile;
     const int tid = threadIdx.x, warp = tid >> 5, nwarps = W32_THREADS / 32;
-    // a half warp spans the 16 feature groups of one sample group (record rows
-    // written whole)
-    const int tm = tid >> 4, tn = tid & 15;
+    // a warp writes 128-byte pieces of four samples' record rows
+    int tm, tn;
+    w32_lane_map(tid, tm, tn);
     float* cs = smem + C::CS;
     constexpr long long PC = param_count(W32H);
     const long long n = *ta.n_tiles;
@@ -462,7 +474,8 @@ __global__ void __launch_bounds__(W32_THREADS, 1) k_w32_dw(W32Args wa) {
     extern __shared__ __align__(16) float smem[];
     const int tid = threadIdx.x;
     // a thread's 8x8 block of dW_l: rows n = w32_m(ta_, i), columns k = w32_n(tb, j)
-    const int tb = tid & 15, ta_ = tid >> 4;
+    int ta_, tb;
+    w32_lane_map(tid, ta_, tb);
     const int ranges = gridDim.x / W32JOBS;
     const int rg = blockIdx.x / W32JOBS, j = blockIdx.x % W32JOBS;
     if (wa.loss_only && j != 0) return;
