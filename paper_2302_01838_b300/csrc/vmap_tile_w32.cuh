@@ -150,8 +150,10 @@ __device__ __forceinline__ unsigned long long w32_store(float (&acc)[8][8], floa
         }
         if (rec) {
             float* r = r0 + (i < 4 ? i : 60 + i) * W32H;
-            *reinterpret_cast<float4*>(r) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
-            *reinterpret_cast<float4*>(r + 64) = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+            // streaming stores: the records (more than L2 holds per step) are read
+            // once, and evicting them first keeps the run slots in L2 for the reduce
+            __stcs(reinterpret_cast<float4*>(r), make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]));
+            __stcs(reinterpret_cast<float4*>(r + 64), make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]));
         }
     }
 #pragma unroll
@@ -181,8 +183,8 @@ __device__ __forceinline__ void w32_record_enc(float* __restrict__ dst, const fl
         float v[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) v[u] = 8 * k8 + u < DINP ? src[(8 * k8 + u) * W32LD + m] : 0.f;
-        *reinterpret_cast<float4*>(dst + m * W32H + 8 * k8) = make_float4(v[0], v[1], v[2], v[3]);
-        *reinterpret_cast<float4*>(dst + m * W32H + 8 * k8 + 4) = make_float4(v[4], v[5], v[6], v[7]);
+        __stcs(reinterpret_cast<float4*>(dst + m * W32H + 8 * k8), make_float4(v[0], v[1], v[2], v[3]));   // streaming (see w32_store)
+        __stcs(reinterpret_cast<float4*>(dst + m * W32H + 8 * k8 + 4), make_float4(v[4], v[5], v[6], v[7]));
     }
 }
 
