@@ -88,7 +88,7 @@ __device__ __forceinline__ void gemm_fwd(const float* __restrict__ A, int lda,
     const int items = ((MQ + 3) >> 2) * 4 * NQ;
     for (int f = threadIdx.x; f < items; f += blockDim.x) {
         int mq, nq;
-        if (NQ % 2 == 0) {
+        if constexpr (NQ % 2 == 0) {
             // each group of four lanes takes 2 sample quads x 2 output quads (a
             // 16-byte shared load costs as many wavefronts as the most distinct
             // vectors any four-lane group reads, two at least)
@@ -181,7 +181,7 @@ __device__ __forceinline__ void gemm_dw(const float* __restrict__ Z, const float
     for (int f = threadIdx.x; f < T * SPLIT; f += blockDim.x) {
         const int s = f / T, r = f % T;
         int kq, nq;
-        if (KQ % 8 == 0 && NQ % 4 == 0) {
+        if constexpr (KQ % 8 == 0 && NQ % 4 == 0) {
             // a warp: 8 k-groups x 4 n-groups, each group of four lanes 2 k x 2 n
             // (two wavefronts per 16-byte load; see gemm_fwd), the warp's eight
             // A rows on distinct banks
