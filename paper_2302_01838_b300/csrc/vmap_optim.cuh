@@ -95,7 +95,8 @@ __device__ __forceinline__ long long wt_index(int H, long long p) {
 // warp of an object to finish (every other one has read the step count)
 // advances the object's step count unless it is frozen, and resets its counter.
 constexpr int REDUCE_THREADS = 256;
-constexpr int REDUCE_SLOT_LOADS = 4;    // slot loads in flight per lane
+constexpr int REDUCE_SLOT_LOADS = 4;    // slot loads in flight per lane (registers)
+constexpr int REDUCE_STAGED_SLOTS = 8;  // slot copies in flight per lane (staged in shared memory)
 constexpr int REDUCE_BLOCKS_PER_SM = 3; // the grid
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
@@ -119,6 +120,8 @@ __global__ void __launch_bounds__(REDUCE_THREADS, REDUCE_BLOCKS_PER_SM) k_reduce
     const int lane = threadIdx.x & 31;
     const int wpb = blockDim.x >> 5;
     const int n_units = 2 * counts[BC_ITEMS];   // (item, half)
+    // per warp: REDUCE_STAGED_SLOTS slots x 32 lanes x 16 bytes of run-slot staging
+    __shared__ __align__(16) float stage[(REDUCE_THREADS / 32) * REDUCE_STAGED_SLOTS * 32 * 4];
     // a second copy of the losses, to the caller's buffer (address read at run time)
     float* const loss_user = loss_user_pp ? *loss_user_pp : nullptr;
     // with n_obj: objects outside the batch report NaN (the batch's heads write the rest)
@@ -181,9 +184,33 @@ __global__ void __launch_bounds__(REDUCE_THREADS, REDUCE_BLOCKS_PER_SM) k_reduce
             const float* el = e + (long long)lane * stride;
             s0 = el[0]; s1 = el[1]; s2 = el[2];
         }
-        if (act) {
+        if (act && nr > REDUCE_STAGED_SLOTS) {
+            // many slots: REDUCE_STAGED_SLOTS per pass in flight as asynchronous 16-byte
+            // copies into this lane's own shared-memory staging (no registers held while
+            // they fly; the lane reads back only what it copied), added in slot order
             const float* src = part + bt.part_off + p;
-            for (int t = 0; t < nr; t += REDUCE_SLOT_LOADS) {   // (predicated) slot loads in flight, added in slot order
+            float* stg = stage + ((threadIdx.x >> 5) * REDUCE_STAGED_SLOTS * 32 + lane) * 4;
+            const unsigned s0a = (unsigned)__cvta_generic_to_shared(stg);
+            for (int t = 0; t < nr; t += REDUCE_STAGED_SLOTS) {
+#pragma unroll
+                for (int w = 0; w < REDUCE_STAGED_SLOTS; ++w)
+                    if (t + w < nr)
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s0a + 512u * w),
+                                     "l"(src + (long long)(t + w) * stride)
+                                     : "memory");
+                asm volatile("cp.async.commit_group;\n" ::: "memory");
+                asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+#pragma unroll
+                for (int w = 0; w < REDUCE_STAGED_SLOTS; ++w)
+                    if (t + w < nr) {
+                        const float4 v = *reinterpret_cast<const float4*>(stg + 128 * w);
+                        g.x += v.x; g.y += v.y; g.z += v.z; g.w += v.w;
+                    }
+            }
+        } else if (act) {
+            // few slots: (predicated) register loads in flight, added in slot order
+            const float* src = part + bt.part_off + p;
+            for (int t = 0; t < nr; t += REDUCE_SLOT_LOADS) {
                 float4 v[REDUCE_SLOT_LOADS];
 #pragma unroll
                 for (int w = 0; w < REDUCE_SLOT_LOADS; ++w) v[w] = t + w < nr ? ld4(src + (long long)(t + w) * stride) : g;
