@@ -564,7 +564,9 @@ vmap_status launch_build_sample(vmap_ctx* ctx, int given, bool build = true) {
         prof_end(ctx, pi);
         CHECK_LAUNCH("k_build");
     }
-    const int blocks = (ctx->cfg.max_rays_total + SAMPLE_RAYS_PER_BLOCK - 1) / SAMPLE_RAYS_PER_BLOCK;
+    // one wave of blocks whose warps stride over the batch (at most one warp per ray)
+    const int blocks = std::min((ctx->cfg.max_rays_total + SAMPLE_RAYS_PER_BLOCK - 1) / SAMPLE_RAYS_PER_BLOCK,
+                                ctx->n_sm * SAMPLE_BLOCKS_PER_SM);
     pi = prof_begin(ctx, PS_SAMPLE);
     k_sample<<<blocks, 32 * SAMPLE_RAYS_PER_BLOCK, 0, ctx->stream>>>(ctx->sp, ctx->objs_d, ctx->ob_d, ctx->bobj_d, ctx->bray_d,
                                              ctx->ray_bj_d, ctx->counts_d, given ? ctx->given_d : ctx->pool_d, given,
