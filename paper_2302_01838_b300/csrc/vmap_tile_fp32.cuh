@@ -167,7 +167,11 @@ __device__ __forceinline__ void gemm_dw(const float* __restrict__ Z, const float
     constexpr int NQ = N / 4, KQ = KP / 4, T = NQ * KQ;
     constexpr int S0 = NT / T > 0 ? NT / T : 1;
     constexpr int S1 = RED_FLOATS / (N * KP) > 0 ? RED_FLOATS / (N * KP) : 1;
-    constexpr int SPLIT = S0 < S1 ? S0 : S1;   // SPLIT == 1 never touches red
+    constexpr int SPLIT0 = S0 < S1 ? S0 : S1;
+    // the output layer (N = 4, few items) combines its partials by a chain of
+    // SPLIT loads per element: at most 64 threads' worth of partials (measured
+    // best at hidden 16 and 32: 16 and 8 parts instead of 64 and 32)
+    constexpr int SPLIT = (N < 8 && T * SPLIT0 > 64) ? (64 / T > 0 ? 64 / T : 1) : SPLIT0;   // SPLIT == 1 never touches red
     static_assert(SPLIT >= 1 && (SPLIT == 1 || SPLIT * N * KP <= RED_FLOATS), "split scratch");
     constexpr int NB = (N * 8 + NT - 1) / NT;   // bias-gradient items per thread
     const int MQ = Mpad >> 2;
